@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties one part of the oracle to something other than itself:
+closed forms on Cartesian cells, the paper's face-distance coefficients on
+affine cells (Sec. 2.2.6), exact reproduction of linear fields, the
+partition of unity of the trilinear weights, rigid-frame identities of
+Sec. 2.1 / Sec. 2.3.1, brute force on tiny grids, and finite differences for
+the guess network's gradients.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gen import axis_angle, euler_zyx
+
+
+def cart_grid(n, lo, hi):
+    axes = [lo[d] + (hi[d] - lo[d]) * np.arange(n[d]) / (n[d] - 1) for d in range(3)]
+    X, Y, Z = np.meshgrid(*axes, indexing="ij")
+    f = lambda a: a.ravel(order="F")
+    return oracle.OracleGrid(n, (False, False, False), f(X), f(Y), f(Z))
+
+
+def lerp_hex(X, xi):
+    """Trilinear map by nested linear interpolation along i, then j, then k (independent of the product form)."""
+    X = np.asarray(X).reshape(2, 2, 2, 3, order="F")  # [di, dj, dk, c], corner a = di + 2dj + 4dk
+    a = X[0] * (1 - xi[0]) + X[1] * xi[0]  # [dj, dk, c]
+    b = a[0] * (1 - xi[1]) + a[1] * xi[1]  # [dk, c]
+    return b[0] * (1 - xi[2]) + b[1] * xi[2]
+
+
+def distorted_hex(rng, amp=0.2, scale=1.0, origin=None):
+    X = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], dtype=float)
+    X = X + amp * rng.uniform(-1, 1, size=(8, 3))
+    X = X * scale
+    if origin is not None:
+        X = X + origin
+    return X
+
+
+# ----------------------------------------------------------------------------- weights
+def test_shape_functions_kronecker_and_unity():
+    rng = np.random.default_rng(1)
+    for a in range(8):
+        corner = np.array([a & 1, (a >> 1) & 1, (a >> 2) & 1], float)
+        N = oracle.shape(corner)
+        assert np.array_equal(N, np.eye(8)[a])
+    for _ in range(100):
+        xi = rng.uniform(-0.5, 1.5, 3)
+        N = oracle.shape(xi)
+        assert abs(N.sum() - 1.0) < 1e-15
+    # the sign-corrected form of the paper's trilinear formula: node (i,j,k) weighs (1-x)(1-y)(1-z)
+    N = oracle.shape(np.array([0.25, 0.5, 0.75]))
+    assert N[0] == pytest.approx(0.75 * 0.5 * 0.25, abs=1e-16)
+    assert N[7] == pytest.approx(0.25 * 0.5 * 0.75, abs=1e-16)
+    assert N[1] == pytest.approx(0.25 * 0.5 * 0.25, abs=1e-16)
+
+
+# ----------------------------------------------------------------------------- Newton
+def test_newton_recovers_xi_on_distorted_hexes():
+    rng = np.random.default_rng(2)
+    for t in range(300):
+        X = distorted_hex(rng, amp=0.2, scale=10 ** rng.uniform(-3, 0), origin=rng.uniform(-5, 5, 3))
+        xi_true = rng.uniform(0, 1, 3)
+        p = lerp_hex(X, xi_true)
+        ok, xi, it = oracle.newton_hex(X, p)
+        assert ok and it <= 10
+        assert np.max(np.abs(xi - xi_true)) < 1e-12
+
+
+def test_affine_cells_match_paper_face_distance_coefficients():
+    """On a parallelepiped the paper's a^1 = d^1/(d^1+d^2) (distances to the two i-faces, Sec. 2.2.6) is the
+    exact local coordinate; the same for j and k."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        E = rng.uniform(-1, 1, (3, 3)) + 2 * np.eye(3)
+        X0 = rng.uniform(-3, 3, 3)
+        X = np.array([X0 + (a & 1) * E[0] + ((a >> 1) & 1) * E[1] + ((a >> 2) & 1) * E[2] for a in range(8)])
+        p = X0 + rng.uniform(-0.3, 1.3, 3) @ E
+        ok, xi, _ = oracle.newton_hex(X, p)
+        assert ok
+        for m in range(3):
+            u, v = E[(m + 1) % 3], E[(m + 2) % 3]
+            n = np.cross(u, v)
+            n = n / np.linalg.norm(n)
+            if np.dot(n, E[m]) < 0:
+                n = -n  # inward normal of the face at offset 0
+            d1 = np.dot(p - X0, n)  # signed distance to the face through X0
+            d2 = np.dot(X0 + E[m] - p, n)  # signed distance to the opposite face
+            assert xi[m] == pytest.approx(d1 / (d1 + d2), abs=1e-13)
+
+
+def test_linear_fields_reproduced_exactly():
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        X = distorted_hex(rng, amp=0.25, scale=0.01, origin=rng.uniform(0, 4, 3))
+        p = lerp_hex(X, rng.uniform(0, 1, 3))
+        ok, xi, _ = oracle.newton_hex(X, p)
+        assert ok
+        N = oracle.shape(xi)
+        a, b = rng.uniform(-1, 1, 3), rng.uniform(-1, 1)
+        q = X @ a + b
+        assert np.dot(N, q) == pytest.approx(np.dot(a, p) + b, abs=1e-13 * (1 + abs(np.dot(a, p) + b)))
+        assert np.allclose(N @ X, p, rtol=0, atol=1e-15 * 4)
+
+
+def test_newton_fails_on_flat_hex():
+    X = np.array([[a & 1, (a >> 1) & 1, 0.0] for a in range(8)], dtype=float)  # zero thickness
+    ok, xi, _ = oracle.newton_hex(X, np.array([0.5, 0.5, 0.0]))
+    assert not ok
+
+
+# ----------------------------------------------------------------------------- donor selection
+def closed_form_cell(t, n):
+    """Lowest cell whose window [-1e-10, 1+1e-10] holds the scaled coordinate t on a uniform axis of n nodes."""
+    i = max(0, math.ceil(t - 1 - 1e-10))
+    return min(i, n - 2)
+
+
+def test_uniform_cartesian_closed_form_generic_points():
+    n, lo, hi = (9, 7, 6), (0.1, -0.3, 2.0), (1.3, 0.9, 2.5)
+    g = cart_grid(n, lo, hi)
+    h = [(hi[d] - lo[d]) / (n[d] - 1) for d in range(3)]
+    rng = np.random.default_rng(5)
+    pts = np.stack([rng.uniform(lo[d], hi[d], 2000) for d in range(3)], axis=1)
+    cell, xi, nodes, w = g.search(pts)
+    for q in range(len(pts)):
+        t = [(pts[q, d] - lo[d]) / h[d] for d in range(3)]
+        ijk = [min(int(math.floor(t[d])), n[d] - 2) for d in range(3)]
+        expect = ijk[0] + (n[0] - 1) * (ijk[1] + (n[1] - 1) * ijk[2])
+        assert cell[q] == expect
+        for d in range(3):
+            assert xi[q, d] == pytest.approx(t[d] - ijk[d], abs=1e-12)
+        assert abs(w[q].sum() - 1) < 1e-14
+
+
+def test_uniform_cartesian_ties_on_nodes_and_faces():
+    n, lo, hi = (6, 5, 7), (0.0, 0.0, 0.0), (1.0, 2.0, 3.0)
+    g = cart_grid(n, lo, hi)
+    h = [(hi[d] - lo[d]) / (n[d] - 1) for d in range(3)]
+    rng = np.random.default_rng(6)
+    pts, ts = [], []
+    for _ in range(400):
+        t = []
+        for d in range(3):
+            kind = rng.integers(3)
+            if kind == 0:
+                t.append(float(rng.integers(0, n[d])))  # on a node plane
+            else:
+                t.append(rng.uniform(0, n[d] - 1))
+        ts.append(t)
+        pts.append([lo[d] + t[d] * h[d] for d in range(3)])
+    pts = np.array(pts)
+    cell, xi, _, _ = g.search(pts)
+    for q, t in enumerate(ts):
+        tt = [(pts[q, d] - lo[d]) / h[d] for d in range(3)]
+        ijk = [closed_form_cell(tt[d], n[d]) for d in range(3)]
+        expect = ijk[0] + (n[0] - 1) * (ijk[1] + (n[1] - 1) * ijk[2])
+        assert cell[q] == expect, (t, cell[q], expect)
+
+
+def test_interior_node_goes_to_lowest_of_eight_cells():
+    n = (5, 5, 5)
+    g = cart_grid(n, (0, 0, 0), (1, 1, 1))
+    p = np.array([[0.5, 0.25, 0.75]])  # node (2,1,3)
+    cell, xi, _, _ = g.search(p)
+    assert cell[0] == 1 + 4 * (0 + 4 * 2)  # cell (1,0,2): the one with the lowest linear id
+    assert np.allclose(xi[0], [1, 1, 1], atol=1e-12)
+
+
+def test_outside_and_nonfinite_points():
+    g = cart_grid((4, 4, 4), (0, 0, 0), (1, 1, 1))
+    cell, xi, _, _ = g.search(np.array([[1.5, 0.5, 0.5], [-1e-6, 0.5, 0.5], [np.nan, 0.5, 0.5], [1 + 1e-12, 0.5, 0.5]]))
+    assert list(cell[:3]) == [-1, -1, -2]
+    assert cell[3] >= 0  # within the 1e-10 window of the boundary cell
+
+
+def random_curvilinear(n, amp, rng, periodic_i=False):
+    """A smooth invertible curvilinear grid: unit-box (or annulus sector when periodic in i) plus a sine warp."""
+    I, J, K = np.meshgrid(*[np.arange(m, dtype=float) for m in n], indexing="ij")
+    if periodic_i:
+        th = 2 * np.pi * I / n[0]
+        r = 1.0 + J / (n[1] - 1)
+        x, y, z = r * np.cos(th), r * np.sin(th), K / (n[2] - 1)
+    else:
+        x, y, z = I / (n[0] - 1), J / (n[1] - 1), K / (n[2] - 1)
+    h = 1.0 / max(n)
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    x = x + amp * h * np.sin(2 * np.pi * y + ph[0]) * np.cos(2 * np.pi * z)
+    y = y + amp * h * np.sin(2 * np.pi * z + ph[1]) * np.cos(2 * np.pi * x)
+    z = z + amp * h * np.sin(2 * np.pi * x + ph[2])
+    f = lambda a: a.ravel(order="F")
+    return oracle.OracleGrid(n, (periodic_i, False, False), f(x), f(y), f(z), bins=(3, 3, 3))
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_bins_equal_brute_force_on_tiny_grids(periodic):
+    rng = np.random.default_rng(7 + periodic)
+    n = (5, 5, 5) if periodic else (8, 8, 8)
+    g = random_curvilinear(n, 0.8, rng, periodic_i=periodic)
+    xyz = np.stack([g.x, g.y, g.z], axis=1)
+    lo, hi = xyz.min(0), xyz.max(0)
+    pts = [rng.uniform(lo - 0.05, hi + 0.05, size=(1500, 3)), xyz[rng.integers(0, len(xyz), 200)]]
+    # points on cell faces: midpoints of node pairs along each axis
+    a = rng.integers(0, len(xyz), 200)
+    pts.append(0.5 * (xyz[a] + xyz[np.minimum(a + 1, len(xyz) - 1)]))
+    pts = np.concatenate(pts)
+    c1, x1, _, _ = g.search(pts, brute=False)
+    c2, x2, _, _ = g.search(pts, brute=True)
+    assert np.array_equal(c1, c2)
+    found = c1 >= 0
+    assert found.sum() > 500
+    assert np.allclose(x1[found], x2[found], atol=0, rtol=0)
+
+
+def test_periodic_seam_cell():
+    rng = np.random.default_rng(9)
+    n = (6, 4, 3)
+    g = random_curvilinear(n, 0.0, rng, periodic_i=True)
+    # the seam cell i = n0-1 joins node i = 5 to node i = 0
+    nodes = g.cell_nodes(5)
+    assert nodes[0] == 5 and nodes[1] == 0
+    xyz = np.stack([g.x, g.y, g.z], axis=1)
+    X = xyz[nodes]
+    p = lerp_hex(X, np.array([0.4, 0.3, 0.6]))
+    cell, xi, _, _ = g.search(p[None])
+    assert cell[0] == 5
+    assert np.allclose(xi[0], [0.4, 0.3, 0.6], atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- frames
+def test_frame_round_trip_and_closed_form():
+    rng = np.random.default_rng(10)
+    R = euler_zyx(*rng.uniform(0, np.pi, 3))
+    assert np.abs(R.T @ R - np.eye(3)).max() < 1e-15
+    f = oracle.Frame(R, rng.uniform(-1, 1, 3), np.zeros(3), np.zeros(3))
+    x = rng.uniform(-1, 1, (100, 3))
+    assert np.abs(oracle.to_frame(f, oracle.to_inertial(f, x)) - x).max() < 1e-15
+    # a quarter turn about z carries body x-axis onto inertial y-axis
+    f = oracle.Frame(axis_angle(np.array([0, 0, 1.0]), np.pi / 2), np.array([1.0, 2.0, 3.0]), np.zeros(3), np.zeros(3))
+    assert np.allclose(oracle.to_inertial(f, np.array([[1.0, 0, 0]])), [[1.0, 3.0, 3.0]], atol=1e-15)
+
+
+def _rigid_case(rng):
+    """Donor body grid (distorted hexes) carrying the relative velocity of the inertial rigid field
+    u(x) = V0 + W0 x x, i.e. u_rel = R^T (u(x_in) - V - omega x (x_in - c)) at each node."""
+    V0, W0 = rng.uniform(-1, 1, 3), rng.uniform(-1, 1, 3)
+    g = random_curvilinear((6, 6, 6), 0.5, rng)
+    fd = oracle.Frame(euler_zyx(*rng.uniform(0, np.pi, 3)), rng.uniform(-1, 1, 3), rng.uniform(-1, 1, 3),
+                      rng.uniform(-1, 1, 3))
+    X = np.stack([g.x, g.y, g.z], axis=1)
+    x_in = oracle.to_inertial(fd, X)
+    u_in = V0 + np.cross(W0, x_in)
+    u_rel = (u_in - fd.V - np.cross(fd.omega, x_in - fd.c)) @ fd.R
+    fields = {"u": u_rel[:, 0], "v": u_rel[:, 1], "w": u_rel[:, 2], "p": np.zeros(len(X))}
+    return V0, W0, g, fd, fields
+
+
+def test_rigid_body_velocity_reproduced_in_inertial_receiver():
+    rng = np.random.default_rng(11)
+    V0, W0, g, fd, fields = _rigid_case(rng)
+    # receiver: an inertial (background) grid whose nodes lie inside the body grid
+    X = np.stack([g.x, g.y, g.z], axis=1)
+    inner = oracle.to_inertial(fd, X[[7 + 6 * 7 + 36 * k for k in range(1, 4)]] * 0.999 + 0.001 * X.mean(0))
+    fr = oracle.Frame(np.eye(3), np.zeros(3), np.zeros(3), np.zeros(3))
+    d = oracle.assemble([None, g], [fr, fd], inner, 0, np.arange(len(inner)), [1])
+    assert np.all(d.status == 0)
+    q = oracle.interpolate(d, [None, fields], [fr, fd], 0, mode="relative")
+    expect = V0 + np.cross(W0, d.x_in)
+    assert np.abs(q[:3].T - expect).max() < 1e-13
+
+
+def test_rigid_body_velocity_between_moving_frames():
+    rng = np.random.default_rng(12)
+    V0, W0, g, fd, fields = _rigid_case(rng)
+    fr = oracle.Frame(euler_zyx(*rng.uniform(0, np.pi, 3)), rng.uniform(-1, 1, 3), rng.uniform(-1, 1, 3),
+                      rng.uniform(-1, 1, 3))
+    X = np.stack([g.x, g.y, g.z], axis=1)
+    pts_in = oracle.to_inertial(fd, 0.5 * (X[8] + X[120]))[None]
+    rec = oracle.to_frame(fr, pts_in)
+    d = oracle.assemble([None, g], [fr, fd], rec, 0, np.arange(1), [1])
+    assert d.status[0] == 0
+    q = oracle.interpolate(d, [None, fields], [fr, fd], 0, mode="relative")
+    u_in = V0 + np.cross(W0, pts_in[0])
+    expect = fr.R.T @ (u_in - fr.V - np.cross(fr.omega, pts_in[0] - fr.c))
+    assert np.abs(q[:3, 0] - expect).max() < 1e-13
+
+
+def test_absolute_mode_is_pure_rotation():
+    """Sec. 2.3.1: u^m = Q^m (Q^n)^-1 u^n with Q = R^T; a quarter turn of the donor about z maps its body
+    x-velocity to the inertial (receiver) y-velocity, independent of V and omega."""
+    n = (3, 3, 3)
+    g = cart_grid(n, (0, 0, 0), (1, 1, 1))
+    fd = oracle.Frame(axis_angle(np.array([0, 0, 1.0]), np.pi / 2), np.zeros(3), np.array([5.0, 6, 7]),
+                      np.array([1.0, 2, 3]))
+    fr = oracle.Frame(np.eye(3), np.zeros(3), np.zeros(3), np.zeros(3))
+    fields = {"u": np.ones(27), "v": np.zeros(27), "w": np.zeros(27), "p": np.full(27, 2.5)}
+    pts = oracle.to_inertial(fd, np.array([[0.3, 0.4, 0.5]]))
+    d = oracle.assemble([None, g], [fr, fd], pts, 0, np.arange(1), [1])
+    q = oracle.interpolate(d, [None, fields], [fr, fd], 0, mode="absolute")
+    assert np.allclose(q[:, 0], [0, 1, 0, 2.5], atol=1e-15)
+
+
+def test_priority_list_falls_through_to_next_grid():
+    g1 = cart_grid((4, 4, 4), (0, 0, 0), (1, 1, 1))
+    g2 = cart_grid((4, 4, 4), (0.5, 0, 0), (2, 1, 1))
+    I = oracle.Frame(np.eye(3), np.zeros(3), np.zeros(3), np.zeros(3))
+    pts = np.array([[0.7, 0.5, 0.5], [1.7, 0.5, 0.5], [3.0, 0.5, 0.5], [np.inf, 0, 0]])
+    d = oracle.assemble([None, g1, g2], [I, I, I], pts, 0, np.arange(4), [1, 2])
+    assert list(d.grid) == [1, 2, -1, -1]
+    assert list(d.status) == [0, 0, 1, 2]
+
+
+# ----------------------------------------------------------------------------- guess network
+def _mlp(rng, H):
+    return {"W1": rng.normal(0, 0.8, (H, 3)), "b1": rng.normal(0, 0.1, H), "W2": rng.normal(0, 0.3, (H, H)),
+            "b2": rng.normal(0, 0.1, H), "W3": rng.normal(0, 0.3, (3, H)), "b3": rng.normal(0, 0.1, 3)}
+
+
+@pytest.mark.parametrize("H", [8, 64])
+def test_mlp_gradients_match_finite_differences(H):
+    rng = np.random.default_rng(13)
+    P = _mlp(rng, H)
+    x = rng.uniform(-1, 1, (16, 3))
+    t = rng.uniform(0, 1, (16, 3))
+    L, g = oracle.mlp_loss_grads(P, x, t)
+    h = 1e-6
+    for k in P:
+        flatp = P[k].reshape(-1)
+        idx = rng.choice(flatp.size, size=min(flatp.size, 12), replace=False)
+        for i in idx:
+            old = flatp[i]
+            flatp[i] = old + h
+            Lp, _ = oracle.mlp_loss_grads(P, x, t)
+            flatp[i] = old - h
+            Lm, _ = oracle.mlp_loss_grads(P, x, t)
+            flatp[i] = old
+            fd = (Lp - Lm) / (2 * h)
+            an = g[k].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(fd), abs(an)), (k, i, fd, an)
+
+
+def test_silu_closed_form():
+    z = np.array([-3.0, 0.0, 2.0])
+    assert np.allclose(oracle.silu(z), z / (1 + np.exp(-z)))
+    assert oracle.silu(np.array([0.0]))[0] == 0.0
+    assert oracle.dsilu(np.array([0.0]))[0] == pytest.approx(0.5)
+
+
+def test_adam_first_step_is_signed_lr():
+    """With bias correction the first Adam step moves each parameter by lr * sign(g) (|g| >> eps)."""
+    P = {"a": np.array([1.0, -2.0, 3.0])}
+    g = {"a": np.array([0.5, -4.0, 1e-2])}
+    m = {"a": np.zeros(3)}
+    v = {"a": np.zeros(3)}
+    oracle.adam_step(P, g, m, v, 1, lr=0.1)
+    assert np.allclose(P["a"], [0.9, -1.9, 2.9], atol=1e-6)
