@@ -1,0 +1,401 @@
+"""Benchmark of the overset assembly + interpolation step on GB300.
+
+One step = one time step of the moving-overset workload: set the frames of the moving grids
+(ovs_set_motion), find the donors of every fringe point (ovs_assemble) and interpolate u, v, w, p with the
+frame velocity transform (ovs_interpolate).  Default workload: the moving-ellipsoid case (stretched
+curvilinear background 128^3, 96x64x64 O-grid rotating at 2 pi rad/time and translating at 0.3/time,
+dt = 1e-3, 100 time steps, FP64 coordinates, FP32 fields), synthetic and seeded.
+
+Prints ONE JSON line (rank 0).  Metric: fringe points assembled + interpolated per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ovs|reference] [--workload cfg1|cfg0|cfg2]
+
+--impl reference times the plain FP64 CPU oracle (the method written out from the paper) on the host cores,
+on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fringe pts assembled+interpolated/s per step (learned vs plain), % HBM peak"
+UNIT = "pts/s"
+# Algorithmic bytes per fringe point (no cache reuse credited): assembly reads the node id (4), the receiver
+# coordinates (24), the previous donor (4) and the donor cell's 8 corners (8 x 3 x 8 = 192) and writes grid,
+# cell, xi, status (33): 257 B; interpolation reads the donor record (32) and 8 x 4 FP32 field values (128)
+# and writes 4 values (16): 176 B.
+BYTES_ASSEMBLE = 257
+BYTES_INTERP = 176
+BYTES_POINT = BYTES_ASSEMBLE + BYTES_INTERP
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_assemble_cfg1.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1910_09315_gb300", "csrc", f) for f in
+                  ("ovs_assemble.cu", "ovs_internal.cuh")]
+WORKLOADS = {
+    "cfg1": "moving ellipsoid: stretched curvilinear bg 128^3 + O-grid 96x64x64, 100 steps dt=1e-3, FP32 fields",
+    "cfg0": "tiny: Cartesian bg 64^3 + rotated perturbed box 32^3, FP64 fields",
+    "cfg2": "moving ellipsoid with bg 256^3 (plain guess), FP32 fields",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ovs", choices=["ovs", "reference"])
+    ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points per CPU-baseline sample (0: auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config_index(name: str) -> int:
+    return int(name[3:])
+
+
+def schedule(n: int, s: int) -> int:
+    """Step s of the run -> time step of the workload; beyond the last step the motion runs back (a triangle
+    wave keeps every step a small motion from the previous one)."""
+    if n <= 1:
+        return 0
+    p = 2 * (n - 1)
+    q = s % p
+    return q if q < n else p - q
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the kernel's source
+    has not changed since the capture (the summary records the source hash); else None."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def measured_peak():
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ovs_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_workload(name: str):
+    import gen
+
+    sc = gen.config(config_index(name))
+    return sc
+
+
+def step_inputs(sc, nsteps_total: int):
+    """Motions and fringe sets of every step the run visits (host, precomputed outside the timed region)."""
+    cache = {}
+    out = []
+    for s in range(nsteps_total):
+        ts = schedule(sc.nsteps, s)
+        if ts not in cache:
+            m = sc.motion(ts)
+            cache[ts] = (m, sc.fringe_sets(ts, m))
+        out.append(cache[ts])
+    return out
+
+
+# ----------------------------------------------------------------------------------------------------- ovs arm
+def run_ovs(args, rank, world, local):
+    import torch
+
+    from paper_1910_09315_gb300 import build as ovs_build
+    from paper_1910_09315_gb300 import ovs
+
+    ovs_build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sc = build_workload(args.workload)
+    K, W = args.steps, args.warmup
+    inputs = step_inputs(sc, W + K)
+    max_pts = max(sum(len(s.node_ids) for s in fs) for _, fs in inputs)
+    xi_dtype = ovs.OVS_F64 if sc.field_dtype == np.float64 else ovs.OVS_F32
+    stream = torch.cuda.current_stream(dev)
+    ctx = ovs.Context(device=local, stream=stream, max_points=max_pts)
+    gids = [ctx.add_grid(g.x, g.y, g.z, g.dims, g.periodic, g.role) for g in sc.grids]
+    fdt = torch.float64 if sc.field_dtype == np.float64 else torch.float32
+    fields = [tuple(torch.as_tensor(f[k]).to(dev, fdt) for k in ("u", "v", "w", "p")) for f in sc.fields]
+    # device-resident inputs of every step (node ids); donors and outputs preallocated
+    dev_sets = []
+    host_sets = []
+    for m, fs in inputs:
+        dev_sets.append([(s.receiver, torch.as_tensor(s.node_ids).to(dev), s.donors) for s in fs])
+        host_sets.append([(s.receiver, torch.as_tensor(s.node_ids).pin_memory(), s.donors) for s in fs])
+    donors = ctx.alloc_donors(max_pts, xi_dtype)
+    outs = [torch.empty(max_pts, dtype=fdt, device=dev) for _ in range(4)]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def donors_view(n):
+        return {"grid": donors["grid"][:n], "cell": donors["cell"][:n], "xi": donors["xi"][:3 * n],
+                "status": donors["status"][:n], "xi_dtype": xi_dtype, "n": n}
+
+    def one_step(s, sets):
+        m, fs = inputs[s]
+        for gid, mo in zip(gids, m):
+            ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
+        n = sum(int(x[1].numel()) for x in sets)
+        d = donors_view(n)
+        ctx.assemble(sets, donors=d)
+        ctx.interpolate(sets, d, fields, out=[o[:n] for o in outs])
+        return n
+
+    # warm-up (hints become warm exactly as in a time loop)
+    for s in range(W):
+        one_step(s, dev_sets[s])
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ovs.ovs_set_trace_events(ctx.ctx, ev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    step_ms, fast_ms, slow_ms, interp_ms, pts = [], [], [], [], 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for s in range(W, W + K):
+        flush.zero_()
+        e0.record(stream)
+        pts += one_step(s, dev_sets[s])
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        fast_ms.append(ev[0].elapsed_time(ev[1]))
+        slow_ms.append(ev[1].elapsed_time(ev[2]))
+        interp_ms.append(ev[3].elapsed_time(ev[4]))
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ovs.ovs_set_trace_events(ctx.ctx, [])
+    total_ms = float(np.sum(step_ms))
+    # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
+    host_out = [torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)]
+    host_status = torch.empty(max_pts, dtype=torch.uint8).pin_memory()
+    e2e_ms, h2d, d2h = [], 0, 0
+    for s in range(W, W + K):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sets = [(r, ids.to(dev, non_blocking=True), dn) for r, ids, dn in host_sets[s]]
+        n = one_step(s, sets)
+        for o, h in zip(outs, host_out):
+            h[:n].copy_(o[:n], non_blocking=True)
+        host_status[:n].copy_(donors["status"][:n], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        h2d += 4 * n
+        d2h += n * (4 * outs[0].element_size() + 1)
+    if world > 1:
+        t = torch.tensor([total_ms, float(np.sum(e2e_ms))], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_total = float(t[0]), float(t[1])
+    else:
+        e2e_total = float(np.sum(e2e_ms))
+    stats = None
+    if rank == 0:
+        ctx.set_options(collect_stats=1)
+        ctx.stats(reset=True)
+        one_step(W, dev_sets[W])
+        stats = ctx.stats(reset=True)
+        ctx.set_options(collect_stats=0)
+    ctx.sync()
+    pts_all = pts * world
+    value = pts_all / (total_ms / 1e3)
+    peak, peak_kind = measured_peak()
+    fast_avg_ms = float(np.mean(fast_ms))
+    pts_per_step = pts / K
+    achieved = BYTES_ASSEMBLE * pts_per_step / (fast_avg_ms / 1e3) / 1e9
+    traffic = profile_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 coords / f32 Newton+fields" if xi_dtype == ovs.OVS_F32 else "f64",
+        "data": "synthetic (seeded generator, shapes of the stated workload)",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "points_per_step": pts_per_step,
+                   "guess": "previous-donor hint + control-cell bins (plain)", "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) between timed steps", "launch": "k_assemble 256 thr/pt-thread"},
+        "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
+        "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_assemble_slow": float(np.mean(slow_ms)),
+                                  "k_interp": float(np.mean(interp_ms))},
+        "roofline": {"kernel": "k_assemble", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "bytes_per_point": BYTES_ASSEMBLE,
+                     "traffic": (traffic * pts_per_step / pts_per_step) if traffic is not None else None},
+        "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
+                "d2h_bytes_per_step": d2h // K},
+        "gpu_launches": 3 * K,
+        "clocks": ck,
+        "walk_stats": stats,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, inputs[W], args.cpu_sample)
+    return line
+
+
+# ----------------------------------------------------------------------------------------------------- oracle
+def oracle_points_per_s(sc, motions, fsets, sample_n: int, rng, grids=None):
+    import oracle
+
+    if grids is None:
+        grids = [oracle.OracleGrid.from_gen(g) for g in sc.grids]
+    frames = [oracle.frame_of(m) for m in motions]
+    sizes = np.array([len(s.node_ids) for s in fsets], dtype=np.int64)
+    tot = sizes.sum()
+    t0 = time.perf_counter()
+    n = 0
+    for s, sz in zip(fsets, sizes):
+        k = int(round(sample_n * sz / tot)) if sample_n < tot else int(sz)
+        if k == 0:
+            continue
+        ids = s.node_ids if k >= sz else np.sort(rng.choice(s.node_ids, size=k, replace=False))
+        d = oracle.assemble(grids, frames, sc.grids[s.receiver].xyz(), s.receiver, ids, s.donors)
+        oracle.interpolate(d, sc.fields, frames, s.receiver)
+        n += len(ids)
+    return n, time.perf_counter() - t0, grids
+
+
+def cpu_baseline(sc, step_input, sample_n: int):
+    import oracle
+
+    motions, fsets = step_input
+    rng = np.random.default_rng(7)
+    tot = sum(len(s.node_ids) for s in fsets)
+    if sample_n <= 0:
+        sample_n = min(tot, 400_000)
+    n, dt, _ = oracle_points_per_s(sc, motions, fsets, sample_n, rng)
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} of the {tot} fringe points of one step (seeded random subset), bins built before timing",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    import oracle
+
+    if rank != 0:
+        return None
+    oracle.build()
+    sc = build_workload(args.workload)
+    K, W = args.steps, args.warmup
+    inputs = step_inputs(sc, W + K)
+    rng = np.random.default_rng(11)
+    per_step = 20_000
+    grids = None
+    for s in range(W):
+        _, _, grids = oracle_points_per_s(sc, inputs[s][0], inputs[s][1], per_step, rng, grids)
+    tot_n, tot_t = 0, 0.0
+    for s in range(W, W + K):
+        n, dt, grids = oracle_points_per_s(sc, inputs[s][0], inputs[s][1], per_step, rng, grids)
+        tot_n += n
+        tot_t += dt
+    value = tot_n / tot_t
+    full = sum(len(x.node_ids) for x in inputs[W][1])
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": tot_t / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                       "points_per_step": tot_n / K, "full_points_per_step": full},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step} seeded random fringe points per step of {full}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        # the oracle runs on the host of rank 0 only; other ranks exit without work
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl")
+    line = run_ovs(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

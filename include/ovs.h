@@ -1,0 +1,207 @@
+/*
+ * ovs.h -- C ABI of libovs: per-time-step overset grid assembly (donor search)
+ * and boundary interpolation on one GPU.
+ *
+ * The method is the moving-overset assembly of Hedayat & Borazjani,
+ * "A parallel dynamic overset grid framework for immersed boundary methods"
+ * (arXiv 1910.09315):
+ *   - every moving grid carries a non-inertial frame: x_in = R x_body + c,
+ *     frame velocity V + omega x (x_in - c)            (Sec. 2.1, eq. "velocity")
+ *   - query (fringe) points of one grid get a donor hexahedron in another
+ *     grid, localised by control cells and found by a walking search with a
+ *     brute-force fallback                                (Sec. 2.2.5, Alg. 3)
+ *   - values are interpolated trilinearly from the donor's 8 nodes
+ *                                                        (Sec. 2.2.6)
+ *   - velocities are carried between frames              (Sec. 2.3.1,
+ *     eq. "velocity_non"), and a query point takes its donor from the first grid
+ *     of a priority list that has one                    (Sec. 2.4 item 1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All pointers marked "device" are CUDA device pointers on the context's
+ *    device; the library never allocates device memory: the caller provides
+ *    workspaces (sizes from the *_workspace_size calls) and all inputs and
+ *    outputs.  Host pointers are read during the call only.
+ *  - Every call that launches work enqueues it on the context's stream and
+ *    returns without waiting, except ovs_create_grid (which synchronises the
+ *    stream to size its control-cell bins) and ovs_sync / ovs_get_stats.
+ *  - Return value: OVS_OK (0) or a negative OVS_ERR_* code; ovs_last_error()
+ *    gives a message.  No C++ exception crosses the ABI.  A context is used by
+ *    one host thread at a time.
+ *  - Node arrays are structure-of-arrays, i fastest: node = i + ni (j + nj k).
+ *    Cell (i,j,k) has corners (i+di, j+dj, k+dk), corner a = di + 2 dj + 4 dk;
+ *    on a periodic axis index n wraps to 0; cells per axis: n-1, or n if
+ *    periodic; linear cell id = i + Ci (j + Cj k).
+ *  - Donor rule: among all cells of a donor grid whose local coordinates of
+ *    the point, from FP64 Newton inversion of the trilinear map, lie in
+ *    [-1e-10, 1 + 1e-10]^3, the one with the lowest linear id.
+ */
+#ifndef OVS_H
+#define OVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define OVS_OK 0
+#define OVS_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, non-orthogonal R, ...) */
+#define OVS_ERR_STATE (-2)     /* call out of order (no workspace attached, unknown grid, ...) */
+#define OVS_ERR_WORKSPACE (-3) /* a workspace is too small for the request */
+#define OVS_ERR_CUDA (-4)      /* a CUDA runtime call failed */
+#define OVS_ERR_NO_DEVICE (-5) /* no usable CUDA device: there is no CPU fallback */
+#define OVS_ERR_DEVICE (-6)    /* a kernel reported an error through the device status word */
+
+/* ---- per-point status (ovs_donors.status) ---- */
+#define OVS_STATUS_FOUND 0    /* donor found */
+#define OVS_STATUS_ORPHAN 1   /* no grid of the priority list contains the point */
+#define OVS_STATUS_BADINPUT 2 /* the point's coordinates are not finite */
+#define OVS_STATUS_MASK 0x0F  /* the bits above are statistics, not results: */
+#define OVS_STATUS_REFINED 0x20  /* decided by FP64 Newton (near a face, or FP64 precision mode) */
+#define OVS_STATUS_FALLBACK 0x10 /* decided by the exhaustive control-cell search */
+
+/* ---- dtypes ---- */
+#define OVS_F32 0
+#define OVS_F64 1
+
+/* ---- limits ---- */
+#define OVS_MAX_GRIDS 31
+#define OVS_MAX_SETS 64
+#define OVS_MAX_DONORS 8
+#define OVS_MAX_CELLS ((int64_t)1 << 27) /* cells per grid: < 2^27 - 1 (donor hints pack the grid id) */
+
+/* ---- options (ovs_set_options) ---- */
+#define OVS_VEL_RELATIVE 0 /* u_in = R_d u_d + V_d + w_d x (x_in - c_d); u_r = R_r^T (u_in - V_r - w_r x (x_in - c_r)) */
+#define OVS_VEL_ABSOLUTE 1 /* u_r = R_r^T R_d u_d (Sec. 2.3.1, eq. "velocity_non" with Q = R^T) */
+#define OVS_VEL_NONE 2     /* no transform: u, v, w interpolated like p */
+
+#define OVS_GUESS_HINT 0 /* start from the donor found for the same receiver node last call, else bins */
+#define OVS_GUESS_BINS 1 /* always start from the control-cell bin of the point */
+#define OVS_GUESS_MLP 2  /* body grids with a trained guess network: start there when no hint */
+
+typedef struct ovs_ctx ovs_ctx;
+
+typedef struct {
+    int32_t n[3];        /* node counts ni, nj, nk (>= 2 each) */
+    int32_t periodic[3]; /* 1 if the axis wraps (its last node connects to its first) */
+    const double* x;     /* device, n0*n1*n2 node coordinates in the grid's own frame (borrowed: must */
+    const double* y;     /*   stay valid and unchanged until ovs_ctx_destroy) */
+    const double* z;
+    int32_t role;        /* 0 background (inertial frame), 1 body (moving frame) */
+} ovs_grid_desc;
+
+typedef struct {
+    int32_t receiver;                     /* receiver grid id */
+    int32_t n_donors;                     /* 1..OVS_MAX_DONORS */
+    int32_t donors[OVS_MAX_DONORS];       /* donor grid ids, priority order (Sec. 2.4 item 1) */
+    int64_t n;                            /* number of query points (0 allowed) */
+    const int32_t* node_ids;              /* device, n receiver node ids */
+} ovs_fringe_set;
+
+typedef struct {
+    int64_t n;       /* capacity in points: >= sum of the sets' n (points are laid out set after set) */
+    int32_t* grid;   /* device [n]: donor grid id, -1 if none */
+    int32_t* cell;   /* device [n]: donor linear cell id, -1 if none */
+    void* xi;        /* device [3n] SoA: xi[0..n) eta[n..2n) zeta[2n..3n); float or double; NaN if none */
+    int32_t xi_dtype;/* OVS_F32 (FP32 Newton, FP64 only near faces) or OVS_F64 (FP64 for every point) */
+    uint8_t* status; /* device [n]: OVS_STATUS_* */
+} ovs_donors;
+
+typedef struct {
+    const void* u;   /* device, one value per node of the grid; NULL for a grid never used as donor */
+    const void* v;
+    const void* w;
+    const void* p;
+    int32_t dtype;   /* OVS_F32 or OVS_F64 */
+} ovs_fields;
+
+typedef struct {
+    void* u;         /* device [n] per point, in the receiver grid's frame */
+    void* v;
+    void* w;
+    void* p;
+    int32_t dtype;   /* must equal the donor fields' dtype */
+} ovs_fields_out;
+
+typedef struct {
+    int32_t velocity_mode; /* OVS_VEL_* (default RELATIVE) */
+    int32_t guess;         /* OVS_GUESS_* (default HINT) */
+    int32_t max_walk;      /* walk steps before the exhaustive fallback (default 48, 1..1024) */
+    int32_t collect_stats; /* 1: count walk steps / slow-path points (small atomic cost) */
+} ovs_options;
+
+typedef struct {
+    int64_t points;      /* points assembled since the last reset */
+    int64_t walk_steps;  /* cells visited by the FP32 walk */
+    int64_t refined;     /* points decided by FP64 Newton */
+    int64_t fallback;    /* points decided by the exhaustive control-cell search */
+    int64_t guess_used;  /* points started from a guess network */
+} ovs_stats;
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  Returns OVS_ERR_NO_DEVICE when no CUDA device is usable. */
+int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream);
+/* Destroy a context (waits for its stream).  Borrowed memory is not freed. */
+int ovs_ctx_destroy(ovs_ctx* ctx);
+/* Message of the last error on this context (never NULL). */
+const char* ovs_last_error(const ovs_ctx* ctx);
+/* Change the stream later calls enqueue on. */
+int ovs_set_stream(ovs_ctx* ctx, void* cuda_stream);
+
+/* Bytes of the context workspace needed for calls of up to `max_points` query points (slow-path
+ * queue, counters, status word). */
+int ovs_workspace_size(const ovs_ctx* ctx, int64_t max_points, size_t* bytes);
+/* Attach a caller-owned device workspace (256-byte aligned) of at least ovs_workspace_size bytes. */
+int ovs_workspace_attach(ovs_ctx* ctx, void* dptr, size_t bytes, int64_t max_points);
+
+/* Bytes of the per-grid workspace for a grid of these dimensions: cell records (128 B per cell),
+ * control-cell bins and the per-node donor hints. */
+int ovs_grid_workspace_size(const ovs_grid_desc* desc, size_t* bytes);
+/* Register a structured curvilinear grid (Sec. 2.2: one block of the composite grid).  Builds, in the
+ * caller's workspace, per-cell records and the control cells of Sec. 2.2.5 (uniform axis-aligned bins over
+ * the grid's bounding box, each cell registered in every bin its bounding box overlaps).  Synchronises the
+ * stream.  Grid ids are 0, 1, 2, ... in creation order.  Motion starts as the identity. */
+int ovs_create_grid(ovs_ctx* ctx, const ovs_grid_desc* desc, void* dworkspace, size_t bytes, int32_t* grid_id);
+
+/* Set a grid's rigid frame (Sec. 2.1, Fig. "non-inertial"): R (row-major 3x3, body -> inertial, must be
+ * orthogonal with det +1 to 1e-12), origin c, translational velocity V and angular velocity omega (inertial
+ * components).  Host arrays; takes effect for later calls. */
+int ovs_set_motion(ovs_ctx* ctx, int32_t grid_id, const double R[9], const double c[3], const double V[3],
+                   const double omega[3]);
+
+int ovs_set_options(ovs_ctx* ctx, const ovs_options* opts);
+int ovs_get_options(const ovs_ctx* ctx, ovs_options* opts);
+
+/* Donor search for every query point of `sets` (Sec. 2.2.5): frame map receiver -> inertial -> donor
+ * frame, localisation (hint / control cell / guess network), FP32 walk + Newton inversion of the trilinear
+ * map, FP64 decision near cell faces and lowest-id rule, exhaustive control-cell fallback.  Writes the
+ * donors of sets[0] first, then sets[1], ...  Updates the per-node hints of the receiver grids. */
+int ovs_assemble(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out);
+
+/* Trilinear interpolation (Sec. 2.2.6) of u, v, w, p from the donors found by ovs_assemble for the same
+ * sets, followed by the velocity transform of the options (Sec. 2.1 / Sec. 2.3.1), using the motions set
+ * now.  `fields` is indexed by grid id (nfields = number of grids).  Points without a donor get 0. */
+int ovs_interpolate(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* in,
+                    const ovs_fields* fields, int32_t nfields, const ovs_fields_out* out);
+
+/* Wait for the stream; returns OVS_ERR_DEVICE (and clears it) if a kernel flagged an error. */
+int ovs_sync(ovs_ctx* ctx);
+/* Read (synchronously) and optionally reset the statistics counters. */
+int ovs_get_stats(ovs_ctx* ctx, ovs_stats* out, int reset);
+
+/* Forget all per-node donor hints (next assemble starts cold). */
+int ovs_reset_hints(ovs_ctx* ctx);
+
+/* Tracing: record caller-created CUDA events (cudaEvent_t, NULL to skip one) on the context's stream at
+ * fixed points of later calls: ev[0] before the fast assembly kernel, ev[1] after it, ev[2] after the
+ * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it.
+ * n = 0 (or ev = NULL) switches tracing off.  The events must outlive their use. */
+int ovs_set_trace_events(ovs_ctx* ctx, void* const* ev, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OVS_H */

@@ -1,0 +1,576 @@
+// C ABI of libovs: argument checking, workspace carving, grid set-up and launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "ovs_internal.cuh"
+
+using namespace ovs;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kReduceBlocks = 1024;
+constexpr double kRegsPerCell = 12.0;  // registration capacity of the control-cell lists
+
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct GridHost {
+    ovs_grid_desc desc;
+    void* ws;
+    size_t ws_bytes;
+    int64_t nbins;
+    int64_t nreg;
+};
+
+}  // namespace
+
+struct ovs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // context workspace
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t max_points = 0;
+    GridDev* d_grids = nullptr;
+    unsigned long long* d_counters = nullptr;
+    int32_t* d_err = nullptr;
+    uint32_t* d_qcount = nullptr;
+    SlowEntry* d_queue = nullptr;
+    // grids
+    int ngrids = 0;
+    GridDev grids[OVS_MAX_GRIDS];
+    GridHost gh[OVS_MAX_GRIDS];
+    MotionDev motion[OVS_MAX_GRIDS];
+    ovs_options opts;
+    cudaEvent_t trace[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool tracing = false;
+};
+
+namespace {
+
+int fail(ovs_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(ovs_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, OVS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define OVS_CUDA(c, call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+void identity_motion(MotionDev& m) {
+    memset(&m, 0, sizeof m);
+    m.R[0] = m.R[4] = m.R[8] = 1.0;
+    m.identity = 1;
+}
+
+int64_t cells_axis(const ovs_grid_desc& d, int a) { return d.periodic[a] ? d.n[a] : d.n[a] - 1; }
+
+struct GridLayout {
+    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, partials, scan, out9, total;
+    int64_t ncells, nnodes, nbins_max, reg_cap;
+};
+
+GridLayout grid_layout(const ovs_grid_desc& d) {
+    GridLayout L;
+    L.ncells = cells_axis(d, 0) * cells_axis(d, 1) * cells_axis(d, 2);
+    L.nnodes = (int64_t)d.n[0] * d.n[1] * d.n[2];
+    L.nbins_max = std::max<int64_t>(1, L.ncells);
+    L.reg_cap = (int64_t)(kRegsPerCell * (double)L.ncells) + 64;
+    size_t off = 0;
+    L.rec = off;
+    off = align_up(off + (size_t)L.ncells * sizeof(CellRec));
+    L.bin_start = off;
+    off = align_up(off + (size_t)(L.nbins_max + 1) * 4);
+    L.bin_count = off;
+    off = align_up(off + (size_t)L.nbins_max * 4);
+    L.bin_rep = off;
+    off = align_up(off + (size_t)L.nbins_max * 4);
+    L.bin_cells = off;
+    off = align_up(off + (size_t)L.reg_cap * 4);
+    L.hint = off;
+    off = align_up(off + (size_t)L.nnodes * 4);
+    L.partials = off;
+    off = align_up(off + (size_t)kReduceBlocks * 9 * sizeof(double));
+    L.scan = off;
+    off = align_up(off + scan_scratch_elems(L.nbins_max) * 4);
+    L.out9 = off;
+    off = align_up(off + 9 * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+int check_desc(ovs_ctx* c, const ovs_grid_desc* d) {
+    if (!d) return fail(c, OVS_ERR_ARG, "grid descriptor is NULL");
+    for (int a = 0; a < 3; ++a) {
+        if (d->n[a] < 2) return fail(c, OVS_ERR_ARG, "grid axis %d has %d nodes (need >= 2)", a, d->n[a]);
+        if (d->periodic[a] != 0 && d->periodic[a] != 1)
+            return fail(c, OVS_ERR_ARG, "periodic[%d] must be 0 or 1", a);
+        if (d->periodic[a] && d->n[a] < 3) return fail(c, OVS_ERR_ARG, "periodic axis %d needs >= 3 nodes", a);
+    }
+    if (!d->x || !d->y || !d->z) return fail(c, OVS_ERR_ARG, "grid coordinate pointer is NULL");
+    if (d->role != 0 && d->role != 1) return fail(c, OVS_ERR_ARG, "role must be 0 (background) or 1 (body)");
+    int64_t ncells = cells_axis(*d, 0) * cells_axis(*d, 1) * cells_axis(*d, 2);
+    if (ncells >= OVS_MAX_CELLS - 1)
+        return fail(c, OVS_ERR_ARG, "grid has %lld cells; the limit is %lld", (long long)ncells,
+                    (long long)(OVS_MAX_CELLS - 1));
+    return OVS_OK;
+}
+
+int check_sets(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, int64_t* total) {
+    if (nsets < 0 || nsets > OVS_MAX_SETS) return fail(c, OVS_ERR_ARG, "nsets = %d (0..%d)", nsets, OVS_MAX_SETS);
+    if (nsets > 0 && !sets) return fail(c, OVS_ERR_ARG, "sets is NULL");
+    int64_t tot = 0;
+    for (int s = 0; s < nsets; ++s) {
+        const ovs_fringe_set& f = sets[s];
+        if (f.receiver < 0 || f.receiver >= c->ngrids)
+            return fail(c, OVS_ERR_ARG, "set %d: receiver grid %d does not exist", s, f.receiver);
+        if (f.n_donors < 1 || f.n_donors > OVS_MAX_DONORS)
+            return fail(c, OVS_ERR_ARG, "set %d: n_donors = %d (1..%d)", s, f.n_donors, OVS_MAX_DONORS);
+        for (int d = 0; d < f.n_donors; ++d)
+            if (f.donors[d] < 0 || f.donors[d] >= c->ngrids)
+                return fail(c, OVS_ERR_ARG, "set %d: donor grid %d does not exist", s, f.donors[d]);
+        if (f.n < 0) return fail(c, OVS_ERR_ARG, "set %d: n = %lld", s, (long long)f.n);
+        if (f.n > 0 && !f.node_ids) return fail(c, OVS_ERR_ARG, "set %d: node_ids is NULL", s);
+        tot += f.n;
+    }
+    if (tot > c->max_points)
+        return fail(c, OVS_ERR_WORKSPACE, "%lld points exceed the workspace's max_points %lld", (long long)tot,
+                    (long long)c->max_points);
+    if (tot >= ((int64_t)1 << 31) - 1) return fail(c, OVS_ERR_ARG, "more than 2^31 points in one call");
+    *total = tot;
+    return OVS_OK;
+}
+
+void fill_sets(const ovs_fringe_set* sets, int32_t nsets, SetDev* out) {
+    int64_t begin = 0;
+    for (int s = 0; s < nsets; ++s) {
+        out[s].receiver = sets[s].receiver;
+        out[s].ndonor = sets[s].n_donors;
+        for (int d = 0; d < OVS_MAX_DONORS; ++d) out[s].donors[d] = d < sets[s].n_donors ? sets[s].donors[d] : -1;
+        out[s].node_ids = sets[s].node_ids;
+        out[s].begin = begin;
+        out[s].n = sets[s].n;
+        begin += sets[s].n;
+    }
+    // empty sets must never be chosen by the point -> set lookup: give them the next set's begin
+}
+
+}  // namespace
+
+extern "C" {
+
+int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
+    if (!out) return OVS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        return OVS_ERR_NO_DEVICE;
+    }
+    if (device < 0 || device >= ndev) return OVS_ERR_ARG;
+    ovs_ctx* c = new (std::nothrow) ovs_ctx();
+    if (!c) return OVS_ERR_ARG;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    for (int g = 0; g < OVS_MAX_GRIDS; ++g) identity_motion(c->motion[g]);
+    c->opts.velocity_mode = OVS_VEL_RELATIVE;
+    c->opts.guess = OVS_GUESS_HINT;
+    c->opts.max_walk = 48;
+    c->opts.collect_stats = 0;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return OVS_ERR_NO_DEVICE;
+    }
+    *out = c;
+    return OVS_OK;
+}
+
+int ovs_ctx_destroy(ovs_ctx* c) {
+    if (!c) return OVS_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+    return OVS_OK;
+}
+
+const char* ovs_last_error(const ovs_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int ovs_set_stream(ovs_ctx* c, void* s) {
+    if (!c) return OVS_ERR_ARG;
+    c->stream = (cudaStream_t)s;
+    return OVS_OK;
+}
+
+int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
+    if (!c || !bytes || max_points < 0) return OVS_ERR_ARG;
+    size_t off = align_up(sizeof(GridDev) * OVS_MAX_GRIDS);
+    off = align_up(off + sizeof(unsigned long long) * kNumCounters);
+    off = align_up(off + 2 * sizeof(int32_t));
+    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    *bytes = off;
+    return OVS_OK;
+}
+
+int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_points) {
+    if (!c) return OVS_ERR_ARG;
+    size_t need = 0;
+    if (ovs_workspace_size(c, max_points, &need) != OVS_OK) return fail(c, OVS_ERR_ARG, "bad max_points");
+    if (!dptr) return fail(c, OVS_ERR_ARG, "workspace pointer is NULL");
+    if ((uintptr_t)dptr % kAlign) return fail(c, OVS_ERR_ARG, "workspace must be 256-byte aligned");
+    if (bytes < need)
+        return fail(c, OVS_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu for %lld points", bytes, need,
+                    (long long)max_points);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    char* base = (char*)dptr;
+    size_t off = 0;
+    c->d_grids = (GridDev*)(base + off);
+    off = align_up(off + sizeof(GridDev) * OVS_MAX_GRIDS);
+    c->d_counters = (unsigned long long*)(base + off);
+    off = align_up(off + sizeof(unsigned long long) * kNumCounters);
+    c->d_err = (int32_t*)(base + off);
+    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));
+    off = align_up(off + 2 * sizeof(int32_t));
+    c->d_queue = (SlowEntry*)(base + off);
+    c->ws = dptr;
+    c->ws_bytes = bytes;
+    c->max_points = max_points;
+    OVS_CUDA(c, cudaMemsetAsync(dptr, 0, off, c->stream));
+    if (c->ngrids)
+        OVS_CUDA(c, cudaMemcpyAsync(c->d_grids, c->grids, sizeof(GridDev) * c->ngrids, cudaMemcpyHostToDevice,
+                                    c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return OVS_OK;
+}
+
+int ovs_grid_workspace_size(const ovs_grid_desc* d, size_t* bytes) {
+    if (!bytes) return OVS_ERR_ARG;
+    int rc = check_desc(nullptr, d);
+    if (rc != OVS_OK) return rc;
+    *bytes = grid_layout(*d).total;
+    return OVS_OK;
+}
+
+int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes, int32_t* grid_id) {
+    if (!c) return OVS_ERR_ARG;
+    int rc = check_desc(c, d);
+    if (rc != OVS_OK) return rc;
+    if (!grid_id) return fail(c, OVS_ERR_ARG, "grid_id is NULL");
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "attach the context workspace before creating grids");
+    if (c->ngrids >= OVS_MAX_GRIDS) return fail(c, OVS_ERR_STATE, "at most %d grids", OVS_MAX_GRIDS);
+    GridLayout L = grid_layout(*d);
+    if (!dws) return fail(c, OVS_ERR_ARG, "grid workspace is NULL");
+    if ((uintptr_t)dws % kAlign) return fail(c, OVS_ERR_ARG, "grid workspace must be 256-byte aligned");
+    if (bytes < L.total) return fail(c, OVS_ERR_WORKSPACE, "grid workspace has %zu bytes, needs %zu", bytes, L.total);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    char* base = (char*)dws;
+    GridDev g;
+    memset(&g, 0, sizeof g);
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = d->n[a];
+        g.per[a] = d->periodic[a];
+        g.C[a] = (int32_t)cells_axis(*d, a);
+    }
+    g.role = d->role;
+    g.ncells = L.ncells;
+    g.nnodes = L.nnodes;
+    g.x = d->x;
+    g.y = d->y;
+    g.z = d->z;
+    g.rec = (const CellRec*)(base + L.rec);
+    g.bin_start = (const int32_t*)(base + L.bin_start);
+    g.bin_cells = (const int32_t*)(base + L.bin_cells);
+    g.bin_rep = (const int32_t*)(base + L.bin_rep);
+    g.hint = (uint32_t*)(base + L.hint);
+    g.mlp = nullptr;
+    double* out9 = (double*)(base + L.out9);
+    int nblk = (int)std::min<int64_t>(kReduceBlocks, (L.ncells + 255) / 256);
+    OVS_CUDA(c, launch_build_records(g, (CellRec*)(base + L.rec), (double*)(base + L.partials), nblk, out9,
+                                     c->stream));
+    double h9[9];
+    OVS_CUDA(c, cudaMemcpyAsync(h9, out9, sizeof h9, cudaMemcpyDeviceToHost, c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    double ext_max = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(h9[a]) || !isfinite(h9[3 + a]))
+            return fail(c, OVS_ERR_ARG, "grid coordinates are not finite");
+        ext_max = std::max(ext_max, h9[3 + a] - h9[a]);
+    }
+    double pad = 4e-6 * ext_max + 1e-300;
+    double ext[3], mean[3];
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = h9[a] - pad;
+        g.hi[a] = h9[3 + a] + pad;
+        ext[a] = g.hi[a] - g.lo[a];
+        mean[a] = std::max(h9[6 + a] / (double)L.ncells, 1e-12 * ext_max + 1e-300);
+    }
+    // bins about two mean cell extents wide, at most one bin per cell
+    double scale = 2.0;
+    int64_t nreg = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        int64_t nb_tot = 1;
+        for (int a = 0; a < 3; ++a) {
+            double nb = ceil(ext[a] / (scale * mean[a]));
+            g.nb[a] = (int32_t)std::min(4096.0, std::max(1.0, nb));
+            nb_tot *= g.nb[a];
+        }
+        if (nb_tot > L.nbins_max) {
+            scale *= 1.26;
+            continue;
+        }
+        for (int a = 0; a < 3; ++a) g.inv_w[a] = (double)g.nb[a] / ext[a];
+        uint32_t* counts = (uint32_t*)(base + L.bin_count);
+        int32_t* start = (int32_t*)(base + L.bin_start);
+        OVS_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nb_tot * 4, c->stream));
+        OVS_CUDA(c, launch_bin_count(g, counts, c->stream));
+        OVS_CUDA(c, launch_scan(counts, start, nb_tot, (uint32_t*)(base + L.scan), c->stream));
+        int32_t tot = 0;
+        OVS_CUDA(c, cudaMemcpyAsync(&tot, start + nb_tot, 4, cudaMemcpyDeviceToHost, c->stream));
+        OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (tot < 0 || (int64_t)tot > L.reg_cap) {
+            scale *= 1.5;
+            continue;
+        }
+        nreg = tot;
+        OVS_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nb_tot * 4, c->stream));
+        OVS_CUDA(c, cudaMemsetAsync(base + L.bin_rep, 0x7F, (size_t)nb_tot * 4, c->stream));
+        OVS_CUDA(c, launch_bin_fill(g, start, counts, (int32_t*)(base + L.bin_cells), (int32_t*)(base + L.bin_rep),
+                                    c->stream));
+        // bins left at 0x7F7F7F7F (>= ncells) are empty; the lookup treats them so
+        c->gh[c->ngrids].nbins = nb_tot;
+        break;
+    }
+    if (nreg == 0 && L.ncells > 0) return fail(c, OVS_ERR_WORKSPACE, "control-cell lists exceed the workspace");
+    OVS_CUDA(c, cudaMemsetAsync(base + L.hint, 0xFF, (size_t)L.nnodes * 4, c->stream));
+    int id = c->ngrids;
+    c->grids[id] = g;
+    c->gh[id].desc = *d;
+    c->gh[id].ws = dws;
+    c->gh[id].ws_bytes = bytes;
+    c->gh[id].nreg = nreg;
+    identity_motion(c->motion[id]);
+    OVS_CUDA(c, cudaMemcpyAsync(c->d_grids + id, &c->grids[id], sizeof(GridDev), cudaMemcpyHostToDevice, c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    OVS_CUDA(c, cudaGetLastError());
+    c->ngrids = id + 1;
+    *grid_id = id;
+    return OVS_OK;
+}
+
+int ovs_set_motion(ovs_ctx* c, int32_t gid, const double R[9], const double cc[3], const double V[3],
+                   const double w[3]) {
+    if (!c) return OVS_ERR_ARG;
+    if (gid < 0 || gid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", gid);
+    if (!R || !cc || !V || !w) return fail(c, OVS_ERR_ARG, "motion array is NULL");
+    for (int q = 0; q < 9; ++q)
+        if (!isfinite(R[q])) return fail(c, OVS_ERR_ARG, "R is not finite");
+    for (int q = 0; q < 3; ++q)
+        if (!isfinite(cc[q]) || !isfinite(V[q]) || !isfinite(w[q])) return fail(c, OVS_ERR_ARG, "c/V/omega not finite");
+    // orthogonality and orientation
+    double err = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += R[3 * k + a] * R[3 * k + b];
+            err = std::max(err, fabs(s - (a == b ? 1.0 : 0.0)));
+        }
+    double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                 R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (err > 1e-12 || det < 0) return fail(c, OVS_ERR_ARG, "R is not a rotation (|R^T R - I| = %g, det %g)", err, det);
+    MotionDev& m = c->motion[gid];
+    memcpy(m.R, R, sizeof m.R);
+    memcpy(m.c, cc, sizeof m.c);
+    memcpy(m.V, V, sizeof m.V);
+    memcpy(m.w, w, sizeof m.w);
+    bool id = R[0] == 1 && R[4] == 1 && R[8] == 1 && R[1] == 0 && R[2] == 0 && R[3] == 0 && R[5] == 0 && R[6] == 0 &&
+              R[7] == 0;
+    for (int q = 0; q < 3; ++q) id = id && cc[q] == 0 && V[q] == 0 && w[q] == 0;
+    m.identity = id ? 1 : 0;
+    return OVS_OK;
+}
+
+int ovs_set_options(ovs_ctx* c, const ovs_options* o) {
+    if (!c) return OVS_ERR_ARG;
+    if (!o) return fail(c, OVS_ERR_ARG, "options is NULL");
+    if (o->velocity_mode < OVS_VEL_RELATIVE || o->velocity_mode > OVS_VEL_NONE)
+        return fail(c, OVS_ERR_ARG, "velocity_mode %d", o->velocity_mode);
+    if (o->guess < OVS_GUESS_HINT || o->guess > OVS_GUESS_MLP) return fail(c, OVS_ERR_ARG, "guess %d", o->guess);
+    if (o->max_walk < 1 || o->max_walk > 1024) return fail(c, OVS_ERR_ARG, "max_walk %d (1..1024)", o->max_walk);
+    c->opts = *o;
+    return OVS_OK;
+}
+
+int ovs_get_options(const ovs_ctx* c, ovs_options* o) {
+    if (!c || !o) return OVS_ERR_ARG;
+    *o = c->opts;
+    return OVS_OK;
+}
+
+int ovs_assemble(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out) {
+    if (!c) return OVS_ERR_ARG;
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "no workspace attached");
+    int64_t total = 0;
+    int rc = check_sets(c, sets, nsets, &total);
+    if (rc != OVS_OK) return rc;
+    if (!out) return fail(c, OVS_ERR_ARG, "donors output is NULL");
+    if (out->n < total) return fail(c, OVS_ERR_ARG, "donors capacity %lld < %lld points", (long long)out->n, (long long)total);
+    if (total == 0) return OVS_OK;
+    if (!out->grid || !out->cell || !out->xi || !out->status) return fail(c, OVS_ERR_ARG, "donors array is NULL");
+    if (out->xi_dtype != OVS_F32 && out->xi_dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "xi_dtype");
+    if (out->n != total)
+        return fail(c, OVS_ERR_ARG, "donors.n (%lld) must equal the number of points (%lld): xi is SoA over n",
+                    (long long)out->n, (long long)total);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    AsmParams* P = new (std::nothrow) AsmParams();
+    if (!P) return fail(c, OVS_ERR_ARG, "host allocation failed");
+    P->nsets = nsets;
+    P->xi_f64 = out->xi_dtype == OVS_F64;
+    P->max_walk = c->opts.max_walk;
+    P->guess = c->opts.guess;
+    P->stats = c->opts.collect_stats;
+    P->total = total;
+    P->queue_cap = c->max_points;
+    P->out_grid = out->grid;
+    P->out_cell = out->cell;
+    P->out_xi = out->xi;
+    P->out_status = out->status;
+    P->queue = c->d_queue;
+    P->queue_count = c->d_qcount;
+    P->counters = c->d_counters;
+    P->err = c->d_err;
+    fill_sets(sets, nsets, P->s);
+    memcpy(P->m, c->motion, sizeof P->m);
+    cudaError_t e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr);
+    delete P;
+    if (e != cudaSuccess) return cuda_fail(c, e, "assemble launch");
+    return OVS_OK;
+}
+
+int ovs_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* in,
+                    const ovs_fields* fields, int32_t nfields, const ovs_fields_out* out) {
+    if (!c) return OVS_ERR_ARG;
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "no workspace attached");
+    int64_t total = 0;
+    int rc = check_sets(c, sets, nsets, &total);
+    if (rc != OVS_OK) return rc;
+    if (!in || !out) return fail(c, OVS_ERR_ARG, "donors or output is NULL");
+    if (in->n != total) return fail(c, OVS_ERR_ARG, "donors.n (%lld) != points (%lld)", (long long)in->n, (long long)total);
+    if (total == 0) return OVS_OK;
+    if (!fields || nfields != c->ngrids) return fail(c, OVS_ERR_ARG, "fields must have one entry per grid (%d)", c->ngrids);
+    if (out->dtype != OVS_F32 && out->dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "output dtype");
+    if (!out->u || !out->v || !out->w || !out->p) return fail(c, OVS_ERR_ARG, "output array is NULL");
+    if (!in->grid || !in->cell || !in->xi || !in->status) return fail(c, OVS_ERR_ARG, "donors array is NULL");
+    // every possible donor of these sets must carry fields of the output dtype
+    for (int s = 0; s < nsets; ++s)
+        for (int d = 0; d < sets[s].n_donors; ++d) {
+            const ovs_fields& f = fields[sets[s].donors[d]];
+            if (!f.u || !f.v || !f.w || !f.p)
+                return fail(c, OVS_ERR_ARG, "donor grid %d has a NULL field", sets[s].donors[d]);
+            if (f.dtype != out->dtype)
+                return fail(c, OVS_ERR_ARG, "donor grid %d fields dtype %d != output dtype %d", sets[s].donors[d],
+                            f.dtype, out->dtype);
+        }
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    InterpParams* P = new (std::nothrow) InterpParams();
+    if (!P) return fail(c, OVS_ERR_ARG, "host allocation failed");
+    P->nsets = nsets;
+    P->xi_f64 = in->xi_dtype == OVS_F64;
+    P->mode = c->opts.velocity_mode;
+    P->f64 = out->dtype == OVS_F64;
+    P->ngrids = c->ngrids;
+    P->err = c->d_err;
+    P->total = total;
+    P->in_grid = in->grid;
+    P->in_cell = in->cell;
+    P->in_xi = in->xi;
+    P->in_status = in->status;
+    P->out[0] = out->u;
+    P->out[1] = out->v;
+    P->out[2] = out->w;
+    P->out[3] = out->p;
+    fill_sets(sets, nsets, P->s);
+    memcpy(P->m, c->motion, sizeof P->m);
+    for (int g = 0; g < c->ngrids; ++g) {
+        P->fields[g].f[0] = fields[g].u;
+        P->fields[g].f[1] = fields[g].v;
+        P->fields[g].f[2] = fields[g].w;
+        P->fields[g].f[3] = fields[g].p;
+    }
+    cudaError_t e = launch_interp(*P, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
+    delete P;
+    if (e != cudaSuccess) return cuda_fail(c, e, "interpolate launch");
+    return OVS_OK;
+}
+
+int ovs_sync(ovs_ctx* c) {
+    if (!c) return OVS_ERR_ARG;
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!c->ws) return OVS_OK;
+    int32_t err = 0;
+    OVS_CUDA(c, cudaMemcpy(&err, c->d_err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        OVS_CUDA(c, cudaMemset(c->d_err, 0, 4));
+        return fail(c, OVS_ERR_DEVICE, "device status word 0x%x%s%s%s", err,
+                    (err & kErrQueueOverflow) ? " (slow-path queue overflow)" : "",
+                    (err & kErrBadNode) ? " (node id out of range: points marked BADINPUT)" : "",
+                    (err & kErrBadCell) ? " (donor record unusable: outputs zeroed)" : "");
+    }
+    return OVS_OK;
+}
+
+int ovs_get_stats(ovs_ctx* c, ovs_stats* out, int reset) {
+    if (!c || !out) return OVS_ERR_ARG;
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "no workspace attached");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    unsigned long long h[kNumCounters];
+    OVS_CUDA(c, cudaMemcpyAsync(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    out->points = (int64_t)h[kCtrPoints];
+    out->walk_steps = (int64_t)h[kCtrWalk];
+    out->refined = (int64_t)h[kCtrRefined];
+    out->fallback = (int64_t)h[kCtrFallback];
+    out->guess_used = (int64_t)h[kCtrGuess];
+    if (reset) OVS_CUDA(c, cudaMemsetAsync(c->d_counters, 0, sizeof h, c->stream));
+    return OVS_OK;
+}
+
+int ovs_set_trace_events(ovs_ctx* c, void* const* ev, int32_t n) {
+    if (!c) return OVS_ERR_ARG;
+    if (n < 0 || n > 5) return fail(c, OVS_ERR_ARG, "n = %d (0..5)", n);
+    for (int q = 0; q < 5; ++q) c->trace[q] = (ev && q < n) ? (cudaEvent_t)ev[q] : nullptr;
+    c->tracing = ev && n > 0;
+    return OVS_OK;
+}
+
+int ovs_reset_hints(ovs_ctx* c) {
+    if (!c) return OVS_ERR_ARG;
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    for (int g = 0; g < c->ngrids; ++g)
+        OVS_CUDA(c, cudaMemsetAsync(c->grids[g].hint, 0xFF, (size_t)c->grids[g].nnodes * 4, c->stream));
+    return OVS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Boundary interpolation (Sec. 2.2.6): q = sum_a N_a(xi) q_a over the donor's 8 nodes for u, v, w, p,
+// then the frame velocity transform (Sec. 2.1 eq. "velocity": u_in = R u_rel + V + Omega x r, and
+// Sec. 2.3.1 eq. "velocity_non": rotation only).  One thread per point; node fields are the caller's SoA
+// arrays (FP32 or FP64), read with read-only loads.
+#include "ovs_internal.cuh"
+
+namespace ovs {
+
+namespace {
+
+constexpr int kInterpThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ void rot(const double R[9], const T a[3], T out[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) out[r] = (T)R[3 * r] * a[0] + (T)R[3 * r + 1] * a[1] + (T)R[3 * r + 2] * a[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void rotT(const double R[9], const T a[3], T out[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) out[r] = (T)R[r] * a[0] + (T)R[3 + r] * a[1] + (T)R[6 + r] * a[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void cross_add(const double w[3], const T r[3], T acc[3], T sign) {
+    acc[0] += sign * ((T)w[1] * r[2] - (T)w[2] * r[1]);
+    acc[1] += sign * ((T)w[2] * r[0] - (T)w[0] * r[2]);
+    acc[2] += sign * ((T)w[0] * r[1] - (T)w[1] * r[0]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kInterpThreads) k_interp(const __grid_constant__ InterpParams P,
+                                                           const GridDev* __restrict__ G) {
+    const int64_t t = blockIdx.x * (int64_t)kInterpThreads + threadIdx.x;
+    if (t >= P.total) return;
+    T* out[4] = {(T*)P.out[0], (T*)P.out[1], (T*)P.out[2], (T*)P.out[3]};
+    const uint8_t st = __ldg(P.in_status + t) & OVS_STATUS_MASK;
+    const int32_t gd = __ldg(P.in_grid + t);
+    if (st != OVS_STATUS_FOUND || gd < 0) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) out[f][t] = (T)0;
+        return;
+    }
+    const int32_t cell = __ldg(P.in_cell + t);
+    if (gd >= P.ngrids || cell < 0 || cell >= G[gd].ncells || !P.fields[gd].f[0] || !P.fields[gd].f[1] ||
+        !P.fields[gd].f[2] || !P.fields[gd].f[3]) {
+        // a donor record this call cannot use (not produced by ovs_assemble for these grids and fields)
+        atomicOr(P.err, kErrBadCell);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) out[f][t] = (T)0;
+        return;
+    }
+    T u, v, w;
+    if (P.xi_f64) {
+        const double* xi = (const double*)P.in_xi;
+        u = (T)__ldg(xi + t);
+        v = (T)__ldg(xi + P.total + t);
+        w = (T)__ldg(xi + 2 * P.total + t);
+    } else {
+        const float* xi = (const float*)P.in_xi;
+        u = (T)__ldg(xi + t);
+        v = (T)__ldg(xi + P.total + t);
+        w = (T)__ldg(xi + 2 * P.total + t);
+    }
+    const GridDev& g = G[gd];
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
+    T q[4] = {0, 0, 0, 0};
+    const T* f[4] = {(const T*)P.fields[gd].f[0], (const T*)P.fields[gd].f[1], (const T*)P.fields[gd].f[2],
+                     (const T*)P.fields[gd].f[3]};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        T wa = ((a & 1) ? u : (T)1 - u) * ((a & 2) ? v : (T)1 - v) * ((a & 4) ? w : (T)1 - w);
+        int64_t nd = corner_node(g, i, j, k, a);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] += wa * __ldg(f[c] + nd);
+    }
+    if (P.mode != OVS_VEL_NONE) {
+        const int si = find_set(P.s, P.nsets, t);
+        const SetDev& s = P.s[si];
+        const MotionDev& md = P.m[gd];
+        const MotionDev& mr = P.m[s.receiver];
+        T ud[3] = {q[0], q[1], q[2]}, uin[3];
+        if (P.mode == OVS_VEL_ABSOLUTE) {
+            if (!md.identity) rot(md.R, ud, uin);
+            else uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
+            if (!mr.identity) rotT(mr.R, uin, ud);
+            else ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+        } else {
+            const int32_t node = __ldg(s.node_ids + (t - s.begin));
+            const GridDev& gr = G[s.receiver];
+            if (node < 0 || node >= gr.nnodes) {
+                atomicOr(P.err, kErrBadNode);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) out[f][t] = (T)0;
+                return;
+            }
+            double3 xr = make_double3(__ldg(gr.x + node), __ldg(gr.y + node), __ldg(gr.z + node));
+            // r_r = x_in - c_r = R_r x_r; r_d = x_in - c_d = R_r x_r + (c_r - c_d)
+            T xrT[3] = {(T)xr.x, (T)xr.y, (T)xr.z};
+            T rr[3], rd[3];
+            if (mr.identity) {
+                rd[0] = (T)(xr.x - md.c[0]);
+                rd[1] = (T)(xr.y - md.c[1]);
+                rd[2] = (T)(xr.z - md.c[2]);
+                rr[0] = rr[1] = rr[2] = (T)0;
+            } else {
+                rot(mr.R, xrT, rr);
+                rd[0] = rr[0] + (T)(mr.c[0] - md.c[0]);
+                rd[1] = rr[1] + (T)(mr.c[1] - md.c[1]);
+                rd[2] = rr[2] + (T)(mr.c[2] - md.c[2]);
+            }
+            if (!md.identity) {
+                rot(md.R, ud, uin);
+                uin[0] += (T)md.V[0];
+                uin[1] += (T)md.V[1];
+                uin[2] += (T)md.V[2];
+                cross_add(md.w, rd, uin, (T)1);
+            } else {
+                uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
+            }
+            if (!mr.identity) {
+                uin[0] -= (T)mr.V[0];
+                uin[1] -= (T)mr.V[1];
+                uin[2] -= (T)mr.V[2];
+                cross_add(mr.w, rr, uin, (T)-1);
+                rotT(mr.R, uin, ud);
+            } else {
+                ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+            }
+        }
+        q[0] = ud[0];
+        q[1] = ud[1];
+        q[2] = ud[2];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c][t] = q[c];
+}
+
+}  // namespace
+
+cudaError_t launch_interp(const InterpParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev) {
+    int64_t blocks = (P.total + kInterpThreads - 1) / kInterpThreads;
+    if (ev && ev[0]) cudaEventRecord(ev[0], st);
+    if (P.f64) k_interp<double><<<(unsigned)blocks, kInterpThreads, 0, st>>>(P, dgrids);
+    else k_interp<float><<<(unsigned)blocks, kInterpThreads, 0, st>>>(P, dgrids);
+    if (ev && ev[1]) cudaEventRecord(ev[1], st);
+    return cudaGetLastError();
+}
+
+}  // namespace ovs

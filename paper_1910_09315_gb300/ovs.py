@@ -1,0 +1,375 @@
+"""Thin ctypes binding of libovs (include/ovs.h): the same entry points, argument marshalling only.
+
+Every computation of the assembly and interpolation path runs in libovs's CUDA kernels.  PyTorch is used
+only for device memory and streams.  There is no CPU fallback: if libovs.so is missing or no GPU is
+present, these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libovs.so")
+
+OVS_OK = 0
+OVS_ERR_ARG = -1
+OVS_ERR_STATE = -2
+OVS_ERR_WORKSPACE = -3
+OVS_ERR_CUDA = -4
+OVS_ERR_NO_DEVICE = -5
+OVS_ERR_DEVICE = -6
+
+OVS_STATUS_FOUND = 0
+OVS_STATUS_ORPHAN = 1
+OVS_STATUS_BADINPUT = 2
+OVS_STATUS_MASK = 0x0F
+OVS_STATUS_FALLBACK = 0x10
+OVS_STATUS_REFINED = 0x20
+
+OVS_F32 = 0
+OVS_F64 = 1
+
+OVS_MAX_GRIDS = 31
+OVS_MAX_SETS = 64
+OVS_MAX_DONORS = 8
+
+OVS_VEL_RELATIVE = 0
+OVS_VEL_ABSOLUTE = 1
+OVS_VEL_NONE = 2
+
+OVS_GUESS_HINT = 0
+OVS_GUESS_BINS = 1
+OVS_GUESS_MLP = 2
+
+EXPORTS = [
+    "ovs_ctx_create", "ovs_ctx_destroy", "ovs_last_error", "ovs_set_stream", "ovs_workspace_size",
+    "ovs_workspace_attach", "ovs_grid_workspace_size", "ovs_create_grid", "ovs_set_motion", "ovs_set_options",
+    "ovs_get_options", "ovs_assemble", "ovs_interpolate", "ovs_sync", "ovs_get_stats", "ovs_reset_hints",
+    "ovs_set_trace_events",
+]
+
+
+class ovs_grid_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("periodic", ctypes.c_int32 * 3), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("role", ctypes.c_int32)]
+
+
+class ovs_fringe_set(ctypes.Structure):
+    _fields_ = [("receiver", ctypes.c_int32), ("n_donors", ctypes.c_int32),
+                ("donors", ctypes.c_int32 * OVS_MAX_DONORS), ("n", ctypes.c_int64), ("node_ids", ctypes.c_void_p)]
+
+
+class ovs_donors(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("grid", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("xi", ctypes.c_void_p),
+                ("xi_dtype", ctypes.c_int32), ("status", ctypes.c_void_p)]
+
+
+class ovs_fields(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32)]
+
+
+class ovs_fields_out(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32)]
+
+
+class ovs_options(ctypes.Structure):
+    _fields_ = [("velocity_mode", ctypes.c_int32), ("guess", ctypes.c_int32), ("max_walk", ctypes.c_int32),
+                ("collect_stats", ctypes.c_int32)]
+
+
+class ovs_stats(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("refined", ctypes.c_int64),
+                ("fallback", ctypes.c_int64), ("guess_used", ctypes.c_int64)]
+
+
+class OvsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libovs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libovs.so (built by ``paper_1910_09315_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libovs.so not built ({p}); run paper_1910_09315_gb300/build.py")
+    L = ctypes.CDLL(p)
+    V, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "ovs_ctx_create": [ctypes.POINTER(V), ctypes.c_int, V],
+        "ovs_ctx_destroy": [V],
+        "ovs_last_error": [V],
+        "ovs_set_stream": [V, V],
+        "ovs_workspace_size": [V, I64, ctypes.POINTER(SZ)],
+        "ovs_workspace_attach": [V, V, SZ, I64],
+        "ovs_grid_workspace_size": [ctypes.POINTER(ovs_grid_desc), ctypes.POINTER(SZ)],
+        "ovs_create_grid": [V, ctypes.POINTER(ovs_grid_desc), V, SZ, ctypes.POINTER(I32)],
+        "ovs_set_motion": [V, I32, V, V, V, V],
+        "ovs_set_options": [V, ctypes.POINTER(ovs_options)],
+        "ovs_get_options": [V, ctypes.POINTER(ovs_options)],
+        "ovs_assemble": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors)],
+        "ovs_interpolate": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors),
+                            ctypes.POINTER(ovs_fields), I32, ctypes.POINTER(ovs_fields_out)],
+        "ovs_sync": [V],
+        "ovs_get_stats": [V, ctypes.POINTER(ovs_stats), ctypes.c_int],
+        "ovs_reset_hints": [V],
+        "ovs_set_trace_events": [V, ctypes.POINTER(V), I32],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "ovs_last_error" else ctypes.c_int
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(ctx, rc: int):
+    if rc != OVS_OK:
+        msg = load().ovs_last_error(ctx).decode() if ctx else ""
+        raise OvsError(rc, msg)
+
+
+# ------------------------------------------------------------------ entry points (same names as the C ABI)
+def ovs_ctx_create(device: int = 0, stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    rc = load().ovs_ctx_create(ctypes.byref(ctx), int(device), ctypes.c_void_p(_stream_handle(stream)))
+    if rc != OVS_OK:
+        raise OvsError(rc, "ovs_ctx_create failed (no usable CUDA device?)")
+    return ctx
+
+
+def ovs_ctx_destroy(ctx):
+    _check(ctx, load().ovs_ctx_destroy(ctx))
+
+
+def ovs_last_error(ctx) -> str:
+    return load().ovs_last_error(ctx).decode()
+
+
+def ovs_set_stream(ctx, stream):
+    _check(ctx, load().ovs_set_stream(ctx, ctypes.c_void_p(_stream_handle(stream))))
+
+
+def ovs_workspace_size(ctx, max_points: int) -> int:
+    b = ctypes.c_size_t()
+    _check(ctx, load().ovs_workspace_size(ctx, int(max_points), ctypes.byref(b)))
+    return b.value
+
+
+def ovs_workspace_attach(ctx, dptr: int, nbytes: int, max_points: int):
+    _check(ctx, load().ovs_workspace_attach(ctx, ctypes.c_void_p(dptr), nbytes, int(max_points)))
+
+
+def ovs_grid_workspace_size(desc: ovs_grid_desc) -> int:
+    b = ctypes.c_size_t()
+    rc = load().ovs_grid_workspace_size(ctypes.byref(desc), ctypes.byref(b))
+    if rc != OVS_OK:
+        raise OvsError(rc, "invalid grid descriptor")
+    return b.value
+
+
+def ovs_create_grid(ctx, desc: ovs_grid_desc, dptr: int, nbytes: int) -> int:
+    gid = ctypes.c_int32()
+    _check(ctx, load().ovs_create_grid(ctx, ctypes.byref(desc), ctypes.c_void_p(dptr), nbytes, ctypes.byref(gid)))
+    return gid.value
+
+
+def ovs_set_motion(ctx, grid_id: int, R, c, V, omega):
+    arrs = [(ctypes.c_double * n)(*[float(x) for x in a]) for a, n in ((_flat(R), 9), (_flat(c), 3), (_flat(V), 3),
+                                                                       (_flat(omega), 3))]
+    _check(ctx, load().ovs_set_motion(ctx, int(grid_id), *[ctypes.cast(a, ctypes.c_void_p) for a in arrs]))
+
+
+def ovs_set_options(ctx, opts: ovs_options):
+    _check(ctx, load().ovs_set_options(ctx, ctypes.byref(opts)))
+
+
+def ovs_get_options(ctx) -> ovs_options:
+    o = ovs_options()
+    _check(ctx, load().ovs_get_options(ctx, ctypes.byref(o)))
+    return o
+
+
+def ovs_assemble(ctx, sets, nsets: int, donors: ovs_donors):
+    _check(ctx, load().ovs_assemble(ctx, sets, int(nsets), ctypes.byref(donors)))
+
+
+def ovs_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
+    _check(ctx, load().ovs_interpolate(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
+                                       ctypes.byref(out)))
+
+
+def ovs_sync(ctx):
+    _check(ctx, load().ovs_sync(ctx))
+
+
+def ovs_get_stats(ctx, reset: bool = False) -> dict:
+    s = ovs_stats()
+    _check(ctx, load().ovs_get_stats(ctx, ctypes.byref(s), int(bool(reset))))
+    return {k: getattr(s, k) for k, _ in ovs_stats._fields_}
+
+
+def ovs_reset_hints(ctx):
+    _check(ctx, load().ovs_reset_hints(ctx))
+
+
+def ovs_set_trace_events(ctx, events):
+    """events: sequence of torch.cuda.Event (or None) -> recorded at the points include/ovs.h lists."""
+    n = len(events)
+    arr = (ctypes.c_void_p * max(1, n))()
+    for i, e in enumerate(events):
+        arr[i] = None if e is None else int(e.cuda_event)
+    _check(ctx, load().ovs_set_trace_events(ctx, arr, n))
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _flat(a) -> List[float]:
+    try:
+        import numpy as np
+
+        return list(np.asarray(a, dtype=float).reshape(-1))
+    except Exception:  # pragma: no cover
+        return [float(x) for x in a]
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_sets(sets: Sequence) -> "ctypes.Array":
+    """sets: sequence of (receiver, node_ids torch int32 cuda tensor, donors list)."""
+    arr = (ovs_fringe_set * max(1, len(sets)))()
+    for i, (rec, ids, donors) in enumerate(sets):
+        arr[i].receiver = int(rec)
+        arr[i].n_donors = len(donors)
+        for j, d in enumerate(donors):
+            arr[i].donors[j] = int(d)
+        arr[i].n = int(ids.numel())
+        arr[i].node_ids = ids.data_ptr() if ids.numel() else None
+    return arr
+
+
+class Context:
+    """Owns an ovs context and the device workspaces it needs (allocated as torch tensors)."""
+
+    def __init__(self, device: int = 0, stream=None, max_points: int = 1 << 20):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libovs needs a CUDA device; there is no CPU fallback")
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = ovs_ctx_create(device, self.stream)
+        self.max_points = int(max_points)
+        nbytes = ovs_workspace_size(self.ctx, self.max_points)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        ovs_workspace_attach(self.ctx, _aligned(self._ws), nbytes, self.max_points)
+        self.grids = []  # (desc, coords tensors, workspace)
+
+    def close(self):
+        if self.ctx:
+            ovs_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_grid(self, x, y, z, dims, periodic=(False, False, False), role: int = 1) -> int:
+        t = self.torch
+        xs = [a if isinstance(a, t.Tensor) else t.as_tensor(a) for a in (x, y, z)]
+        xs = [a.to(device=self.device, dtype=t.float64).contiguous() for a in xs]
+        d = ovs_grid_desc()
+        for a in range(3):
+            d.n[a] = int(dims[a])
+            d.periodic[a] = int(bool(periodic[a]))
+        d.x, d.y, d.z = xs[0].data_ptr(), xs[1].data_ptr(), xs[2].data_ptr()
+        d.role = int(role)
+        nbytes = ovs_grid_workspace_size(d)
+        ws = t.empty(nbytes + 256, dtype=t.uint8, device=self.device)
+        gid = ovs_create_grid(self.ctx, d, _aligned(ws), nbytes)
+        self.grids.append((d, xs, ws))
+        return gid
+
+    def set_motion(self, gid: int, R, c, V, omega):
+        ovs_set_motion(self.ctx, gid, R, c, V, omega)
+
+    def set_options(self, **kw):
+        o = ovs_get_options(self.ctx)
+        for k, v in kw.items():
+            setattr(o, k, int(v))
+        ovs_set_options(self.ctx, o)
+
+    def alloc_donors(self, n: int, xi_dtype: int = OVS_F32):
+        t = self.torch
+        dt = t.float64 if xi_dtype == OVS_F64 else t.float32
+        return {"grid": t.empty(n, dtype=t.int32, device=self.device),
+                "cell": t.empty(n, dtype=t.int32, device=self.device),
+                "xi": t.empty(3 * n, dtype=dt, device=self.device),
+                "status": t.empty(n, dtype=t.uint8, device=self.device), "xi_dtype": xi_dtype, "n": n}
+
+    @staticmethod
+    def donors_struct(d) -> ovs_donors:
+        s = ovs_donors()
+        s.n = d["n"]
+        s.grid, s.cell, s.xi, s.status = (d["grid"].data_ptr(), d["cell"].data_ptr(), d["xi"].data_ptr(),
+                                          d["status"].data_ptr())
+        s.xi_dtype = d["xi_dtype"]
+        return s
+
+    def assemble(self, sets, donors=None, xi_dtype: int = OVS_F32):
+        n = sum(int(s[1].numel()) for s in sets)
+        if donors is None:
+            donors = self.alloc_donors(n, xi_dtype)
+        arr = make_sets(sets)
+        ovs_assemble(self.ctx, arr, len(sets), self.donors_struct(donors))
+        return donors
+
+    def interpolate(self, sets, donors, fields, out=None):
+        """fields: list indexed by grid id of (u, v, w, p) cuda tensors (or None)."""
+        t = self.torch
+        n = donors["n"]
+        dtype = None
+        farr = (ovs_fields * len(self.grids))()
+        for g, f in enumerate(fields):
+            if f is None:
+                continue
+            farr[g].u, farr[g].v, farr[g].w, farr[g].p = (a.data_ptr() for a in f)
+            farr[g].dtype = OVS_F64 if f[0].dtype == t.float64 else OVS_F32
+            dtype = f[0].dtype
+        if out is None:
+            out = [t.empty(n, dtype=dtype, device=self.device) for _ in range(4)]
+        o = ovs_fields_out()
+        o.u, o.v, o.w, o.p = (a.data_ptr() for a in out)
+        o.dtype = OVS_F64 if out[0].dtype == t.float64 else OVS_F32
+        ovs_interpolate(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr, len(self.grids), o)
+        return out
+
+    def sync(self):
+        ovs_sync(self.ctx)
+
+    def stats(self, reset=False):
+        return ovs_get_stats(self.ctx, reset)
+
+
+def _aligned(t) -> int:
+    p = t.data_ptr()
+    return (p + 255) // 256 * 256
