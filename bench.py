@@ -222,6 +222,8 @@ def run_ovs(args, rank, world, local):
         one_step(s, dev_sets[s])
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for e in ev:
+        e.record(stream)  # torch creates the CUDA event on its first record
     ovs.ovs_set_trace_events(ctx.ctx, ev)
     if world > 1:
         torch.distributed.barrier()

@@ -199,9 +199,9 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const __grid_constant_
     }
 }
 
-// lowest-id FP64 decision among the cells sharing the near face / edge / corner of `cell`
-__device__ bool neighbourhood64(const GridDev& g, double3 p, int64_t cell, const float xi32[3], int64_t& out_cell,
-                                double& u, double& v, double& w) {
+// Candidate cells sharing the near face / edge / corner of `cell` (FP32 local coordinates within kNearFace
+// of a face), in ascending linear id.  Returns their count (<= 8) and the offsets to shift the FP32 guess.
+__device__ int near_candidates(const GridDev& g, int64_t cell, const float xi32[3], int64_t ids[8], int off[8][3]) {
     int ijk[3];
     cell_ijk(g, cell, ijk[0], ijk[1], ijk[2]);
     int lo[3], hi[3];
@@ -210,8 +210,6 @@ __device__ bool neighbourhood64(const GridDev& g, double3 p, int64_t cell, const
         lo[m] = xi32[m] < kNearFace ? -1 : 0;
         hi[m] = xi32[m] > 1.f - kNearFace ? 1 : 0;
     }
-    int64_t ids[8];
-    int off[8][3];
     int nc = 0;
     for (int oz = lo[2]; oz <= hi[2]; ++oz)
         for (int oy = lo[1]; oy <= hi[1]; ++oy)
@@ -229,7 +227,6 @@ __device__ bool neighbourhood64(const GridDev& g, double3 p, int64_t cell, const
                 }
                 if (!ok) continue;
                 int64_t id = cell_id(g, q[0], q[1], q[2]);
-                // insertion sort by id
                 int pos = nc++;
                 while (pos > 0 && ids[pos - 1] > id) {
                     ids[pos] = ids[pos - 1];
@@ -243,33 +240,88 @@ __device__ bool neighbourhood64(const GridDev& g, double3 p, int64_t cell, const
                 off[pos][1] = o[1];
                 off[pos][2] = o[2];
             }
-    for (int q = 0; q < nc; ++q) {
-        double a = (double)xi32[0] - off[q][0], b = (double)xi32[1] - off[q][1], c = (double)xi32[2] - off[q][2];
-        if (newton64_contains(g, ids[q], p, a, b, c)) {
-            out_cell = ids[q];
-            u = a;
-            v = b;
-            w = c;
-            return true;
-        }
-    }
-    return false;
+    return nc;
 }
 
-// exhaustive search of the point's control cell (Sec. 2.2.5 brute-force fallback), FP64 predicate
-__device__ bool exhaustive64(const GridDev& g, double3 p, int64_t bin, int64_t& out_cell, double& u, double& v,
-                             double& w) {
-    int64_t best = INT64_MAX;
+// Warp-cooperative lowest-id FP64 decision over the near candidates: lane q tests candidate q; the lowest
+// lane (= lowest id) whose cell holds the point wins.  All 32 lanes must call this.
+__device__ bool neighbourhood64_warp(const GridDev& g, double3 p, int64_t cell, const float xi32[3],
+                                     int64_t& out_cell, double& u, double& v, double& w) {
+    int64_t ids[8];
+    int off[8][3];
+    int nc = near_candidates(g, cell, xi32, ids, off);
+    const int lane = (int)lane_id();
+    bool hit = false;
+    double a = 0, b = 0, c = 0;
+    int64_t mine = -1;
+    if (lane < nc) {
+        // select this lane's candidate without dynamic register indexing
+        int o0 = 0, o1 = 0, o2 = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q == lane) {
+                mine = ids[q];
+                o0 = off[q][0];
+                o1 = off[q][1];
+                o2 = off[q][2];
+            }
+        a = (double)xi32[0] - o0;
+        b = (double)xi32[1] - o1;
+        c = (double)xi32[2] - o2;
+        hit = newton64_contains(g, mine, p, a, b, c);
+    }
+    unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (!m) return false;
+    int src = __ffs(m) - 1;
+    out_cell = __shfl_sync(0xffffffffu, mine, src);
+    u = __shfl_sync(0xffffffffu, a, src);
+    v = __shfl_sync(0xffffffffu, b, src);
+    w = __shfl_sync(0xffffffffu, c, src);
+    return true;
+}
+
+// Warp-cooperative exhaustive search of the point's control cell (Sec. 2.2.5 brute-force fallback): lanes
+// split the registered cells; a cell is rejected by its padded box (FP32, relative to its corner 0) or by a
+// converged FP32 Newton that lands clearly outside; the rest get the FP64 predicate.  Lowest id wins.
+__device__ bool exhaustive64_warp(const GridDev& g, double3 p, int64_t bin, int64_t& out_cell, double& u, double& v,
+                                  double& w) {
+    const int lane = (int)lane_id();
+    uint32_t best = 0xFFFFFFFFu;
     double bu = 0, bv = 0, bw = 0;
     int32_t r0 = __ldg(g.bin_start + bin), r1 = __ldg(g.bin_start + bin + 1);
-    for (int32_t r = r0; r < r1; ++r) {
-        int64_t c = __ldg(g.bin_cells + r);
+    for (int32_t r = r0 + lane; r < r1; r += 32) {
+        uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
         if (c >= best) continue;
         CellRec rec;
         load_rec(g.rec, c, rec);
-        double lo[3], hi[3];
-        rec_box(rec, lo, hi);
-        if (!(p.x >= lo[0] && p.x <= hi[0] && p.y >= lo[1] && p.y <= hi[1] && p.z >= lo[2] && p.z <= hi[2]))
+        float dx = (float)(p.x - rec.x0[0]), dy = (float)(p.y - rec.x0[1]), dz = (float)(p.z - rec.x0[2]);
+        float d[3] = {dx, dy, dz};
+        bool inbox = true;
+        float diag2 = 0.f;
+        float mn[3], mx[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float a1 = rec.a[k], a2 = rec.a[3 + k], a3 = rec.a[6 + k], a4 = rec.a[9 + k], a5 = rec.a[12 + k],
+                  a6 = rec.a[15 + k], a7 = rec.a[18 + k];
+            float e[8] = {0.f, a1, a2, a1 + a2 + a4, a3, a1 + a3 + a6, a2 + a3 + a5,
+                          a1 + a2 + a3 + a4 + a5 + a6 + a7};
+            mn[k] = e[0];
+            mx[k] = e[0];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+                mn[k] = fminf(mn[k], e[q]);
+                mx[k] = fmaxf(mx[k], e[q]);
+            }
+            diag2 += (mx[k] - mn[k]) * (mx[k] - mn[k]);
+        }
+        float pad = 4e-6f * sqrtf(diag2) + 1e-30f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) inbox = inbox && d[k] >= mn[k] - pad && d[k] <= mx[k] + pad;
+        if (!inbox) continue;
+        float fu = 0.5f, fv = 0.5f, fw = 0.5f;
+        bool conv = newton32(rec, dx, dy, dz, fu, fv, fw);
+        const float far = 0.05f;
+        if (conv && (fu < -far || fu > 1.f + far || fv < -far || fv > 1.f + far || fw < -far || fw > 1.f + far))
             continue;
         double a = 0.5, b = 0.5, cc = 0.5;
         if (newton64_contains(g, c, p, a, b, cc)) {
@@ -279,20 +331,29 @@ __device__ bool exhaustive64(const GridDev& g, double3 p, int64_t bin, int64_t& 
             bw = cc;
         }
     }
-    if (best == INT64_MAX) return false;
-    out_cell = best;
-    u = bu;
-    v = bv;
-    w = bw;
+    uint32_t wbest = __reduce_min_sync(0xffffffffu, best);
+    if (wbest == 0xFFFFFFFFu) return false;
+    unsigned m = __ballot_sync(0xffffffffu, best == wbest);
+    int src = __ffs(m) - 1;
+    out_cell = wbest;
+    u = __shfl_sync(0xffffffffu, bu, src);
+    v = __shfl_sync(0xffffffffu, bv, src);
+    w = __shfl_sync(0xffffffffu, bw, src);
     return true;
 }
 
-__global__ void __launch_bounds__(128) k_assemble_slow(const __grid_constant__ AsmParams P,
-                                                       const GridDev* __restrict__ G) {
+constexpr int kSlowThreads = 256;
+
+// One warp per queued point.
+__global__ void __launch_bounds__(kSlowThreads) k_assemble_slow(const __grid_constant__ AsmParams P,
+                                                                const GridDev* __restrict__ G) {
     uint32_t count = *P.queue_count;
     if (count > P.queue_cap) count = (uint32_t)P.queue_cap;
+    const int lane = (int)lane_id();
+    const uint32_t warp = (blockIdx.x * kSlowThreads + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kSlowThreads) >> 5;
     unsigned refined = 0, fallback = 0;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    for (uint32_t q = warp; q < count; q += nwarps) {
         SlowEntry e = P.queue[q];
         const int64_t t = e.t;
         const int si = find_set(P.s, P.nsets, t);
@@ -308,26 +369,28 @@ __global__ void __launch_bounds__(128) k_assemble_slow(const __grid_constant__ A
             double3 p = to_body(P.m[gd], xin);
             int64_t b = point_bin(g, p);
             if (b < 0) continue;
-            int64_t cell;
-            double u, v, w;
+            int64_t cell = -1;
+            double u = 0, v = 0, w = 0;
             uint8_t st = OVS_STATUS_FOUND | OVS_STATUS_REFINED;
             bool ok = false;
-            if (di == e.di && e.cell >= 0) ok = neighbourhood64(g, p, e.cell, e.xi, cell, u, v, w);
+            if (di == e.di && e.cell >= 0) ok = neighbourhood64_warp(g, p, e.cell, e.xi, cell, u, v, w);
             if (!ok) {
-                ok = exhaustive64(g, p, b, cell, u, v, w);
+                ok = exhaustive64_warp(g, p, b, cell, u, v, w);
                 st |= OVS_STATUS_FALLBACK;
                 ++fallback;
             }
             if (ok) {
-                write_donor(P, t, gd, cell, u, v, w, st);
-                gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
+                if (lane == 0) {
+                    write_donor(P, t, gd, cell, u, v, w, st);
+                    gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
+                }
                 done = true;
                 ++refined;
             }
         }
-        if (!done) write_none(P, t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+        if (!done && lane == 0) write_none(P, t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
     }
-    if (P.stats) {
+    if (P.stats && lane == 0) {
         if (refined) atomicAdd(P.counters + kCtrRefined, (unsigned long long)refined);
         if (fallback) atomicAdd(P.counters + kCtrFallback, (unsigned long long)fallback);
     }
@@ -344,7 +407,7 @@ cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStrea
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    k_assemble_slow<<<152 * 4, 128, 0, st>>>(P, dgrids);
+    k_assemble_slow<<<152 * 4, kSlowThreads, 0, st>>>(P, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

@@ -225,10 +225,13 @@ def ovs_reset_hints(ctx):
 
 
 def ovs_set_trace_events(ctx, events):
-    """events: sequence of torch.cuda.Event (or None) -> recorded at the points include/ovs.h lists."""
+    """events: sequence of torch.cuda.Event (or None) -> recorded at the points include/ovs.h lists.  A torch
+    event exists only after its first record(), so record each once before passing it."""
     n = len(events)
     arr = (ctypes.c_void_p * max(1, n))()
     for i, e in enumerate(events):
+        if e is not None and not int(e.cuda_event):
+            raise ValueError("torch.cuda.Event has no CUDA event yet: record() it once first")
         arr[i] = None if e is None else int(e.cuda_event)
     _check(ctx, load().ovs_set_trace_events(ctx, arr, n))
 

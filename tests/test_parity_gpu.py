@@ -111,7 +111,8 @@ def test_cfg1_cold_equals_warm(torch_cuda):
     # deterministic: the same call twice gives bit-identical outputs
     _, dc2, _ = scene.step(m, fsets, interpolate=False)
     again = GpuScene.to_numpy(dc2)
-    assert np.array_equal(cold["xi"], again["xi"]) and np.array_equal(cold["cell"], again["cell"])
+    assert np.array_equal(cold["xi"], again["xi"], equal_nan=True)  # orphans carry NaN local coordinates
+    assert np.array_equal(cold["cell"], again["cell"])
 
 
 def test_cfg2_full_size_sampled(torch_cuda):
@@ -177,12 +178,12 @@ def test_ragged_empty_sets_orphans_priority(torch_cuda):
     sc = mini_scenario([g0, g1, g2], sets, motions)
     scene, _, n = run_and_compare(sc, 0, ovs.OVS_F64, label="ragged")
     st = GpuScene.to_numpy(scene.ctx.assemble(scene.upload_sets(sets), xi_dtype=ovs.OVS_F64))["status"] & 15
-    assert (st == ovs.OVS_STATUS_ORPHAN).sum() > 50 and (st == ovs.OVS_STATUS_FOUND).sum() > 500
+    assert (st == ovs.OVS_STATUS_ORPHAN).sum() > 50 and (st == ovs.OVS_STATUS_FOUND).sum() > 200
 
 
 def test_nonfinite_inputs_are_badinput(torch_cuda):
     donor = cart("d", 5, 0.0, 1.0, role=0)
-    rec = cart("r", 3, 0.5e308, 1.7e308, role=1)  # finite nodes whose inertial image overflows
+    rec = cart("r", 3, 1.0e308, 1.2e308, role=1)  # finite nodes whose inertial image overflows
     motions = [gen.Motion.identity(), gen.Motion(np.eye(3), np.array([1e308, 0, 0]), np.zeros(3), np.zeros(3))]
     sc = mini_scenario([donor, rec], [gen.FringeSet(1, np.arange(27, dtype=np.int32), [0])], motions)
     scene = GpuScene(sc, max_points=64, xi_dtype=ovs.OVS_F64)
