@@ -201,6 +201,32 @@ int ovs_reset_hints(ovs_ctx* ctx);
  * n = 0 (or ev = NULL) switches tracing off.  The events must outlive their use. */
 int ovs_set_trace_events(ovs_ctx* ctx, void* const* ev, int32_t n);
 
+/* Assembly for callers that cannot allocate device memory when they call it.
+ *
+ * The paper has no counterpart: this is a property of the library, not of the method.  ovs_assemble needs
+ * a context workspace sized for the largest call (ovs_workspace_size(max_points)), so a caller whose
+ * point count grows must allocate a larger one.  Some callers cannot: code running while a CUDA stream is
+ * being captured (cudaMalloc is not allowed there), solver plug-ins whose host application owns all device
+ * memory, and time loops that must not take the implicit device synchronisation of cudaMalloc/cudaFree.
+ * This entry point behaves exactly like ovs_assemble but keeps its only per-call scratch (the slow-path
+ * queue of points decided in FP64) in a fixed array inside the library instead of the context workspace.
+ *
+ *  - Limit: at most OVS_NOALLOC_MAX_POINTS points per call (sum over the sets); larger calls return
+ *    OVS_ERR_WORKSPACE without launching anything.  The array is 24 MiB of device memory
+ *    (OVS_NOALLOC_MAX_POINTS x 24 bytes + 256), held by every GPU on which the library's kernels are
+ *    loaded until the process exits.
+ *  - Allocates nothing: no cudaMalloc/cudaFree and no allocating library routine, host or device.  It
+ *    still needs a context with a workspace attached and grids created (set-up time objects): the grid
+ *    table, the device status word and the statistics counters live there.
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress) with that
+ *    device current; make that first call before any stream capture begins.
+ *  - Every call on a device shares the one array and resets its queue counter: calls whose kernels
+ *    overlap on the GPU (other streams, other contexts, other threads) race and corrupt each other's
+ *    results.  Order them on one stream or synchronise between them.
+ *  - Errors and outputs as ovs_assemble. */
+#define OVS_NOALLOC_MAX_POINTS (1 << 20)
+int ovs_assemble_noalloc(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -574,3 +575,89 @@ int ovs_reset_hints(ovs_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------------
+// ovs_assemble_noalloc: the slow-path queue of k_assemble in a fixed device array instead of the context
+// workspace (see include/ovs.h for who needs this and its limits).
+//
+// Layout of the array: [queue counter, padded to 256 bytes][OVS_NOALLOC_MAX_POINTS slow-path entries].
+// In host code `ovs_noalloc_scratch` is only a host-side stand-in for the symbol; the device address comes
+// from cudaGetSymbolAddress, looked up once per device with that device current.
+namespace {
+constexpr size_t kNoAllocHead = 256;
+constexpr size_t kNoAllocBytes = kNoAllocHead + (size_t)OVS_NOALLOC_MAX_POINTS * sizeof(SlowEntry);
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char ovs_noalloc_scratch[kNoAllocBytes];
+
+extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out) {
+    if (!c) return OVS_ERR_ARG;
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "no context workspace attached (it holds the grid table)");
+    if (c->device < 0 || c->device >= kNoAllocMaxDevices) return fail(c, OVS_ERR_ARG, "device %d", c->device);
+    // the same checks as ovs_assemble, with the fixed array's capacity as the point limit
+    if (nsets < 0 || nsets > OVS_MAX_SETS) return fail(c, OVS_ERR_ARG, "nsets = %d (0..%d)", nsets, OVS_MAX_SETS);
+    if (nsets > 0 && !sets) return fail(c, OVS_ERR_ARG, "sets is NULL");
+    int64_t total = 0;
+    for (int s = 0; s < nsets; ++s) {
+        const ovs_fringe_set& f = sets[s];
+        if (f.receiver < 0 || f.receiver >= c->ngrids)
+            return fail(c, OVS_ERR_ARG, "set %d: receiver grid %d does not exist", s, f.receiver);
+        if (f.n_donors < 1 || f.n_donors > OVS_MAX_DONORS)
+            return fail(c, OVS_ERR_ARG, "set %d: n_donors = %d (1..%d)", s, f.n_donors, OVS_MAX_DONORS);
+        for (int d = 0; d < f.n_donors; ++d)
+            if (f.donors[d] < 0 || f.donors[d] >= c->ngrids)
+                return fail(c, OVS_ERR_ARG, "set %d: donor grid %d does not exist", s, f.donors[d]);
+        if (f.n < 0) return fail(c, OVS_ERR_ARG, "set %d: n = %lld", s, (long long)f.n);
+        if (f.n > 0 && !f.node_ids) return fail(c, OVS_ERR_ARG, "set %d: node_ids is NULL", s);
+        total += f.n;
+    }
+    if (total > OVS_NOALLOC_MAX_POINTS)
+        return fail(c, OVS_ERR_WORKSPACE,
+                    "ovs_assemble_noalloc: %lld points exceed its fixed capacity of %d points per call "
+                    "(split the sets or use ovs_assemble with a larger workspace)",
+                    (long long)total, OVS_NOALLOC_MAX_POINTS);
+    if (!out) return fail(c, OVS_ERR_ARG, "donors output is NULL");
+    if (out->n != total)
+        return fail(c, OVS_ERR_ARG, "donors.n (%lld) must equal the number of points (%lld)", (long long)out->n,
+                    (long long)total);
+    if (total == 0) return OVS_OK;
+    if (!out->grid || !out->cell || !out->xi || !out->status) return fail(c, OVS_ERR_ARG, "donors array is NULL");
+    if (out->xi_dtype != OVS_F32 && out->xi_dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "xi_dtype");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[c->device]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, ovs_noalloc_scratch);
+            if (e != cudaSuccess || !p) return cuda_fail(c, e, "cudaGetSymbolAddress(ovs_noalloc_scratch)");
+            g_noalloc_ptr[c->device] = p;
+        }
+        base = g_noalloc_ptr[c->device];
+    }
+    AsmParams P;  // on the stack: this entry point allocates nothing, not even host memory
+    memset(&P, 0, sizeof P);
+    P.nsets = nsets;
+    P.xi_f64 = out->xi_dtype == OVS_F64;
+    P.max_walk = c->opts.max_walk;
+    P.guess = c->opts.guess;
+    P.stats = c->opts.collect_stats;
+    P.total = total;
+    P.queue_cap = OVS_NOALLOC_MAX_POINTS;
+    P.out_grid = out->grid;
+    P.out_cell = out->cell;
+    P.out_xi = out->xi;
+    P.out_status = out->status;
+    P.queue_count = (uint32_t*)base;  // zeroed on the stream by launch_assemble before the kernels run
+    P.queue = (SlowEntry*)((char*)base + kNoAllocHead);
+    P.counters = c->d_counters;
+    P.err = c->d_err;
+    fill_sets(sets, nsets, P.s);
+    memcpy(P.m, c->motion, sizeof P.m);
+    cudaError_t e = launch_assemble(P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "assemble (no-alloc) launch");
+    return OVS_OK;
+}

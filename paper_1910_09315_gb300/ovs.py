@@ -47,8 +47,10 @@ EXPORTS = [
     "ovs_ctx_create", "ovs_ctx_destroy", "ovs_last_error", "ovs_set_stream", "ovs_workspace_size",
     "ovs_workspace_attach", "ovs_grid_workspace_size", "ovs_create_grid", "ovs_set_motion", "ovs_set_options",
     "ovs_get_options", "ovs_assemble", "ovs_interpolate", "ovs_sync", "ovs_get_stats", "ovs_reset_hints",
-    "ovs_set_trace_events",
+    "ovs_set_trace_events", "ovs_assemble_noalloc",
 ]
+
+OVS_NOALLOC_MAX_POINTS = 1 << 20
 
 
 class ovs_grid_desc(ctypes.Structure):
@@ -124,6 +126,7 @@ def load(path: Optional[str] = None):
         "ovs_get_stats": [V, ctypes.POINTER(ovs_stats), ctypes.c_int],
         "ovs_reset_hints": [V],
         "ovs_set_trace_events": [V, ctypes.POINTER(V), I32],
+        "ovs_assemble_noalloc": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -203,6 +206,12 @@ def ovs_get_options(ctx) -> ovs_options:
 
 def ovs_assemble(ctx, sets, nsets: int, donors: ovs_donors):
     _check(ctx, load().ovs_assemble(ctx, sets, int(nsets), ctypes.byref(donors)))
+
+
+def ovs_assemble_noalloc(ctx, sets, nsets: int, donors: ovs_donors):
+    """ovs_assemble with its slow-path queue in the library's fixed device array: allocates nothing, at most
+    OVS_NOALLOC_MAX_POINTS points per call (see include/ovs.h)."""
+    _check(ctx, load().ovs_assemble_noalloc(ctx, sets, int(nsets), ctypes.byref(donors)))
 
 
 def ovs_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
