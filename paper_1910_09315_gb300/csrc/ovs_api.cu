@@ -87,7 +87,7 @@ void identity_motion(MotionDev& m) {
 int64_t cells_axis(const ovs_grid_desc& d, int a) { return d.periodic[a] ? d.n[a] : d.n[a] - 1; }
 
 struct GridLayout {
-    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, partials, scan, out9, total;
+    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, xff, partials, scan, out9, total;
     int64_t ncells, nnodes, nbins_max, reg_cap;
 };
 
@@ -110,6 +110,8 @@ GridLayout grid_layout(const ovs_grid_desc& d) {
     off = align_up(off + (size_t)L.reg_cap * 4);
     L.hint = off;
     off = align_up(off + (size_t)L.nnodes * 4);
+    L.xff = off;
+    off = align_up(off + (size_t)L.nnodes * 6 * sizeof(float));
     L.partials = off;
     off = align_up(off + (size_t)kReduceBlocks * 9 * sizeof(double));
     L.scan = off;
@@ -173,7 +175,51 @@ void fill_sets(const ovs_fringe_set* sets, int32_t nsets, SetDev* out) {
         out[s].n = sets[s].n;
         begin += sets[s].n;
     }
-    // empty sets must never be chosen by the point -> set lookup: give them the next set's begin
+    // empty sets share the next set's begin; the point -> set lookup takes the last set with begin <= t
+}
+
+// FP32-pair split of an FP64 value: hi = nearest float, lo = nearest float to the remainder
+void split(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// Per set: the receiver -> first-donor transform x_d = M x_r + t, composed in FP64 (M = R_d^T R_r,
+// t = R_d^T (c_r - c_d)) and handed to the kernel as FP32 pairs.
+void fill_xforms(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, XfFF* out) {
+    for (int s = 0; s < nsets; ++s) {
+        const MotionDev& r = c->motion[sets[s].receiver];
+        const MotionDev& d = c->motion[sets[s].donors[0]];
+        XfFF& X = out[s];
+        memset(&X, 0, sizeof X);
+        X.identity = r.identity && d.identity;
+        for (int i = 0; i < 3; ++i) {
+            for (int k = 0; k < 3; ++k) {
+                double m = 0;
+                for (int j = 0; j < 3; ++j) m += d.R[3 * j + i] * r.R[3 * j + k];
+                split(m, X.Mh[3 * i + k], X.Ml[3 * i + k]);
+            }
+            double tv = 0;
+            for (int j = 0; j < 3; ++j) tv += d.R[3 * j + i] * (r.c[j] - d.c[j]);
+            split(tv, X.th[i], X.tl[i]);
+        }
+    }
+}
+
+// FP32 copies of the motions for the FP32 velocity transform
+void fill_motion_f32(const ovs_ctx* c, MotionF* out) {
+    for (int g = 0; g < OVS_MAX_GRIDS; ++g) {
+        const MotionDev& m = c->motion[g];
+        MotionF& f = out[g];
+        memset(&f, 0, sizeof f);
+        for (int q = 0; q < 9; ++q) f.R[q] = (float)m.R[q];
+        for (int q = 0; q < 3; ++q) {
+            split(m.c[q], f.ch[q], f.cl[q]);
+            f.V[q] = (float)m.V[q];
+            f.w[q] = (float)m.w[q];
+        }
+        f.identity = m.identity;
+    }
 }
 
 }  // namespace
@@ -229,7 +275,7 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     if (!c || !bytes || max_points < 0) return OVS_ERR_ARG;
     size_t off = align_up(sizeof(GridDev) * OVS_MAX_GRIDS);
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
-    off = align_up(off + 2 * sizeof(int32_t));
+    off = align_up(off + 4 * sizeof(int32_t));
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
     *bytes = off;
     return OVS_OK;
@@ -252,8 +298,8 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     c->d_counters = (unsigned long long*)(base + off);
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     c->d_err = (int32_t*)(base + off);
-    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));
-    off = align_up(off + 2 * sizeof(int32_t));
+    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // two counters: near-face and stuck queues
+    off = align_up(off + 4 * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
     c->ws = dptr;
     c->ws_bytes = bytes;
@@ -305,11 +351,12 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
     g.bin_cells = (const int32_t*)(base + L.bin_cells);
     g.bin_rep = (const int32_t*)(base + L.bin_rep);
     g.hint = (uint32_t*)(base + L.hint);
+    g.xff = (const float*)(base + L.xff);
     g.mlp = nullptr;
     double* out9 = (double*)(base + L.out9);
     int nblk = (int)std::min<int64_t>(kReduceBlocks, (L.ncells + 255) / 256);
-    OVS_CUDA(c, launch_build_records(g, (CellRec*)(base + L.rec), (double*)(base + L.partials), nblk, out9,
-                                     c->stream));
+    OVS_CUDA(c, launch_build_records(g, (CellRec*)(base + L.rec), (float*)(base + L.xff),
+                                     (double*)(base + L.partials), nblk, out9, c->stream));
     double h9[9];
     OVS_CUDA(c, cudaMemcpyAsync(h9, out9, sizeof h9, cudaMemcpyDeviceToHost, c->stream));
     OVS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -462,6 +509,7 @@ int ovs_assemble(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     P->counters = c->d_counters;
     P->err = c->d_err;
     fill_sets(sets, nsets, P->s);
+    fill_xforms(c, sets, nsets, P->xf);
     memcpy(P->m, c->motion, sizeof P->m);
     cudaError_t e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr);
     delete P;
@@ -513,6 +561,7 @@ int ovs_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const
     P->out[3] = out->p;
     fill_sets(sets, nsets, P->s);
     memcpy(P->m, c->motion, sizeof P->m);
+    fill_motion_f32(c, P->mf);
     for (int g = 0; g < c->ngrids; ++g) {
         P->fields[g].f[0] = fields[g].u;
         P->fields[g].f[1] = fields[g].v;
@@ -651,11 +700,12 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     P.out_cell = out->cell;
     P.out_xi = out->xi;
     P.out_status = out->status;
-    P.queue_count = (uint32_t*)base;  // zeroed on the stream by launch_assemble before the kernels run
+    P.queue_count = (uint32_t*)base;  // two counters, zeroed on the stream by launch_assemble before the kernels run
     P.queue = (SlowEntry*)((char*)base + kNoAllocHead);
     P.counters = c->d_counters;
     P.err = c->d_err;
     fill_sets(sets, nsets, P.s);
+    fill_xforms(c, sets, nsets, P.xf);
     memcpy(P.m, c->motion, sizeof P.m);
     cudaError_t e = launch_assemble(P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble (no-alloc) launch");

@@ -1,15 +1,17 @@
 // Donor search (Sec. 2.2.5, Algorithm 3 "donor search", with Newton inversion of the trilinear map):
 //
-//   k_assemble       one thread per query point: frame map (FP64), localisation (hint | control cell),
-//                    FP32 walk over 128-byte cell records with FP32 Newton; points that end strictly
-//                    inside a cell (every local coordinate at least 1e-4 from a face) are final.
-//                    Points near a face, points in FP64 precision mode and stuck walks are compacted
-//                    (warp ballot + one atomic per warp) into the slow queue.
-//   k_assemble_slow  one thread per queued point: FP64 Newton on the exact node coordinates over the
-//                    cells sharing the near face/edge/corner, lowest linear id first; if none holds the
-//                    point, the exhaustive search of the point's control cell of Sec. 2.2.5 (the paper's
-//                    brute-force fallback) with the same FP64 predicate.  Then the later grids of the
-//                    set's priority list (Sec. 2.4 item 1).
+//   k_assemble       one thread per query point, no FP64 instruction on its common path: frame map of the
+//                    receiver node (FP32 pairs) into the first donor's frame, localisation (per-node hint |
+//                    control cell), FP32 walk over 128-byte cell records with FP32 Newton.  Points that end
+//                    strictly inside a cell (every local coordinate at least 1e-4 from a face) are final.
+//                    Points near a face, points in FP64 precision mode and stuck walks are compacted (warp
+//                    ballot + one atomic per warp) into the slow queue.
+//   k_slow_near      one warp per point near a face: the donor predicate (FP32-pair Newton on the node
+//                    coordinates, FP64 where that cannot decide) over the cells sharing the near faces /
+//                    edges / corner, one lane each, lowest linear id first.
+//   k_slow_stuck     one block per stuck walk: the exhaustive search of the point's control cell of
+//                    Sec. 2.2.5 (the paper's brute-force fallback); all threads filter the list, warp 0 decides.
+//   Both continue with the later grids of the set's priority list (Sec. 2.4 item 1).
 #include "ovs_internal.cuh"
 
 namespace ovs {
@@ -17,13 +19,14 @@ namespace ovs {
 namespace {
 
 constexpr int kAsmThreads = 256;
+constexpr int kAsmMinBlocks = 3;
 
 enum WalkResult { kWalkFound = 0, kWalkStuck = 1 };
 
-// FP32 walk from `cell`.  On kWalkFound, cell/u/v/w hold a cell whose FP32 local coordinates lie within
-// kAccept32 of [0,1]^3.
-__device__ __forceinline__ int walk32(const GridDev& g, double3 p, int64_t& cell, float& u, float& v, float& w,
-                                      int max_walk, int& steps) {
+// FP32 walk from `cell` toward the donor-frame point xd (FP32 pairs).  On kWalkFound, cell/u/v/w hold a cell
+// whose FP32 local coordinates lie within kAccept32 of [0,1]^3.
+__device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t& cell, float& u, float& v, float& w,
+                                      float& tau, int max_walk, int& steps) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
     u = v = w = 0.5f;
@@ -32,14 +35,20 @@ __device__ __forceinline__ int walk32(const GridDev& g, double3 p, int64_t& cell
         ++steps;
         CellRec r;
         load_rec(g.rec, cell, r);
-        float dx = (float)(p.x - r.x0[0]), dy = (float)(p.y - r.x0[1]), dz = (float)(p.z - r.x0[2]);
+        // point minus corner 0: the high parts cancel exactly near the cell, the low parts carry the rest
+        float dx = __fadd_rn(__fsub_rn(xd[0].hi, r.x0h[0]), __fsub_rn(xd[0].lo, r.x0l[0]));
+        float dy = __fadd_rn(__fsub_rn(xd[1].hi, r.x0h[1]), __fsub_rn(xd[1].lo, r.x0l[1]));
+        float dz = __fadd_rn(__fsub_rn(xd[2].hi, r.x0h[2]), __fsub_rn(xd[2].lo, r.x0l[2]));
         bool conv = newton32(r, dx, dy, dz, u, v, w);
         if (!(fabsf(u) < 1e30f && fabsf(v) < 1e30f && fabsf(w) < 1e30f)) return kWalkStuck;
         bool in = u >= -kAccept32 && u <= 1.f + kAccept32 && v >= -kAccept32 && v <= 1.f + kAccept32 &&
                   w >= -kAccept32 && w <= 1.f + kAccept32;
-        if (in && conv) return kWalkFound;
-        // step toward the point by the sign (and size, up to kMaxJump) of the local coordinates: the
-        // sign test of the paper's walk, applied to Newton's local coordinates
+        if (in && conv) {
+            tau = near_tau(r, u, v, w);
+            return kWalkFound;
+        }
+        // step toward the point by the sign (and size, up to kMaxJump) of the local coordinates: the sign
+        // test of the paper's walk, applied to Newton's local coordinates
         float q[3] = {u, v, w};
         int cur[3] = {i, j, k};
         int nxt[3];
@@ -50,15 +59,16 @@ __device__ __forceinline__ int walk32(const GridDev& g, double3 p, int64_t& cell
             if (q[m] < -kAccept32) jm = max(-kMaxJump, (int)floorf(fmaxf(q[m], -1e6f)));
             else if (q[m] > 1.f + kAccept32) jm = min(kMaxJump, (int)floorf(fminf(q[m], 1e6f)));
             int t = cur[m] + jm;
+            int applied;
             if (g.per[m]) {
                 t %= g.C[m];
                 if (t < 0) t += g.C[m];
+                applied = jm;
             } else {
                 t = min(max(t, 0), g.C[m] - 1);
+                applied = t - cur[m];
             }
             nxt[m] = t;
-            int applied = t - cur[m];
-            if (g.per[m] && applied != jm) applied = jm;  // wrapped: same local shift
             if (applied != 0) moved = true;
             q[m] = conv ? fminf(fmaxf(q[m] - (float)applied, -1.f), 2.f) : 0.5f;
         }
@@ -92,6 +102,17 @@ __device__ __forceinline__ void write_donor(const AsmParams& P, int64_t t, int32
     P.out_status[t] = status;
 }
 
+__device__ __forceinline__ void write_donor32(const AsmParams& P, int64_t t, int32_t gd, int64_t cell, float u,
+                                              float v, float w, uint8_t status) {
+    P.out_grid[t] = gd;
+    P.out_cell[t] = (int32_t)cell;
+    float* xi = (float*)P.out_xi;
+    xi[t] = u;
+    xi[P.total + t] = v;
+    xi[2 * P.total + t] = w;
+    P.out_status[t] = status;
+}
+
 __device__ __forceinline__ void write_none(const AsmParams& P, int64_t t, uint8_t status) {
     P.out_grid[t] = -1;
     P.out_cell[t] = -1;
@@ -110,8 +131,8 @@ __device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned v) {
     if (lane_id() == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_assemble(const __grid_constant__ AsmParams P,
-                                                          const GridDev* __restrict__ G) {
+__global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const __grid_constant__ AsmParams P,
+                                                                         const GridDev* __restrict__ G) {
     const int64_t t = blockIdx.x * (int64_t)kAsmThreads + threadIdx.x;
     const bool active = t < P.total;
     bool slow = false;
@@ -122,74 +143,110 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const __grid_constant_
         const SetDev& s = P.s[si];
         const int32_t node = __ldg(s.node_ids + (t - s.begin));
         const GridDev& gr = G[s.receiver];
-        const bool node_ok = node >= 0 && node < gr.nnodes;
-        double3 xin = make_double3(0.0, 0.0, 0.0);
+        const int64_t nn = gr.nnodes;
+        const bool node_ok = node >= 0 && node < nn;
+        if (!node_ok) atomicOr(P.err, kErrBadNode);
+        // receiver node as FP32 pairs and its image in the first donor's frame
+        ff x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, xd[3];
         if (node_ok) {
-            double3 xr = make_double3(__ldg(gr.x + node), __ldg(gr.y + node), __ldg(gr.z + node));
-            xin = to_inertial(P.m[s.receiver], xr);
-        } else {
-            atomicOr(P.err, kErrBadNode);
+            const float* xf = gr.xff;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = {__ldg(xf + 2 * c * nn + node), __ldg(xf + (2 * c + 1) * nn + node)};
         }
-        if (!node_ok || !finite3(xin)) {
-            write_none(P, t, OVS_STATUS_BADINPUT);
-        } else {
-            bool done = false;
-            for (int di = 0; di < s.ndonor && !done && !slow; ++di) {
-                const int gd = s.donors[di];
-                const GridDev& g = G[gd];
-                double3 p = to_body(P.m[gd], xin);
-                int64_t b = point_bin(g, p);
-                if (b < 0) continue;
-                int64_t cell = -1;
-                if (P.guess == OVS_GUESS_HINT) {
-                    uint32_t h = gr.hint[node];
-                    if (h != kNoHint && (int)(h >> kCellBits) == gd) cell = h & ((1u << kCellBits) - 1);
-                    if (cell >= g.ncells) cell = -1;
-                }
-                if (cell < 0) {
-                    // lowest registered cell of the control cell; >= ncells marks an empty control cell, where
-                    // no cell of this grid can hold the point
-                    cell = __ldg(g.bin_rep + b);
-                    if (cell < 0 || cell >= g.ncells) continue;
-                }
-                float u, v, w;
-                int r = walk32(g, p, cell, u, v, w, P.max_walk, steps);
-                e.t = (int32_t)t;
-                e.di = di;
-                if (r == kWalkFound) {
-                    float mu = fminf(u, 1.f - u), mv = fminf(v, 1.f - v), mw = fminf(w, 1.f - w);
-                    bool near = fminf(mu, fminf(mv, mw)) < kNearFace;
-                    if (near || P.xi_f64) {
-                        slow = true;
-                        e.cell = (int32_t)cell;
-                        e.xi[0] = u;
-                        e.xi[1] = v;
-                        e.xi[2] = w;
-                    } else {
-                        write_donor(P, t, gd, cell, u, v, w, OVS_STATUS_FOUND);
-                        gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
-                        done = true;
+        xf_apply(P.xf[si], x, xd);
+        bool fast_ok = ff_finite(xd[0]) && ff_finite(xd[1]) && ff_finite(xd[2]);
+        // FP64 route: later donors of the list, and points whose FP32-pair image is not finite
+        bool have64 = false, bad = !node_ok;
+        double3 xin = make_double3(0.0, 0.0, 0.0);
+        bool done = false;
+        for (int di = 0; di < s.ndonor && !done && !slow && !bad; ++di) {
+            const int gd = s.donors[di];
+            const GridDev& g = G[gd];
+            if (di > 0 || !fast_ok) {
+                if (!have64) {
+                    double3 xr = make_double3(__ldg(gr.x + node), __ldg(gr.y + node), __ldg(gr.z + node));
+                    xin = to_inertial(P.m[s.receiver], xr);
+                    have64 = true;
+                    if (!finite3(xin)) {
+                        bad = true;
+                        break;
                     }
-                } else {
-                    slow = true;
-                    e.cell = -1;
-                    e.xi[0] = e.xi[1] = e.xi[2] = 0.5f;
+                }
+                double3 p = to_body(P.m[gd], xin);
+                xd[0] = split_double(p.x);
+                xd[1] = split_double(p.y);
+                xd[2] = split_double(p.z);
+                if (!(ff_finite(xd[0]) && ff_finite(xd[1]) && ff_finite(xd[2]))) {
+                    if (finite3(p)) {  // finite in FP64 but beyond FP32 range: only the FP64 path can decide
+                        slow = true;
+                        e.t = (int32_t)t;
+                        e.di = di;
+                        e.cell = -1;
+                        e.xi[0] = e.xi[1] = e.xi[2] = 0.5f;
+                    }
+                    continue;
                 }
             }
-            if (!done && !slow) write_none(P, t, OVS_STATUS_ORPHAN);
+            int64_t cell = -1;
+            if (P.guess == OVS_GUESS_HINT) {
+                uint32_t h = gr.hint[node];
+                if (h != kNoHint && (int)(h >> kCellBits) == gd) cell = h & ((1u << kCellBits) - 1);
+                if (cell >= g.ncells) cell = -1;
+            }
+            if (cell < 0) {
+                // cold start: the lowest registered cell of the point's control cell.  Outside the bins' box
+                // or in an empty control cell (rep >= ncells), no cell of this grid can hold the point.
+                double3 p = make_double3((double)xd[0].hi + (double)xd[0].lo, (double)xd[1].hi + (double)xd[1].lo,
+                                         (double)xd[2].hi + (double)xd[2].lo);
+                int64_t b = point_bin(g, p);
+                if (b < 0) continue;
+                cell = __ldg(g.bin_rep + b);
+                if (cell < 0 || cell >= g.ncells) continue;
+            }
+            float u, v, w, tau = 0.25f;
+            int r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps);
+            e.t = (int32_t)t;
+            e.di = di;
+            if (r == kWalkFound) {
+                const int mask = near_mask(u, v, w, tau);
+                if (mask == 0 && !P.xi_f64) {
+                    write_donor32(P, t, gd, cell, u, v, w, OVS_STATUS_FOUND);
+                    gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
+                    done = true;
+                } else {
+                    // near a face (FP64 decision among the neighbours), or FP64 precision (FP64 refinement)
+                    slow = true;
+                    e.di = di | (mask << 8);
+                    e.cell = (int32_t)cell;
+                    e.xi[0] = u;
+                    e.xi[1] = v;
+                    e.xi[2] = w;
+                }
+            } else {
+                slow = true;
+                e.cell = -1;
+                e.xi[0] = e.xi[1] = e.xi[2] = 0.5f;
+            }
         }
+        if (bad) write_none(P, t, OVS_STATUS_BADINPUT);
+        else if (!done && !slow) write_none(P, t, OVS_STATUS_ORPHAN);
     }
-    // warp-aggregated append to the slow queue
-    unsigned mask = __ballot_sync(0xffffffffu, slow);
-    if (mask) {
-        unsigned lane = lane_id();
+    // warp-aggregated append to the slow queues: points near a face (a candidate cell is known) from the front
+    // of the buffer, stuck walks from the back.  Each point is queued at most once, so the two never meet.
+    const bool near = slow && e.cell >= 0;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int qk = 0; qk < 2; ++qk) {
+        const bool mine = qk == 0 ? near : (slow && !near);
+        unsigned mask = __ballot_sync(0xffffffffu, mine);
+        if (!mask) continue;
         int leader = __ffs(mask) - 1;
         uint32_t base = 0;
-        if ((int)lane == leader) base = atomicAdd(P.queue_count, (uint32_t)__popc(mask));
+        if ((int)lane == leader) base = atomicAdd(P.queue_count + qk, (uint32_t)__popc(mask));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (slow) {
+        if (mine) {
             uint32_t idx = base + __popc(mask & ((1u << lane) - 1u));
-            if (idx < P.queue_cap) P.queue[idx] = e;
+            if (idx < P.queue_cap) P.queue[qk == 0 ? idx : P.queue_cap - 1 - idx] = e;
             else atomicOr(P.err, kErrQueueOverflow);
         }
     }
@@ -199,16 +256,19 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const __grid_constant_
     }
 }
 
-// Candidate cells sharing the near face / edge / corner of `cell` (FP32 local coordinates within kNearFace
-// of a face), in ascending linear id.  Returns their count (<= 8) and the offsets to shift the FP32 guess.
-__device__ int near_candidates(const GridDev& g, int64_t cell, const float xi32[3], int64_t ids[8], int off[8][3]) {
+// ------------------------------------------------------------------------------------------------------
+// slow path
+
+// Candidate cells sharing the near faces / edges / corner of `cell` given by the near-face mask, in ascending
+// linear id.  Returns their count (<= 8) and the offsets to shift the FP32 guess.
+__device__ int near_candidates(const GridDev& g, int64_t cell, int mask, int64_t ids[8], int off[8][3]) {
     int ijk[3];
     cell_ijk(g, cell, ijk[0], ijk[1], ijk[2]);
     int lo[3], hi[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        lo[m] = xi32[m] < kNearFace ? -1 : 0;
-        hi[m] = xi32[m] > 1.f - kNearFace ? 1 : 0;
+        lo[m] = (mask >> m) & 1 ? -1 : 0;
+        hi[m] = (mask >> (3 + m)) & 1 ? 1 : 0;
     }
     int nc = 0;
     for (int oz = lo[2]; oz <= hi[2]; ++oz)
@@ -243,19 +303,20 @@ __device__ int near_candidates(const GridDev& g, int64_t cell, const float xi32[
     return nc;
 }
 
-// Warp-cooperative lowest-id FP64 decision over the near candidates: lane q tests candidate q; the lowest
-// lane (= lowest id) whose cell holds the point wins.  All 32 lanes must call this.
-__device__ bool neighbourhood64_warp(const GridDev& g, double3 p, int64_t cell, const float xi32[3],
-                                     int64_t& out_cell, double& u, double& v, double& w) {
+// Warp-cooperative lowest-id decision over the near candidates (donor predicate of contains_exact): lane q
+// tests candidate q; the lowest lane (= lowest id) whose cell holds the point wins.  All 32 lanes of the warp
+// must call this.
+template <class P64>
+__device__ bool neighbourhood_warp(const GridDev& g, const ff pf[3], const P64& p64, int64_t cell, int mask,
+                                   const float xi32[3], int64_t& out_cell, double& u, double& v, double& w) {
     int64_t ids[8];
     int off[8][3];
-    int nc = near_candidates(g, cell, xi32, ids, off);
+    int nc = near_candidates(g, cell, mask, ids, off);
     const int lane = (int)lane_id();
     bool hit = false;
     double a = 0, b = 0, c = 0;
     int64_t mine = -1;
     if (lane < nc) {
-        // select this lane's candidate without dynamic register indexing
         int o0 = 0, o1 = 0, o2 = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -265,10 +326,8 @@ __device__ bool neighbourhood64_warp(const GridDev& g, double3 p, int64_t cell, 
                 o1 = off[q][1];
                 o2 = off[q][2];
             }
-        a = (double)xi32[0] - o0;
-        b = (double)xi32[1] - o1;
-        c = (double)xi32[2] - o2;
-        hit = newton64_contains(g, mine, p, a, b, c);
+        hit = contains_exact(g, mine, pf, p64, xi32[0] - (float)o0, xi32[1] - (float)o1, xi32[2] - (float)o2, a, b,
+                             c);
     }
     unsigned m = __ballot_sync(0xffffffffu, hit);
     if (!m) return false;
@@ -280,126 +339,328 @@ __device__ bool neighbourhood64_warp(const GridDev& g, double3 p, int64_t cell, 
     return true;
 }
 
-// Warp-cooperative exhaustive search of the point's control cell (Sec. 2.2.5 brute-force fallback): lanes
-// split the registered cells; a cell is rejected by its padded box (FP32, relative to its corner 0) or by a
-// converged FP32 Newton that lands clearly outside; the rest get the FP64 predicate.  Lowest id wins.
-__device__ bool exhaustive64_warp(const GridDev& g, double3 p, int64_t bin, int64_t& out_cell, double& u, double& v,
-                                  double& w) {
+constexpr int kSlowThreads = 256;
+constexpr int kSlowWarps = kSlowThreads / 32;
+
+// Cheap rejections of one cell of an exhaustive search: its padded box (FP32, relative to its corner 0), the
+// slabs along its three affine face normals (the cell, the convex hull of its corners, lies between the extreme
+// corner projections), and the FP32 Newton iteration from the cell centre (up to 24 steps) ending more than
+// 1e-3 outside [0,1]^3 (the same iteration in FP32 pairs or FP64 from the same start follows it to within
+// rounding, ~1e-5 in local coordinates for the cells accepted here, so it cannot end in the donor window).
+// On pass, xi holds the FP32 iterate, the start of the donor predicate.
+__device__ __forceinline__ bool exhaustive_filter(const GridDev& g, double3 p, uint32_t c, float xi[3]) {
+    CellRec rec;
+    load_rec(g.rec, c, rec);
+    float d[3];
+    d[0] = (float)(p.x - ((double)rec.x0h[0] + (double)rec.x0l[0]));
+    d[1] = (float)(p.y - ((double)rec.x0h[1] + (double)rec.x0l[1]));
+    d[2] = (float)(p.z - ((double)rec.x0h[2] + (double)rec.x0l[2]));
+    const float* A = rec.a;
+    float E[8][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float a1 = A[k], a2 = A[3 + k], a3 = A[6 + k], a4 = A[9 + k], a5 = A[12 + k], a6 = A[15 + k], a7 = A[18 + k];
+        E[0][k] = 0.f;
+        E[1][k] = a1;
+        E[2][k] = a2;
+        E[3][k] = a1 + a2 + a4;
+        E[4][k] = a3;
+        E[5][k] = a1 + a3 + a6;
+        E[6][k] = a2 + a3 + a5;
+        E[7][k] = a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    }
+    float mn[3], mx[3], diag2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        mn[k] = mx[k] = 0.f;
+#pragma unroll
+        for (int a = 1; a < 8; ++a) {
+            mn[k] = fminf(mn[k], E[a][k]);
+            mx[k] = fmaxf(mx[k], E[a][k]);
+        }
+        diag2 += (mx[k] - mn[k]) * (mx[k] - mn[k]);
+    }
+    const float pad = 4e-6f * sqrtf(diag2) + 1e-30f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (!(d[k] >= mn[k] - pad && d[k] <= mx[k] + pad)) return false;
+    const float* c1 = A;
+    const float* c2 = A + 3;
+    const float* c3 = A + 6;
+    const float nrm[3][3] = {{c2[1] * c3[2] - c2[2] * c3[1], c2[2] * c3[0] - c2[0] * c3[2], c2[0] * c3[1] - c2[1] * c3[0]},
+                             {c3[1] * c1[2] - c3[2] * c1[1], c3[2] * c1[0] - c3[0] * c1[2], c3[0] * c1[1] - c3[1] * c1[0]},
+                             {c1[1] * c2[2] - c1[2] * c2[1], c1[2] * c2[0] - c1[0] * c2[2], c1[0] * c2[1] - c1[1] * c2[0]}};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int a = 1; a < 8; ++a) {
+            float pr = nrm[q][0] * E[a][0] + nrm[q][1] * E[a][1] + nrm[q][2] * E[a][2];
+            lo = fminf(lo, pr);
+            hi = fmaxf(hi, pr);
+        }
+        float len = sqrtf(nrm[q][0] * nrm[q][0] + nrm[q][1] * nrm[q][1] + nrm[q][2] * nrm[q][2]);
+        float pp = nrm[q][0] * d[0] + nrm[q][1] * d[1] + nrm[q][2] * d[2];
+        float sp = pad * len + 1e-6f * (hi - lo) + 1e-30f;  // rounding of the FP32 projections
+        if (!(pp >= lo - sp && pp <= hi + sp)) return false;
+    }
+    float fu = 0.5f, fv = 0.5f, fw = 0.5f;
+    newton32(rec, d[0], d[1], d[2], fu, fv, fw, 24);
+    const float far = 1e-3f;
+    if (!(fu >= -far && fu <= 1.f + far && fv >= -far && fv <= 1.f + far && fw >= -far && fw <= 1.f + far))
+        return false;
+    xi[0] = fu;
+    xi[1] = fv;
+    xi[2] = fw;
+    return true;
+}
+
+// Warp-level exhaustive search of a control cell (lanes stride its list); lowest id wins.  All lanes call.
+__device__ bool exhaustive_warp(const GridDev& g, double3 p, const ff pf[3], int64_t b, int64_t& cell, double& u,
+                                double& v, double& w) {
     const int lane = (int)lane_id();
     uint32_t best = 0xFFFFFFFFu;
     double bu = 0, bv = 0, bw = 0;
-    int32_t r0 = __ldg(g.bin_start + bin), r1 = __ldg(g.bin_start + bin + 1);
+    int32_t r0 = __ldg(g.bin_start + b), r1 = __ldg(g.bin_start + b + 1);
     for (int32_t r = r0 + lane; r < r1; r += 32) {
         uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
         if (c >= best) continue;
-        CellRec rec;
-        load_rec(g.rec, c, rec);
-        float dx = (float)(p.x - rec.x0[0]), dy = (float)(p.y - rec.x0[1]), dz = (float)(p.z - rec.x0[2]);
-        float d[3] = {dx, dy, dz};
-        bool inbox = true;
-        float diag2 = 0.f;
-        float mn[3], mx[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float a1 = rec.a[k], a2 = rec.a[3 + k], a3 = rec.a[6 + k], a4 = rec.a[9 + k], a5 = rec.a[12 + k],
-                  a6 = rec.a[15 + k], a7 = rec.a[18 + k];
-            float e[8] = {0.f, a1, a2, a1 + a2 + a4, a3, a1 + a3 + a6, a2 + a3 + a5,
-                          a1 + a2 + a3 + a4 + a5 + a6 + a7};
-            mn[k] = e[0];
-            mx[k] = e[0];
-#pragma unroll
-            for (int q = 1; q < 8; ++q) {
-                mn[k] = fminf(mn[k], e[q]);
-                mx[k] = fmaxf(mx[k], e[q]);
-            }
-            diag2 += (mx[k] - mn[k]) * (mx[k] - mn[k]);
-        }
-        float pad = 4e-6f * sqrtf(diag2) + 1e-30f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) inbox = inbox && d[k] >= mn[k] - pad && d[k] <= mx[k] + pad;
-        if (!inbox) continue;
-        float fu = 0.5f, fv = 0.5f, fw = 0.5f;
-        bool conv = newton32(rec, dx, dy, dz, fu, fv, fw);
-        const float far = 0.05f;
-        if (conv && (fu < -far || fu > 1.f + far || fv < -far || fv > 1.f + far || fw < -far || fw > 1.f + far))
-            continue;
-        double a = 0.5, b = 0.5, cc = 0.5;
-        if (newton64_contains(g, c, p, a, b, cc)) {
+        float xi[3];
+        if (!exhaustive_filter(g, p, c, xi)) continue;
+        double a, bb, cc;
+        if (contains_exact(g, c, pf, [&]() { return p; }, xi[0], xi[1], xi[2], a, bb, cc)) {
             best = c;
             bu = a;
-            bv = b;
+            bv = bb;
             bw = cc;
         }
     }
     uint32_t wbest = __reduce_min_sync(0xffffffffu, best);
     if (wbest == 0xFFFFFFFFu) return false;
-    unsigned m = __ballot_sync(0xffffffffu, best == wbest);
-    int src = __ffs(m) - 1;
-    out_cell = wbest;
+    int src = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+    cell = wbest;
     u = __shfl_sync(0xffffffffu, bu, src);
     v = __shfl_sync(0xffffffffu, bv, src);
     w = __shfl_sync(0xffffffffu, bw, src);
     return true;
 }
 
-constexpr int kSlowThreads = 256;
+// Everything a queued point needs: its set, receiver node, and the donor-frame point for one donor.
+struct SlowPoint {
+    int64_t t;
+    int si;
+    int32_t node;
+    int di0, mask0;
+};
 
-// One warp per queued point.
-__global__ void __launch_bounds__(kSlowThreads) k_assemble_slow(const __grid_constant__ AsmParams P,
-                                                                const GridDev* __restrict__ G) {
-    uint32_t count = *P.queue_count;
-    if (count > P.queue_cap) count = (uint32_t)P.queue_cap;
-    const int lane = (int)lane_id();
-    const uint32_t warp = (blockIdx.x * kSlowThreads + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * kSlowThreads) >> 5;
-    unsigned refined = 0, fallback = 0;
-    for (uint32_t q = warp; q < count; q += nwarps) {
-        SlowEntry e = P.queue[q];
-        const int64_t t = e.t;
-        const int si = find_set(P.s, P.nsets, t);
-        const SetDev& s = P.s[si];
-        const int32_t node = __ldg(s.node_ids + (t - s.begin));
+__device__ __forceinline__ SlowPoint slow_point(const AsmParams& P, const SlowEntry& e) {
+    SlowPoint sp;
+    sp.t = e.t;
+    sp.si = find_set(P.s, P.nsets, sp.t);
+    sp.node = __ldg(P.s[sp.si].node_ids + (sp.t - P.s[sp.si].begin));
+    sp.di0 = e.di & 0xFF;
+    sp.mask0 = (e.di >> 8) & 0x3F;
+    return sp;
+}
+
+// FP64 image of the receiver node in donor gd's frame (the donor rule's definition)
+__device__ __forceinline__ double3 point64(const AsmParams& P, const GridDev* G, const SlowPoint& sp, int gd) {
+    const SetDev& s = P.s[sp.si];
+    const GridDev& gr = G[s.receiver];
+    double3 xr = make_double3(gr.x[sp.node], gr.y[sp.node], gr.z[sp.node]);
+    return to_body(P.m[gd], to_inertial(P.m[s.receiver], xr));
+}
+
+// The point as FP32 pairs in donor di's frame: the fast kernel's transform for the first donor, else from FP64
+__device__ __forceinline__ bool point_ff(const AsmParams& P, const GridDev* G, const SlowPoint& sp, int di, ff pf[3]) {
+    const SetDev& s = P.s[sp.si];
+    if (di == 0) {
         const GridDev& gr = G[s.receiver];
-        double3 xr = make_double3(gr.x[node], gr.y[node], gr.z[node]);
-        double3 xin = to_inertial(P.m[s.receiver], xr);
+        const int64_t nn = gr.nnodes;
+        ff x[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            x[c] = {__ldg(gr.xff + 2 * c * nn + sp.node), __ldg(gr.xff + (2 * c + 1) * nn + sp.node)};
+        xf_apply(P.xf[sp.si], x, pf);
+    } else {
+        double3 pp = point64(P, G, sp, s.donors[di]);
+        pf[0] = split_double(pp.x);
+        pf[1] = split_double(pp.y);
+        pf[2] = split_double(pp.z);
+    }
+    return ff_finite(pf[0]) && ff_finite(pf[1]) && ff_finite(pf[2]);
+}
+
+__device__ __forceinline__ void finish(const AsmParams& P, const GridDev* G, const SlowPoint& sp, int gd, int64_t cell,
+                                       double u, double v, double w, uint8_t st) {
+    write_donor(P, sp.t, gd, cell, u, v, w, st);
+    G[P.s[sp.si].receiver].hint[sp.node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
+}
+
+// Points near a face: one warp each, one lane per candidate cell.  A point whose candidates all fail (or a
+// later donor of its list) gets the warp-level exhaustive search.
+__global__ void __launch_bounds__(kSlowThreads) k_slow_near(const __grid_constant__ AsmParams P,
+                                                            const GridDev* __restrict__ G) {
+    uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
+    const int lane = (int)lane_id();
+    unsigned nref = 0, nfb = 0;
+    for (uint32_t q = blockIdx.x * kSlowWarps + (threadIdx.x >> 5); q < count; q += gridDim.x * kSlowWarps) {
+        const SlowEntry e = P.queue[q];
+        const SlowPoint sp = slow_point(P, e);
+        const SetDev& s = P.s[sp.si];
         bool done = false;
-        for (int di = e.di; di < s.ndonor && !done; ++di) {
+        for (int di = sp.di0; di < s.ndonor && !done; ++di) {
             const int gd = s.donors[di];
             const GridDev& g = G[gd];
-            double3 p = to_body(P.m[gd], xin);
-            int64_t b = point_bin(g, p);
-            if (b < 0) continue;
+            auto p64 = [&]() { return point64(P, G, sp, gd); };
+            ff pf[3];
+            const bool pf_ok = point_ff(P, G, sp, di, pf);
             int64_t cell = -1;
             double u = 0, v = 0, w = 0;
             uint8_t st = OVS_STATUS_FOUND | OVS_STATUS_REFINED;
             bool ok = false;
-            if (di == e.di && e.cell >= 0) ok = neighbourhood64_warp(g, p, e.cell, e.xi, cell, u, v, w);
+            if (di == sp.di0 && pf_ok) ok = neighbourhood_warp(g, pf, p64, e.cell, sp.mask0, e.xi, cell, u, v, w);
             if (!ok) {
-                ok = exhaustive64_warp(g, p, b, cell, u, v, w);
+                const double3 p = p64();
+                const int64_t b = point_bin(g, p);
+                if (b < 0) continue;
+                if (!pf_ok) {
+                    pf[0] = split_double(p.x);
+                    pf[1] = split_double(p.y);
+                    pf[2] = split_double(p.z);
+                }
                 st |= OVS_STATUS_FALLBACK;
-                ++fallback;
+                ++nfb;
+                ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
             }
             if (ok) {
-                if (lane == 0) {
-                    write_donor(P, t, gd, cell, u, v, w, st);
-                    gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
-                }
+                if (lane == 0) finish(P, G, sp, gd, cell, u, v, w, st);
                 done = true;
-                ++refined;
+                ++nref;
             }
         }
-        if (!done && lane == 0) write_none(P, t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+        if (!done && lane == 0) write_none(P, sp.t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
     }
     if (P.stats && lane == 0) {
-        if (refined) atomicAdd(P.counters + kCtrRefined, (unsigned long long)refined);
-        if (fallback) atomicAdd(P.counters + kCtrFallback, (unsigned long long)fallback);
+        if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
+        if (nfb) atomicAdd(P.counters + kCtrFallback, (unsigned long long)nfb);
+    }
+}
+
+constexpr int kMaxCand = 128;
+
+// Stuck walks (points outside the grid, or where the walk gave up): one block each.  All threads filter the
+// control cell's list (box, slabs, FP32 Newton); warp 0 applies the donor predicate to the survivors.
+__global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const __grid_constant__ AsmParams P,
+                                                             const GridDev* __restrict__ G) {
+    __shared__ uint32_t cand[kMaxCand];
+    __shared__ float cxi[kMaxCand][3];
+    __shared__ int ncand;
+    __shared__ int found;
+    __shared__ long long fcell;
+    __shared__ double fuvw[3];
+    const uint32_t count = min(P.queue_count[1], (uint32_t)P.queue_cap);
+    const int lane = (int)lane_id();
+    const int warp = threadIdx.x >> 5;
+    unsigned nref = 0, nfb = 0;
+    for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
+        const SlowEntry e = P.queue[P.queue_cap - 1 - q];
+        const SlowPoint sp = slow_point(P, e);
+        const SetDev& s = P.s[sp.si];
+        bool done = false;
+        for (int di = sp.di0; di < s.ndonor && !done; ++di) {
+            const int gd = s.donors[di];
+            const GridDev& g = G[gd];
+            const double3 p = point64(P, G, sp, gd);
+            const int64_t b = point_bin(g, p);
+            if (b < 0) continue;  // outside the bins' box: no cell of this grid holds the point
+            ff pf[3];
+            if (!point_ff(P, G, sp, di, pf)) {
+                pf[0] = split_double(p.x);
+                pf[1] = split_double(p.y);
+                pf[2] = split_double(p.z);
+            }
+            if (threadIdx.x == 0) {
+                ncand = 0;
+                found = 0;
+            }
+            __syncthreads();
+            const int32_t r0 = __ldg(g.bin_start + b), r1 = __ldg(g.bin_start + b + 1);
+            for (int32_t r = r0 + (int32_t)threadIdx.x; r < r1; r += kSlowThreads) {
+                uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
+                float xi[3];
+                if (exhaustive_filter(g, p, c, xi)) {
+                    int k = atomicAdd(&ncand, 1);
+                    if (k < kMaxCand) {
+                        cand[k] = c;
+                        cxi[k][0] = xi[0];
+                        cxi[k][1] = xi[1];
+                        cxi[k][2] = xi[2];
+                    }
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int64_t cell = -1;
+                double u = 0, v = 0, w = 0;
+                bool ok;
+                if (ncand <= kMaxCand) {
+                    uint32_t best = 0xFFFFFFFFu;
+                    double bu = 0, bv = 0, bw = 0;
+                    for (int k = lane; k < ncand; k += 32) {
+                        uint32_t c = cand[k];
+                        if (c >= best) continue;
+                        double a, bb, cc;
+                        if (contains_exact(g, c, pf, [&]() { return p; }, cxi[k][0], cxi[k][1], cxi[k][2], a, bb, cc)) {
+                            best = c;
+                            bu = a;
+                            bv = bb;
+                            bw = cc;
+                        }
+                    }
+                    uint32_t wbest = __reduce_min_sync(0xffffffffu, best);
+                    ok = wbest != 0xFFFFFFFFu;
+                    if (ok) {
+                        int src = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+                        cell = wbest;
+                        u = __shfl_sync(0xffffffffu, bu, src);
+                        v = __shfl_sync(0xffffffffu, bv, src);
+                        w = __shfl_sync(0xffffffffu, bw, src);
+                    }
+                } else {
+                    ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);  // more survivors than the list holds
+                }
+                if (ok && lane == 0) {
+                    found = 1;
+                    fcell = cell;
+                    fuvw[0] = u;
+                    fuvw[1] = v;
+                    fuvw[2] = w;
+                }
+            }
+            __syncthreads();
+            ++nfb;
+            if (found) {
+                if (threadIdx.x == 0)
+                    finish(P, G, sp, gd, fcell, fuvw[0], fuvw[1], fuvw[2],
+                           OVS_STATUS_FOUND | OVS_STATUS_REFINED | OVS_STATUS_FALLBACK);
+                done = true;
+                ++nref;
+            }
+            __syncthreads();
+        }
+        if (!done && threadIdx.x == 0) write_none(P, sp.t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+    }
+    if (P.stats && threadIdx.x == 0) {
+        if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
+        if (nfb) atomicAdd(P.counters + kCtrFallback, (unsigned long long)nfb);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev) {
-    cudaError_t err = cudaMemsetAsync(P.queue_count, 0, sizeof(uint32_t), st);
+    cudaError_t err = cudaMemsetAsync(P.queue_count, 0, 2 * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     int64_t blocks = (P.total + kAsmThreads - 1) / kAsmThreads;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
@@ -407,7 +668,8 @@ cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStrea
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    k_assemble_slow<<<152 * 4, kSlowThreads, 0, st>>>(P, dgrids);
+    k_slow_near<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+    k_slow_stuck<<<152, kSlowThreads, 0, st>>>(P, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

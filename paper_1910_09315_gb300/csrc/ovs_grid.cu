@@ -35,7 +35,21 @@ __device__ void block_reduce9(double v[9], double* out) {
     }
 }
 
-__global__ void __launch_bounds__(kBuildThreads) k_build_records(GridDev g, CellRec* rec, double* partials) {
+__device__ __forceinline__ void split_store(double v, float* hi, float* lo) {
+    float h = (float)v;
+    *hi = h;
+    *lo = (float)(v - (double)h);
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_build_records(GridDev g, CellRec* rec, float* xff,
+                                                                 double* partials) {
+    // node coordinates as FP32 pairs, SoA [xh | xl | yh | yl | zh | zl]
+    for (int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nd < g.nnodes;
+         nd += (int64_t)gridDim.x * blockDim.x) {
+        split_store(g.x[nd], xff + nd, xff + g.nnodes + nd);
+        split_store(g.y[nd], xff + 2 * g.nnodes + nd, xff + 3 * g.nnodes + nd);
+        split_store(g.z[nd], xff + 4 * g.nnodes + nd, xff + 5 * g.nnodes + nd);
+    }
     double v[9] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX, 0, 0, 0};
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < g.ncells;
          cell += (int64_t)gridDim.x * blockDim.x) {
@@ -54,7 +68,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_records(GridDev g, Cell
         for (int c = 0; c < 3; ++c) {
             double e1 = X[1][c] - X[0][c], e2 = X[2][c] - X[0][c], e3 = X[3][c] - X[0][c], e4 = X[4][c] - X[0][c],
                    e5 = X[5][c] - X[0][c], e6 = X[6][c] - X[0][c], e7 = X[7][c] - X[0][c];
-            r.x0[c] = X[0][c];
+            split_store(X[0][c], &r.x0h[c], &r.x0l[c]);
             r.a[c] = (float)e1;
             r.a[3 + c] = (float)e2;
             r.a[6 + c] = (float)e4;
@@ -79,17 +93,15 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_records(GridDev g, Cell
     block_reduce9(v, partials + 9 * blockIdx.x);
 }
 
-__global__ void k_reduce_partials(const double* partials, int nblocks, double* out9) {
-    // one thread, fixed order: the set-up reduction is tiny
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double v[9];
-    for (int q = 0; q < 9; ++q) v[q] = partials[q];
-    for (int b = 1; b < nblocks; ++b)
+__global__ void __launch_bounds__(kBuildThreads) k_reduce_partials(const double* partials, int nblocks, double* out9) {
+    // one block: thread t folds partials t, t + 256, ... in order, then the block reduction (fixed order)
+    double v[9] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += kBuildThreads)
         for (int q = 0; q < 9; ++q) {
             double o = partials[9 * b + q];
             v[q] = q < 3 ? fmin(v[q], o) : (q < 6 ? fmax(v[q], o) : v[q] + o);
         }
-    for (int q = 0; q < 9; ++q) out9[q] = v[q];
+    block_reduce9(v, out9);
 }
 
 __device__ __forceinline__ void cell_bin_range(const GridDev& g, const CellRec& r, int b0[3], int b1[3]) {
@@ -212,10 +224,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t* out, int64_t
 
 }  // namespace
 
-cudaError_t launch_build_records(const GridDev& g, CellRec* rec, double* partials, int nblocks, double* out9,
-                                 cudaStream_t st) {
-    k_build_records<<<nblocks, kBuildThreads, 0, st>>>(g, rec, partials);
-    k_reduce_partials<<<1, 32, 0, st>>>(partials, nblocks, out9);
+cudaError_t launch_build_records(const GridDev& g, CellRec* rec, float* xff, double* partials, int nblocks,
+                                 double* out9, cudaStream_t st) {
+    k_build_records<<<nblocks, kBuildThreads, 0, st>>>(g, rec, xff, partials);
+    k_reduce_partials<<<1, kBuildThreads, 0, st>>>(partials, nblocks, out9);
     return cudaGetLastError();
 }
 

@@ -2,9 +2,11 @@
 //
 // Data layout in HBM
 //   grid nodes   : caller's SoA FP64 x, y, z (i fastest), read only for exact FP64 decisions
-//   cell records : 128 B per cell (one L2 line): corner 0 in FP64 and the 7 monomial coefficient
-//                  vectors of the trilinear map relative to it in FP32, so one walk step is one
-//                  line fetch and the FP32 Newton needs only 3 FP64 subtractions
+//   cell records : 128 B per cell (one L2 line): corner 0 as an FP32 pair (hi + lo, ~48-bit) and the 7
+//                  monomial coefficient vectors of the trilinear map relative to it in FP32, so one walk
+//                  step is one line fetch and no FP64 instruction
+//   node pairs   : per node, x, y, z as FP32 pairs (hi + lo), SoA [xh|xl|yh|yl|zh|zl]: the receiver points
+//                  of the FP64-free fast path
 //   bins         : control cells of Sec. 2.2.5, CSR (start[nbins+1], cells[]) + lowest registered
 //                  cell per bin (cold-start cell)
 //   hints        : per receiver node, uint32 (donor grid << 27 | cell) of the last donor found
@@ -16,22 +18,25 @@
 
 namespace ovs {
 
-constexpr float kNearFace = 1e-4f;   // FP32 xi within this of a face -> decide in FP64
 constexpr float kAccept32 = 1e-4f;   // FP32 walk accepts a cell when xi is within this of [0,1]^3
 constexpr double kWinLo = -1e-10;    // donor window (lowest-id rule)
 constexpr double kWinHi = 1.0 + 1e-10;
 constexpr double kNewtonTol64 = 1e-13;
 constexpr int kNewtonMaxIt64 = 50;
 constexpr int kNewtonMaxIt32 = 8;
-constexpr float kNewtonTol32 = 2e-6f;
+// FP32 Newton stops once a step is below 1e-5: convergence is quadratic, so the local coordinates are then
+// accurate to ~1e-10 plus FP32 rounding (~1e-7), and a tighter test would stall at the rounding floor of
+// thin cells
+constexpr float kNewtonTol32 = 1e-5f;
 constexpr int kMaxJump = 4;
 constexpr uint32_t kNoHint = 0xFFFFFFFFu;
 constexpr int kCellBits = 27;
 
 // One cell: x(xi) = x0 + a1 xi + a2 eta + a3 zeta + a4 xi eta + a5 eta zeta + a6 xi zeta + a7 xi eta zeta
 struct __align__(16) CellRec {
-    double x0[3];
-    float a[21];  // a1.xyz, a2.xyz, ..., a7.xyz
+    float x0h[3];  // corner 0 = x0h + x0l (FP32 pair)
+    float x0l[3];
+    float a[21];   // a1.xyz, a2.xyz, ..., a7.xyz relative to corner 0
     float pad[5];
 };
 static_assert(sizeof(CellRec) == 128, "cell record must be one 128-byte line");
@@ -51,6 +56,7 @@ struct GridDev {
     const int32_t* bin_cells;
     const int32_t* bin_rep;    // lowest registered cell, -1 if empty
     uint32_t* hint;            // per node
+    const float* xff;          // node coordinates as FP32 pairs: 6 arrays of nnodes floats
     const void* mlp;           // guess network (device), or null
     double lo[3], hi[3];       // padded bounding box of the bins
     double inv_w[3];           // bins per unit length
@@ -67,6 +73,25 @@ struct MotionDev {
     int32_t pad;
 };
 
+// Receiver frame -> donor frame of a set's first donor, x_d = M x_r + t, as FP32 pairs (composed in FP64 on
+// the host: M = R_d^T R_r, t = R_d^T (c_r - c_d)).
+struct XfFF {
+    float Mh[9], Ml[9];
+    float th[3], tl[3];
+    int32_t identity;
+    int32_t pad;
+};
+
+// One grid's motion in FP32 for the FP32 velocity transform (c as an FP32 pair).
+struct MotionF {
+    float R[9];
+    float ch[3], cl[3];
+    float V[3];
+    float w[3];
+    int32_t identity;
+    int32_t pad;
+};
+
 struct SetDev {
     int32_t receiver;
     int32_t ndonor;
@@ -78,10 +103,45 @@ struct SetDev {
 
 struct SlowEntry {
     int32_t t;      // point index
-    int32_t di;     // position in the set's donor list to resume at
+    int32_t di;     // bits 0-7: position in the set's donor list to resume at; bits 8-13: near-face mask
+                    // (bit 8+m: neighbour at -1 on axis m, bit 11+m: neighbour at +1 on axis m)
     int32_t cell;   // FP32 walk result, -1 if the walk got stuck
     float xi[3];
 };
+
+// Bound on the error of the FP32 local coordinates of a point in a cell: FP32 rounding of the offsets and
+// coefficients (~6e-8 relative to the largest edge) amplified by the cell's aspect ratio and skew, with a
+// safety factor of 64, plus 1e-5.  Below this distance from a face the FP32 decision is not trusted.
+__device__ __forceinline__ float near_tau(const CellRec& r, float u, float v, float w) {
+    const float* a = r.a;
+    float Ju[3], Jv[3], Jw[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Ju[c] = a[c] + a[9 + c] * v + a[15 + c] * w + a[18 + c] * v * w;
+        Jv[c] = a[3 + c] + a[9 + c] * u + a[12 + c] * w + a[18 + c] * u * w;
+        Jw[c] = a[6 + c] + a[12 + c] * v + a[15 + c] * u + a[18 + c] * u * v;
+    }
+    float nu = sqrtf(Ju[0] * Ju[0] + Ju[1] * Ju[1] + Ju[2] * Ju[2]);
+    float nv = sqrtf(Jv[0] * Jv[0] + Jv[1] * Jv[1] + Jv[2] * Jv[2]);
+    float nw = sqrtf(Jw[0] * Jw[0] + Jw[1] * Jw[1] + Jw[2] * Jw[2]);
+    float det = Ju[0] * (Jv[1] * Jw[2] - Jv[2] * Jw[1]) + Ju[1] * (Jv[2] * Jw[0] - Jv[0] * Jw[2]) +
+                Ju[2] * (Jv[0] * Jw[1] - Jv[1] * Jw[0]);
+    float mx = fmaxf(nu, fmaxf(nv, nw)), mn = fminf(nu, fminf(nv, nw));
+    float t = 1e-5f + 4e-6f * (mx / mn) * (nu * nv * nw / fabsf(det));
+    return t < 0.25f ? t : 0.25f;  // also catches NaN (degenerate cell): everything counts as near
+}
+
+// near-face mask of FP32 local coordinates for threshold tau (see SlowEntry::di)
+__device__ __forceinline__ int near_mask(float u, float v, float w, float tau) {
+    int m = 0;
+    if (u < tau) m |= 1;
+    if (v < tau) m |= 2;
+    if (w < tau) m |= 4;
+    if (u > 1.f - tau) m |= 8;
+    if (v > 1.f - tau) m |= 16;
+    if (w > 1.f - tau) m |= 32;
+    return m;
+}
 
 enum Counter { kCtrPoints = 0, kCtrWalk, kCtrRefined, kCtrFallback, kCtrGuess, kNumCounters };
 
@@ -103,6 +163,7 @@ struct AsmParams {
     unsigned long long* counters;
     int32_t* err;
     SetDev s[OVS_MAX_SETS];
+    XfFF xf[OVS_MAX_SETS];
     MotionDev m[OVS_MAX_GRIDS];
 };
 
@@ -126,11 +187,85 @@ struct InterpParams {
     void* out[4];
     SetDev s[OVS_MAX_SETS];
     MotionDev m[OVS_MAX_GRIDS];
+    MotionF mf[OVS_MAX_GRIDS];
     FieldsDev fields[OVS_MAX_GRIDS];
 };
 
 // error bits of the device status word
 enum DevErr { kErrQueueOverflow = 1, kErrBadCell = 2, kErrBadNode = 4 };
+
+// ------------------------------------------------------------------------------------------------
+// FP32-pair ("double-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.  Error-free sum
+// (Knuth, TAOCP vol. 2, Sec. 4.2.2, "TwoSum") and product (Dekker 1971, here with a fused multiply-add);
+// written from those published definitions.  About 44-48 significant bits: enough to form point-minus-
+// corner offsets of 1e-10 relative accuracy without FP64 instructions.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ bool ff_finite(ff a) { return fabsf(a.hi) <= 3.0e38f && fabsf(a.lo) <= 3.0e38f; }
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+// quotient: q1 = a.hi / b.hi, then one correction from the remainder a - q1 b (Dekker 1971)
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    ff p = ff_mul(b, {q1, 0.f});
+    ff r = ff_sub(a, p);
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ float ff_abs_f(ff a) { return fabsf(__fadd_rn(a.hi, a.lo)); }
+
+// x_d = M x + t, all FP32 pairs
+__device__ __forceinline__ void xf_apply(const XfFF& X, const ff x[3], ff xd[3]) {
+    if (X.identity) {
+        xd[0] = x[0];
+        xd[1] = x[1];
+        xd[2] = x[2];
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ff acc = {X.th[c], X.tl[c]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc = ff_add(acc, ff_mul({X.Mh[3 * c + k], X.Ml[3 * c + k]}, x[k]));
+        xd[c] = acc;
+    }
+}
+
+__device__ __forceinline__ ff split_double(double v) {
+    float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
 
 // ------------------------------------------------------------------------------------------------
 // small helpers
@@ -162,16 +297,17 @@ __device__ __forceinline__ bool finite3(double3 p) {
     return isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
 }
 
+// cell ids are < 2^27: 32-bit arithmetic
 __device__ __forceinline__ void cell_ijk(const GridDev& g, int64_t cell, int& i, int& j, int& k) {
-    int64_t cij = (int64_t)g.C[0] * g.C[1];
-    k = (int)(cell / cij);
-    int64_t r = cell - (int64_t)k * cij;
-    j = (int)(r / g.C[0]);
-    i = (int)(r - (int64_t)j * g.C[0]);
+    uint32_t c = (uint32_t)cell, c0 = (uint32_t)g.C[0], c1 = (uint32_t)g.C[1];
+    uint32_t q = c / c0;
+    i = (int)(c - q * c0);
+    k = (int)(q / c1);
+    j = (int)(q - (uint32_t)k * c1);
 }
 
 __device__ __forceinline__ int64_t cell_id(const GridDev& g, int i, int j, int k) {
-    return (int64_t)i + (int64_t)g.C[0] * ((int64_t)j + (int64_t)g.C[1] * k);
+    return (int64_t)((uint32_t)i + (uint32_t)g.C[0] * ((uint32_t)j + (uint32_t)g.C[1] * (uint32_t)k));
 }
 
 // node id of corner (i+di, j+dj, k+dk) with periodic wrap
@@ -225,18 +361,19 @@ __device__ __forceinline__ void rec_box(const CellRec& r, double lo[3], double h
     double pad = 2e-6 * sqrt(d2) + 1e-300;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        lo[c] = r.x0[c] + (double)mn[c] - pad;
-        hi[c] = r.x0[c] + (double)mx[c] + pad;
+        double x0 = (double)r.x0h[c] + (double)r.x0l[c];
+        lo[c] = x0 + (double)mn[c] - pad;
+        hi[c] = x0 + (double)mx[c] + pad;
     }
 }
 
 // FP32 Newton on the monomial form.  Returns true if the last step was below tolerance.
 __device__ __forceinline__ bool newton32(const CellRec& r, float dx, float dy, float dz, float& u, float& v,
-                                         float& w) {
+                                         float& w, int maxit = kNewtonMaxIt32) {
     const float* a = r.a;
     bool conv = false;
 #pragma unroll 1
-    for (int it = 0; it < kNewtonMaxIt32; ++it) {
+    for (int it = 0; it < maxit; ++it) {
         float uv = u * v, vw = v * w, uw = u * w, uvw = uv * w;
         float F[3], Ju[3], Jv[3], Jw[3];
 #pragma unroll
@@ -335,11 +472,130 @@ __device__ __forceinline__ bool newton64_contains(const GridDev& g, int64_t cell
     return conv && u >= kWinLo && u <= kWinHi && v >= kWinLo && v <= kWinHi && w >= kWinLo && w <= kWinHi;
 }
 
+// The donor predicate in FP32-pair arithmetic (~44 significant bits) on the node coordinates' FP32 pairs,
+// started at (u,v,w): the same Newton iteration as newton64_contains, with steps <= 1e-12 as convergence.
+// Returns 1 (the cell holds the point), 0 (it does not) or -1 (undecided: not converged, or a local coordinate
+// within 1e-12 of a window bound, where only the FP64 predicate may decide).  Away from that band the FP64
+// definition gives the same answer, because the two iterations agree to far better than 1e-12.
+__device__ __forceinline__ int newton_ff(const GridDev& g, int64_t cell, const ff p[3], float u0, float v0, float w0,
+                                         double& u, double& v, double& w) {
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
+    const int64_t nn = g.nnodes;
+    ff X0[3], A[7][3], d[3];
+    ff E[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        int64_t nd = corner_node(g, i, j, k, a);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) E[a][c] = {__ldg(g.xff + 2 * c * nn + nd), __ldg(g.xff + (2 * c + 1) * nn + nd)};
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        X0[c] = E[0][c];
+        ff e1 = ff_sub(E[1][c], X0[c]), e2 = ff_sub(E[2][c], X0[c]), e3 = ff_sub(E[3][c], X0[c]),
+           e4 = ff_sub(E[4][c], X0[c]), e5 = ff_sub(E[5][c], X0[c]), e6 = ff_sub(E[6][c], X0[c]),
+           e7 = ff_sub(E[7][c], X0[c]);
+        A[0][c] = e1;
+        A[1][c] = e2;
+        A[2][c] = e4;
+        A[3][c] = ff_sub(ff_sub(e3, e1), e2);
+        A[4][c] = ff_sub(ff_sub(e6, e2), e4);
+        A[5][c] = ff_sub(ff_sub(e5, e1), e4);
+        A[6][c] = ff_add(ff_add(ff_add(ff_sub(ff_sub(ff_sub(e7, e3), e5), e6), e1), e2), e4);
+        d[c] = ff_sub(p[c], X0[c]);
+    }
+    ff U = {u0, 0.f}, V = {v0, 0.f}, W = {w0, 0.f};
+    bool conv = false;
+#pragma unroll 1
+    for (int it = 0; it < kNewtonMaxIt64; ++it) {
+        ff uv = ff_mul(U, V), vw = ff_mul(V, W), uw = ff_mul(U, W), uvw = ff_mul(uv, W);
+        ff F[3], Ju[3], Jv[3], Jw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ff f = ff_sub(ff_mul(A[0][c], U), d[c]);
+            f = ff_add(f, ff_mul(A[1][c], V));
+            f = ff_add(f, ff_mul(A[2][c], W));
+            f = ff_add(f, ff_mul(A[3][c], uv));
+            f = ff_add(f, ff_mul(A[4][c], vw));
+            f = ff_add(f, ff_mul(A[5][c], uw));
+            F[c] = ff_add(f, ff_mul(A[6][c], uvw));
+            Ju[c] = ff_add(ff_add(ff_add(A[0][c], ff_mul(A[3][c], V)), ff_mul(A[5][c], W)), ff_mul(A[6][c], vw));
+            Jv[c] = ff_add(ff_add(ff_add(A[1][c], ff_mul(A[3][c], U)), ff_mul(A[4][c], W)), ff_mul(A[6][c], uw));
+            Jw[c] = ff_add(ff_add(ff_add(A[2][c], ff_mul(A[4][c], V)), ff_mul(A[5][c], U)), ff_mul(A[6][c], uv));
+        }
+        ff cvw[3], cwu[3], cuv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+            cvw[c] = ff_sub(ff_mul(Jv[c1], Jw[c2]), ff_mul(Jv[c2], Jw[c1]));
+            cwu[c] = ff_sub(ff_mul(Jw[c1], Ju[c2]), ff_mul(Jw[c2], Ju[c1]));
+            cuv[c] = ff_sub(ff_mul(Ju[c1], Jv[c2]), ff_mul(Ju[c2], Jv[c1]));
+        }
+        ff det = ff_add(ff_add(ff_mul(Ju[0], cvw[0]), ff_mul(Ju[1], cvw[1])), ff_mul(Ju[2], cvw[2]));
+        if (!(fabsf(det.hi) > 0.f)) return 0;
+        ff nu = ff_add(ff_add(ff_mul(F[0], cvw[0]), ff_mul(F[1], cvw[1])), ff_mul(F[2], cvw[2]));
+        ff nv = ff_add(ff_add(ff_mul(F[0], cwu[0]), ff_mul(F[1], cwu[1])), ff_mul(F[2], cwu[2]));
+        ff nw = ff_add(ff_add(ff_mul(F[0], cuv[0]), ff_mul(F[1], cuv[1])), ff_mul(F[2], cuv[2]));
+        ff du = ff_neg(ff_div(nu, det)), dv = ff_neg(ff_div(nv, det)), dw = ff_neg(ff_div(nw, det));
+        U = ff_add(U, du);
+        V = ff_add(V, dv);
+        W = ff_add(W, dw);
+        float m = fmaxf(ff_abs_f(du), fmaxf(ff_abs_f(dv), ff_abs_f(dw)));
+        if (!(m < 1e30f) || !ff_finite(U) || !ff_finite(V) || !ff_finite(W)) return 0;
+        if (m <= 1e-12f) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) return -1;
+    // undecided band: 1e-12 plus the FP32-pair error of the point and corners (~4e-14 of the coordinates'
+    // magnitude) measured in local-coordinate units of the cell's shortest edge
+    float pm = fmaxf(fabsf(p[0].hi), fmaxf(fabsf(p[1].hi), fabsf(p[2].hi))) +
+               fmaxf(fabsf(X0[0].hi), fmaxf(fabsf(X0[1].hi), fabsf(X0[2].hi)));
+    float hmin = 3.4e38f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float n2 = A[q][0].hi * A[q][0].hi + A[q][1].hi * A[q][1].hi + A[q][2].hi * A[q][2].hi;
+        hmin = fminf(hmin, sqrtf(n2));
+    }
+    const float band = 1e-12f + 4e-14f * pm / hmin;
+    ff q[3] = {U, V, W};
+    bool in = true, amb = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float lo = __fadd_rn(q[c].hi, q[c].lo);                    // ~ xi (accurate near 0)
+        ff one = ff_sub(q[c], {1.f, 0.f});
+        float hi = __fadd_rn(one.hi, one.lo);                       // ~ xi - 1 (accurate near 1)
+        float dlo = lo - (float)kWinLo, dhi = hi - (float)(kWinHi - 1.0);
+        if (fabsf(dlo) <= band || fabsf(dhi) <= band) amb = true;
+        if (dlo < 0.f || dhi > 0.f) in = false;
+    }
+    if (amb) return -1;
+    u = (double)U.hi + (double)U.lo;
+    v = (double)V.hi + (double)V.lo;
+    w = (double)W.hi + (double)W.lo;
+    return in ? 1 : 0;
+}
+
+// The donor predicate: FP32-pair Newton, and the FP64 definition (on the FP64 point p64) only where the
+// FP32-pair iteration cannot decide.
+template <class P64>
+__device__ __forceinline__ bool contains_exact(const GridDev& g, int64_t cell, const ff p[3], const P64& p64, float u0,
+                                               float v0, float w0, double& u, double& v, double& w) {
+    int r = newton_ff(g, cell, p, u0, v0, w0, u, v, w);
+    if (r >= 0) return r == 1;
+    u = u0;
+    v = v0;
+    w = w0;
+    return newton64_contains(g, cell, p64(), u, v, w);
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // host-side launchers (defined in the .cu files)
-cudaError_t launch_build_records(const GridDev& g, CellRec* rec, double* partials, int nblocks, double* out9,
-                                 cudaStream_t st);
+cudaError_t launch_build_records(const GridDev& g, CellRec* rec, float* xff, double* partials, int nblocks,
+                                 double* out9, cudaStream_t st);
 cudaError_t launch_bin_count(const GridDev& g, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint32_t* block_sums, cudaStream_t st);
 cudaError_t launch_bin_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, int32_t* rep,

@@ -10,23 +10,133 @@ namespace {
 
 constexpr int kInterpThreads = 256;
 
-template <typename T>
-__device__ __forceinline__ void rot(const double R[9], const T a[3], T out[3]) {
+template <typename M, typename T>
+__device__ __forceinline__ void rot(const M R[9], const T a[3], T out[3]) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) out[r] = (T)R[3 * r] * a[0] + (T)R[3 * r + 1] * a[1] + (T)R[3 * r + 2] * a[2];
 }
 
-template <typename T>
-__device__ __forceinline__ void rotT(const double R[9], const T a[3], T out[3]) {
+template <typename M, typename T>
+__device__ __forceinline__ void rotT(const M R[9], const T a[3], T out[3]) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) out[r] = (T)R[r] * a[0] + (T)R[3 + r] * a[1] + (T)R[6 + r] * a[2];
 }
 
-template <typename T>
-__device__ __forceinline__ void cross_add(const double w[3], const T r[3], T acc[3], T sign) {
+template <typename M, typename T>
+__device__ __forceinline__ void cross_add(const M w[3], const T r[3], T acc[3], T sign) {
     acc[0] += sign * ((T)w[1] * r[2] - (T)w[2] * r[1]);
     acc[1] += sign * ((T)w[2] * r[0] - (T)w[0] * r[2]);
     acc[2] += sign * ((T)w[0] * r[1] - (T)w[1] * r[0]);
+}
+
+// FP32 velocity transform: positions from the receiver node's FP32 pair, motions from their FP32 copies.
+// r_r = x_in - c_r = R_r x_r;  r_d = x_in - c_d = R_r x_r + (c_r - c_d)  (inertial components)
+__device__ __forceinline__ void transform_f32(const InterpParams& P, const GridDev* __restrict__ G, const SetDev& s,
+                                              int64_t t, int gd, float ud[3]) {
+    const MotionF& md = P.mf[gd];
+    const MotionF& mr = P.mf[s.receiver];
+    float uin[3];
+    if (P.mode == OVS_VEL_ABSOLUTE) {
+        if (!md.identity) rot(md.R, ud, uin);
+        else uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
+        if (!mr.identity) rotT(mr.R, uin, ud);
+        else ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+        return;
+    }
+    const int32_t node = __ldg(s.node_ids + (t - s.begin));
+    const GridDev& gr = G[s.receiver];
+    const int64_t nn = gr.nnodes;
+    if (node < 0 || node >= nn) {
+        atomicOr(P.err, kErrBadNode);
+        ud[0] = ud[1] = ud[2] = 0.f;
+        return;
+    }
+    float xh[3], xl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xh[c] = __ldg(gr.xff + 2 * c * nn + node);
+        xl[c] = __ldg(gr.xff + (2 * c + 1) * nn + node);
+    }
+    float rr[3], rd[3];
+    if (mr.identity) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rd[c] = (xh[c] - md.ch[c]) + (xl[c] - md.cl[c]);
+            rr[c] = 0.f;
+        }
+    } else {
+        float xr[3] = {xh[0] + xl[0], xh[1] + xl[1], xh[2] + xl[2]};
+        rot(mr.R, xr, rr);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rd[c] = rr[c] + ((mr.ch[c] - md.ch[c]) + (mr.cl[c] - md.cl[c]));
+    }
+    if (!md.identity) {
+        rot(md.R, ud, uin);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uin[c] += md.V[c];
+        cross_add(md.w, rd, uin, 1.f);
+    } else {
+        uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
+    }
+    if (!mr.identity) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uin[c] -= mr.V[c];
+        cross_add(mr.w, rr, uin, -1.f);
+        rotT(mr.R, uin, ud);
+    } else {
+        ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+    }
+}
+
+// FP64 velocity transform (FP64 fields): positions from the receiver node's FP64 coordinates.
+__device__ __forceinline__ void transform_f64(const InterpParams& P, const GridDev* __restrict__ G, const SetDev& s,
+                                              int64_t t, int gd, double ud[3]) {
+    const MotionDev& md = P.m[gd];
+    const MotionDev& mr = P.m[s.receiver];
+    double uin[3];
+    if (P.mode == OVS_VEL_ABSOLUTE) {
+        if (!md.identity) rot(md.R, ud, uin);
+        else uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
+        if (!mr.identity) rotT(mr.R, uin, ud);
+        else ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+        return;
+    }
+    const int32_t node = __ldg(s.node_ids + (t - s.begin));
+    const GridDev& gr = G[s.receiver];
+    if (node < 0 || node >= gr.nnodes) {
+        atomicOr(P.err, kErrBadNode);
+        ud[0] = ud[1] = ud[2] = 0.0;
+        return;
+    }
+    double xr[3] = {__ldg(gr.x + node), __ldg(gr.y + node), __ldg(gr.z + node)};
+    double rr[3], rd[3];
+    if (mr.identity) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rd[c] = xr[c] - md.c[c];
+            rr[c] = 0.0;
+        }
+    } else {
+        rot(mr.R, xr, rr);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rd[c] = rr[c] + (mr.c[c] - md.c[c]);
+    }
+    if (!md.identity) {
+        rot(md.R, ud, uin);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uin[c] += md.V[c];
+        cross_add(md.w, rd, uin, 1.0);
+    } else {
+        uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
+    }
+    if (!mr.identity) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uin[c] -= mr.V[c];
+        cross_add(mr.w, rr, uin, -1.0);
+        rotT(mr.R, uin, ud);
+    } else {
+        ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+    }
 }
 
 template <typename T>
@@ -79,56 +189,11 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp(const __grid_constant
     if (P.mode != OVS_VEL_NONE) {
         const int si = find_set(P.s, P.nsets, t);
         const SetDev& s = P.s[si];
-        const MotionDev& md = P.m[gd];
-        const MotionDev& mr = P.m[s.receiver];
-        T ud[3] = {q[0], q[1], q[2]}, uin[3];
-        if (P.mode == OVS_VEL_ABSOLUTE) {
-            if (!md.identity) rot(md.R, ud, uin);
-            else uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
-            if (!mr.identity) rotT(mr.R, uin, ud);
-            else ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
+        T ud[3] = {q[0], q[1], q[2]};
+        if constexpr (sizeof(T) == 4) {
+            transform_f32(P, G, s, t, gd, ud);
         } else {
-            const int32_t node = __ldg(s.node_ids + (t - s.begin));
-            const GridDev& gr = G[s.receiver];
-            if (node < 0 || node >= gr.nnodes) {
-                atomicOr(P.err, kErrBadNode);
-#pragma unroll
-                for (int f = 0; f < 4; ++f) out[f][t] = (T)0;
-                return;
-            }
-            double3 xr = make_double3(__ldg(gr.x + node), __ldg(gr.y + node), __ldg(gr.z + node));
-            // r_r = x_in - c_r = R_r x_r; r_d = x_in - c_d = R_r x_r + (c_r - c_d)
-            T xrT[3] = {(T)xr.x, (T)xr.y, (T)xr.z};
-            T rr[3], rd[3];
-            if (mr.identity) {
-                rd[0] = (T)(xr.x - md.c[0]);
-                rd[1] = (T)(xr.y - md.c[1]);
-                rd[2] = (T)(xr.z - md.c[2]);
-                rr[0] = rr[1] = rr[2] = (T)0;
-            } else {
-                rot(mr.R, xrT, rr);
-                rd[0] = rr[0] + (T)(mr.c[0] - md.c[0]);
-                rd[1] = rr[1] + (T)(mr.c[1] - md.c[1]);
-                rd[2] = rr[2] + (T)(mr.c[2] - md.c[2]);
-            }
-            if (!md.identity) {
-                rot(md.R, ud, uin);
-                uin[0] += (T)md.V[0];
-                uin[1] += (T)md.V[1];
-                uin[2] += (T)md.V[2];
-                cross_add(md.w, rd, uin, (T)1);
-            } else {
-                uin[0] = ud[0], uin[1] = ud[1], uin[2] = ud[2];
-            }
-            if (!mr.identity) {
-                uin[0] -= (T)mr.V[0];
-                uin[1] -= (T)mr.V[1];
-                uin[2] -= (T)mr.V[2];
-                cross_add(mr.w, rr, uin, (T)-1);
-                rotT(mr.R, uin, ud);
-            } else {
-                ud[0] = uin[0], ud[1] = uin[1], ud[2] = uin[2];
-            }
+            transform_f64(P, G, s, t, gd, ud);
         }
         q[0] = ud[0];
         q[1] = ud[1];
