@@ -40,7 +40,7 @@ BYTES_INTERP = 176
 BYTES_POINT = BYTES_ASSEMBLE + BYTES_INTERP
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_assemble_cfg1.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1910_09315_gb300", "csrc", f) for f in
-                  ("ovs_assemble.cu", "ovs_internal.cuh")]
+                  ("ovs_assemble.cu", "ovs_internal.cuh", "ovs_fields.cuh")]
 WORKLOADS = {
     "cfg1": "moving ellipsoid: stretched curvilinear bg 128^3 + O-grid 96x64x64, 100 steps dt=1e-3, FP32 fields",
     "cfg0": "tiny: Cartesian bg 64^3 + rotated perturbed box 32^3, FP64 fields",
@@ -207,45 +207,61 @@ def run_ovs(args, rank, world, local):
         return {"grid": donors["grid"][:n], "cell": donors["cell"][:n], "xi": donors["xi"][:3 * n],
                 "status": donors["status"][:n], "xi_dtype": xi_dtype, "n": n}
 
-    def one_step(s, sets):
+    def one_step(s, sets, fused=True):
         m, fs = inputs[s]
         for gid, mo in zip(gids, m):
             ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
         n = sum(int(x[1].numel()) for x in sets)
         d = donors_view(n)
-        ctx.assemble(sets, donors=d)
-        ctx.interpolate(sets, d, fields, out=[o[:n] for o in outs])
+        if fused:
+            ctx.assemble_interpolate(sets, fields, donors=d, out=[o[:n] for o in outs])
+        else:
+            ctx.assemble(sets, donors=d)
+            ctx.interpolate(sets, d, fields, out=[o[:n] for o in outs])
         return n
 
     # warm-up (hints become warm exactly as in a time loop)
     for s in range(W):
         one_step(s, dev_sets[s])
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    for e in ev:
-        e.record(stream)  # torch creates the CUDA event on its first record
-    ovs.ovs_set_trace_events(ctx.ctx, ev)
+    def events(n):
+        out = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for e in out:
+            e.record(stream)  # torch creates the CUDA event on its first record
+        return out
+
+    def timed(fused: bool):
+        """K steps enqueued back to back (the host runs ahead as in a time loop); an L2 flush before each step
+        sits outside its events; one synchronisation at the end."""
+        e0, e1, tr = events(K), events(K), [events(5) for _ in range(K)]
+        torch.cuda.synchronize()
+        n = 0
+        for k, s in enumerate(range(W, W + K)):
+            flush.zero_()
+            ovs.ovs_set_trace_events(ctx.ctx, tr[k])
+            e0[k].record(stream)
+            n += one_step(s, dev_sets[s], fused=fused)
+            e1[k].record(stream)
+        torch.cuda.synchronize()
+        ovs.ovs_set_trace_events(ctx.ctx, [])
+        step = [e0[k].elapsed_time(e1[k]) for k in range(K)]
+        fast = [tr[k][0].elapsed_time(tr[k][1]) for k in range(K)]
+        slow = [tr[k][1].elapsed_time(tr[k][2]) for k in range(K)]
+        interp = [tr[k][3].elapsed_time(tr[k][4]) for k in range(K)]
+        return n, step, fast, slow, interp
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    step_ms, fast_ms, slow_ms, interp_ms, pts = [], [], [], [], 0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for s in range(W, W + K):
-        flush.zero_()
-        e0.record(stream)
-        pts += one_step(s, dev_sets[s])
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        fast_ms.append(ev[0].elapsed_time(ev[1]))
-        slow_ms.append(ev[1].elapsed_time(ev[2]))
-        interp_ms.append(ev[3].elapsed_time(ev[4]))
-    torch.cuda.synchronize()
+    pts, step_ms, fast_ms, slow_ms, interp_ms = timed(True)
     ck = clocks.stop()
-    ovs.ovs_set_trace_events(ctx.ctx, [])
     total_ms = float(np.sum(step_ms))
+    # the same steps through the two separate calls (ovs_assemble, then ovs_interpolate), for comparison
+    for s in range(W):
+        one_step(s, dev_sets[s], fused=False)
+    _, sep_ms, _, sep_slow, sep_int = timed(False)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
     host_out = [torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)]
     host_status = torch.empty(max_pts, dtype=torch.uint8).pin_memory()
@@ -291,17 +307,19 @@ def run_ovs(args, rank, world, local):
         "data": "synthetic (seeded generator, shapes of the stated workload)",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "points_per_step": pts_per_step,
                    "guess": "previous-donor hint + control-cell bins (plain)", "parallelism": f"replicas x{world}",
-                   "l2": "flushed (256 MB write) between timed steps", "launch": "k_assemble 256 thr/pt-thread"},
+                   "l2": "flushed (256 MB write) between timed steps", "timing": "per-step CUDA events, steps enqueued back to back",
+                   "call": "ovs_set_motion x2 + ovs_assemble_interpolate per step"},
         "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
-        "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_assemble_slow": float(np.mean(slow_ms)),
+        "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_slow_near || k_slow_stuck": float(np.mean(slow_ms)),
                                   "k_interp": float(np.mean(interp_ms))},
-        "roofline": {"kernel": "k_assemble", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                     "bytes_per_point": BYTES_ASSEMBLE,
-                     "traffic": (traffic * pts_per_step / pts_per_step) if traffic is not None else None},
+        "separate_calls": {"ms_per_step": float(np.mean(sep_ms)), "value": pts_all / (float(np.sum(sep_ms)) / 1e3)},
+        "roofline": {"kernel": "k_assemble", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)", "bytes_per_point": BYTES_ASSEMBLE,
+                     "traffic": traffic},
         "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                 "d2h_bytes_per_step": d2h // K},
-        "gpu_launches": 3 * K,
+        "gpu_launches": 4 * K,  # per step: k_assemble, k_slow_near, k_slow_stuck, k_interp
         "clocks": ck,
         "walk_stats": stats,
     }

@@ -181,6 +181,12 @@ int ovs_get_options(const ovs_ctx* ctx, ovs_options* opts);
  * donors of sets[0] first, then sets[1], ...  Updates the per-node hints of the receiver grids. */
 int ovs_assemble(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out);
 
+/* ovs_assemble followed by ovs_interpolate for the same sets, fields and motions, in one call (one time step
+ * of the method: donors, then the interpolated boundary values).  Writes the same donors and field values as
+ * the two calls (`out` as in ovs_assemble, `fields`/`fout` as in ovs_interpolate). */
+int ovs_assemble_interpolate(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                             const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout);
+
 /* Trilinear interpolation (Sec. 2.2.6) of u, v, w, p from the donors found by ovs_assemble for the same
  * sets, followed by the velocity transform of the options (Sec. 2.1 / Sec. 2.3.1), using the motions set
  * now.  `fields` is indexed by grid id (nfields = number of grids).  Points without a donor get 0. */

@@ -30,7 +30,7 @@ def _deps_newer(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "ovs_internal.cuh"), os.path.join(INCLUDE, "ovs.h")]
+    deps = [src, os.path.join(INCLUDE, "ovs.h")] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

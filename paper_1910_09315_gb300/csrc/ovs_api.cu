@@ -52,6 +52,10 @@ struct ovs_ctx {
     ovs_options opts;
     cudaEvent_t trace[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool tracing = false;
+    // a second stream and two events to run the two slow-path kernels side by side (fork / join on `stream`)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join = nullptr;
 };
 
 namespace {
@@ -248,6 +252,15 @@ int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
         delete c;
         return OVS_ERR_NO_DEVICE;
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->fork) cudaEventDestroy(c->fork);
+        delete c;
+        return OVS_ERR_CUDA;
+    }
     *out = c;
     return OVS_OK;
 }
@@ -256,6 +269,12 @@ int ovs_ctx_destroy(ovs_ctx* c) {
     if (!c) return OVS_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     delete c;
     return OVS_OK;
 }
@@ -476,7 +495,60 @@ int ovs_get_options(const ovs_ctx* c, ovs_options* o) {
     return OVS_OK;
 }
 
-int ovs_assemble(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out) {
+}  // extern "C"
+
+namespace {
+
+// fields checks shared by ovs_interpolate and ovs_assemble_interpolate
+int check_fields(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_fields* fields, int32_t nfields,
+                 const ovs_fields_out* out) {
+    if (!fields || nfields != c->ngrids) return fail(c, OVS_ERR_ARG, "fields must have one entry per grid (%d)", c->ngrids);
+    if (!out) return fail(c, OVS_ERR_ARG, "fields output is NULL");
+    if (out->dtype != OVS_F32 && out->dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "output dtype");
+    if (!out->u || !out->v || !out->w || !out->p) return fail(c, OVS_ERR_ARG, "output array is NULL");
+    // every possible donor of these sets must carry fields of the output dtype
+    for (int s = 0; s < nsets; ++s)
+        for (int d = 0; d < sets[s].n_donors; ++d) {
+            const ovs_fields& f = fields[sets[s].donors[d]];
+            if (!f.u || !f.v || !f.w || !f.p)
+                return fail(c, OVS_ERR_ARG, "donor grid %d has a NULL field", sets[s].donors[d]);
+            if (f.dtype != out->dtype)
+                return fail(c, OVS_ERR_ARG, "donor grid %d fields dtype %d != output dtype %d", sets[s].donors[d],
+                            f.dtype, out->dtype);
+        }
+    return OVS_OK;
+}
+
+void fill_interp(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* in,
+                 const ovs_fields* fields, const ovs_fields_out* out, int64_t total, InterpParams* P) {
+    P->nsets = nsets;
+    P->xi_f64 = in->xi_dtype == OVS_F64;
+    P->mode = c->opts.velocity_mode;
+    P->f64 = out->dtype == OVS_F64;
+    P->ngrids = c->ngrids;
+    P->err = c->d_err;
+    P->total = total;
+    P->in_grid = in->grid;
+    P->in_cell = in->cell;
+    P->in_xi = in->xi;
+    P->in_status = in->status;
+    P->out[0] = out->u;
+    P->out[1] = out->v;
+    P->out[2] = out->w;
+    P->out[3] = out->p;
+    fill_sets(sets, nsets, P->s);
+    memcpy(P->m, c->motion, sizeof P->m);
+    fill_motion_f32(c, P->mf);
+    for (int g = 0; g < c->ngrids; ++g) {
+        P->fields[g].f[0] = fields[g].u;
+        P->fields[g].f[1] = fields[g].v;
+        P->fields[g].f[2] = fields[g].w;
+        P->fields[g].f[3] = fields[g].p;
+    }
+}
+
+int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                  const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout) {
     if (!c) return OVS_ERR_ARG;
     if (!c->ws) return fail(c, OVS_ERR_STATE, "no workspace attached");
     int64_t total = 0;
@@ -484,6 +556,10 @@ int ovs_assemble(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     if (rc != OVS_OK) return rc;
     if (!out) return fail(c, OVS_ERR_ARG, "donors output is NULL");
     if (out->n < total) return fail(c, OVS_ERR_ARG, "donors capacity %lld < %lld points", (long long)out->n, (long long)total);
+    if (fout) {
+        rc = check_fields(c, sets, nsets, fields, nfields, fout);
+        if (rc != OVS_OK) return rc;
+    }
     if (total == 0) return OVS_OK;
     if (!out->grid || !out->cell || !out->xi || !out->status) return fail(c, OVS_ERR_ARG, "donors array is NULL");
     if (out->xi_dtype != OVS_F32 && out->xi_dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "xi_dtype");
@@ -511,10 +587,36 @@ int ovs_assemble(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     fill_sets(sets, nsets, P->s);
     fill_xforms(c, sets, nsets, P->xf);
     memcpy(P->m, c->motion, sizeof P->m);
-    cudaError_t e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr);
+    InterpParams* I = nullptr;
+    if (fout) {
+        I = new (std::nothrow) InterpParams();
+        if (!I) {
+            delete P;
+            return fail(c, OVS_ERR_ARG, "host allocation failed");
+        }
+        fill_interp(c, sets, nsets, out, fields, fout, total, I);
+    }
+    cudaError_t e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork,
+                                    c->join);
+    if (e == cudaSuccess && I) e = launch_interp(*I, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
     delete P;
+    delete I;
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble launch");
     return OVS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ovs_assemble(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out) {
+    return assemble_impl(c, sets, nsets, out, nullptr, 0, nullptr);
+}
+
+int ovs_assemble_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                             const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout) {
+    if (c && !fout) return fail(c, OVS_ERR_ARG, "fields output is NULL");
+    return assemble_impl(c, sets, nsets, out, fields, nfields, fout);
 }
 
 int ovs_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* in,
@@ -527,47 +629,13 @@ int ovs_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const
     if (!in || !out) return fail(c, OVS_ERR_ARG, "donors or output is NULL");
     if (in->n != total) return fail(c, OVS_ERR_ARG, "donors.n (%lld) != points (%lld)", (long long)in->n, (long long)total);
     if (total == 0) return OVS_OK;
-    if (!fields || nfields != c->ngrids) return fail(c, OVS_ERR_ARG, "fields must have one entry per grid (%d)", c->ngrids);
-    if (out->dtype != OVS_F32 && out->dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "output dtype");
-    if (!out->u || !out->v || !out->w || !out->p) return fail(c, OVS_ERR_ARG, "output array is NULL");
+    rc = check_fields(c, sets, nsets, fields, nfields, out);
+    if (rc != OVS_OK) return rc;
     if (!in->grid || !in->cell || !in->xi || !in->status) return fail(c, OVS_ERR_ARG, "donors array is NULL");
-    // every possible donor of these sets must carry fields of the output dtype
-    for (int s = 0; s < nsets; ++s)
-        for (int d = 0; d < sets[s].n_donors; ++d) {
-            const ovs_fields& f = fields[sets[s].donors[d]];
-            if (!f.u || !f.v || !f.w || !f.p)
-                return fail(c, OVS_ERR_ARG, "donor grid %d has a NULL field", sets[s].donors[d]);
-            if (f.dtype != out->dtype)
-                return fail(c, OVS_ERR_ARG, "donor grid %d fields dtype %d != output dtype %d", sets[s].donors[d],
-                            f.dtype, out->dtype);
-        }
     OVS_CUDA(c, cudaSetDevice(c->device));
     InterpParams* P = new (std::nothrow) InterpParams();
     if (!P) return fail(c, OVS_ERR_ARG, "host allocation failed");
-    P->nsets = nsets;
-    P->xi_f64 = in->xi_dtype == OVS_F64;
-    P->mode = c->opts.velocity_mode;
-    P->f64 = out->dtype == OVS_F64;
-    P->ngrids = c->ngrids;
-    P->err = c->d_err;
-    P->total = total;
-    P->in_grid = in->grid;
-    P->in_cell = in->cell;
-    P->in_xi = in->xi;
-    P->in_status = in->status;
-    P->out[0] = out->u;
-    P->out[1] = out->v;
-    P->out[2] = out->w;
-    P->out[3] = out->p;
-    fill_sets(sets, nsets, P->s);
-    memcpy(P->m, c->motion, sizeof P->m);
-    fill_motion_f32(c, P->mf);
-    for (int g = 0; g < c->ngrids; ++g) {
-        P->fields[g].f[0] = fields[g].u;
-        P->fields[g].f[1] = fields[g].v;
-        P->fields[g].f[2] = fields[g].w;
-        P->fields[g].f[3] = fields[g].p;
-    }
+    fill_interp(c, sets, nsets, in, fields, out, total, P);
     cudaError_t e = launch_interp(*P, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
     delete P;
     if (e != cudaSuccess) return cuda_fail(c, e, "interpolate launch");
@@ -707,7 +775,8 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     fill_sets(sets, nsets, P.s);
     fill_xforms(c, sets, nsets, P.xf);
     memcpy(P.m, c->motion, sizeof P.m);
-    cudaError_t e = launch_assemble(P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr);
+    cudaError_t e = launch_assemble(P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork,
+                                    c->join);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble (no-alloc) launch");
     return OVS_OK;
 }

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const _
         }
         if (bad) write_none(P, t, OVS_STATUS_BADINPUT);
         else if (!done && !slow) write_none(P, t, OVS_STATUS_ORPHAN);
+
     }
     // warp-aggregated append to the slow queues: points near a face (a candidate cell is known) from the front
     // of the buffer, stuck walks from the back.  Each point is queued at most once, so the two never meet.
@@ -342,19 +343,19 @@ __device__ bool neighbourhood_warp(const GridDev& g, const ff pf[3], const P64& 
 constexpr int kSlowThreads = 256;
 constexpr int kSlowWarps = kSlowThreads / 32;
 
-// Cheap rejections of one cell of an exhaustive search: its padded box (FP32, relative to its corner 0), the
+// Cheap rejections of one cell of an exhaustive search, all in FP32 from the point's FP32 pair (offsets to corner 0
+// as in the walk): its padded box, the
 // slabs along its three affine face normals (the cell, the convex hull of its corners, lies between the extreme
 // corner projections), and the FP32 Newton iteration from the cell centre (up to 24 steps) ending more than
 // 1e-3 outside [0,1]^3 (the same iteration in FP32 pairs or FP64 from the same start follows it to within
 // rounding, ~1e-5 in local coordinates for the cells accepted here, so it cannot end in the donor window).
 // On pass, xi holds the FP32 iterate, the start of the donor predicate.
-__device__ __forceinline__ bool exhaustive_filter(const GridDev& g, double3 p, uint32_t c, float xi[3]) {
+__device__ __forceinline__ bool exhaustive_filter(const GridDev& g, const ff pf[3], uint32_t c, float xi[3]) {
     CellRec rec;
     load_rec(g.rec, c, rec);
     float d[3];
-    d[0] = (float)(p.x - ((double)rec.x0h[0] + (double)rec.x0l[0]));
-    d[1] = (float)(p.y - ((double)rec.x0h[1] + (double)rec.x0l[1]));
-    d[2] = (float)(p.z - ((double)rec.x0h[2] + (double)rec.x0l[2]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = __fadd_rn(__fsub_rn(pf[k].hi, rec.x0h[k]), __fsub_rn(pf[k].lo, rec.x0l[k]));
     const float* A = rec.a;
     float E[8][3];
 #pragma unroll
@@ -426,7 +427,7 @@ __device__ bool exhaustive_warp(const GridDev& g, double3 p, const ff pf[3], int
         uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
         if (c >= best) continue;
         float xi[3];
-        if (!exhaustive_filter(g, p, c, xi)) continue;
+        if (!exhaustive_filter(g, pf, c, xi)) continue;
         double a, bb, cc;
         if (contains_exact(g, c, pf, [&]() { return p; }, xi[0], xi[1], xi[2], a, bb, cc)) {
             best = c;
@@ -497,6 +498,10 @@ __device__ __forceinline__ void finish(const AsmParams& P, const GridDev* G, con
     G[P.s[sp.si].receiver].hint[sp.node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
 }
 
+__device__ __forceinline__ void finish_none(const AsmParams& P, int64_t t) {
+    write_none(P, t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+}
+
 // Points near a face: one warp each, one lane per candidate cell.  A point whose candidates all fail (or a
 // later donor of its list) gets the warp-level exhaustive search.
 __global__ void __launch_bounds__(kSlowThreads) k_slow_near(const __grid_constant__ AsmParams P,
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_near(const __grid_constan
                 ++nref;
             }
         }
-        if (!done && lane == 0) write_none(P, sp.t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+        if (!done && lane == 0) finish_none(P, sp.t);
     }
     if (P.stats && lane == 0) {
         if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
@@ -589,7 +594,7 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const __grid_consta
             for (int32_t r = r0 + (int32_t)threadIdx.x; r < r1; r += kSlowThreads) {
                 uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
                 float xi[3];
-                if (exhaustive_filter(g, p, c, xi)) {
+                if (exhaustive_filter(g, pf, c, xi)) {
                     int k = atomicAdd(&ncand, 1);
                     if (k < kMaxCand) {
                         cand[k] = c;
@@ -649,7 +654,7 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const __grid_consta
             }
             __syncthreads();
         }
-        if (!done && threadIdx.x == 0) write_none(P, sp.t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+        if (!done && threadIdx.x == 0) finish_none(P, sp.t);
     }
     if (P.stats && threadIdx.x == 0) {
         if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
@@ -659,7 +664,8 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const __grid_consta
 
 }  // namespace
 
-cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev) {
+cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev,
+                            cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     cudaError_t err = cudaMemsetAsync(P.queue_count, 0, 2 * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     int64_t blocks = (P.total + kAsmThreads - 1) / kAsmThreads;
@@ -668,8 +674,18 @@ cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStrea
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    k_slow_near<<<152, kSlowThreads, 0, st>>>(P, dgrids);
-    k_slow_stuck<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+    if (side && fork && join) {
+        // the two slow-path kernels work on disjoint queues: run them side by side
+        if ((err = cudaEventRecord(fork, st)) != cudaSuccess) return err;
+        if ((err = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return err;
+        k_slow_stuck<<<152, kSlowThreads, 0, side>>>(P, dgrids);
+        k_slow_near<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+        if ((err = cudaEventRecord(join, side)) != cudaSuccess) return err;
+        if ((err = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return err;
+    } else {
+        k_slow_near<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+        k_slow_stuck<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+    }
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

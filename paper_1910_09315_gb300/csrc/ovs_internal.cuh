@@ -101,6 +101,10 @@ struct SetDev {
     int64_t n;
 };
 
+struct FieldsDev {
+    const void* f[4];
+};
+
 struct SlowEntry {
     int32_t t;      // point index
     int32_t di;     // bits 0-7: position in the set's donor list to resume at; bits 8-13: near-face mask
@@ -165,10 +169,6 @@ struct AsmParams {
     SetDev s[OVS_MAX_SETS];
     XfFF xf[OVS_MAX_SETS];
     MotionDev m[OVS_MAX_GRIDS];
-};
-
-struct FieldsDev {
-    const void* f[4];
 };
 
 struct InterpParams {
@@ -601,8 +601,11 @@ cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint3
 cudaError_t launch_bin_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, int32_t* rep,
                             cudaStream_t st);
 size_t scan_scratch_elems(int64_t n);
-// ev: 3 optional events (before fast kernel, after it, after the slow kernel); 2 for interpolation
-cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev);
+// ev: 3 optional events (before the fast kernel, after it, after the slow kernels); 2 for interpolation.
+// side/fork/join: a second stream and two events for running the two slow-path kernels concurrently (null:
+// everything on st).
+cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev,
+                            cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 cudaError_t launch_interp(const InterpParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev);
 
 }  // namespace ovs

@@ -47,7 +47,7 @@ EXPORTS = [
     "ovs_ctx_create", "ovs_ctx_destroy", "ovs_last_error", "ovs_set_stream", "ovs_workspace_size",
     "ovs_workspace_attach", "ovs_grid_workspace_size", "ovs_create_grid", "ovs_set_motion", "ovs_set_options",
     "ovs_get_options", "ovs_assemble", "ovs_interpolate", "ovs_sync", "ovs_get_stats", "ovs_reset_hints",
-    "ovs_set_trace_events", "ovs_assemble_noalloc",
+    "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -127,6 +127,8 @@ def load(path: Optional[str] = None):
         "ovs_reset_hints": [V],
         "ovs_set_trace_events": [V, ctypes.POINTER(V), I32],
         "ovs_assemble_noalloc": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors)],
+        "ovs_assemble_interpolate": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors),
+                                     ctypes.POINTER(ovs_fields), I32, ctypes.POINTER(ovs_fields_out)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -206,6 +208,11 @@ def ovs_get_options(ctx) -> ovs_options:
 
 def ovs_assemble(ctx, sets, nsets: int, donors: ovs_donors):
     _check(ctx, load().ovs_assemble(ctx, sets, int(nsets), ctypes.byref(donors)))
+
+
+def ovs_assemble_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
+    _check(ctx, load().ovs_assemble_interpolate(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
+                                                ctypes.byref(out)))
 
 
 def ovs_assemble_noalloc(ctx, sets, nsets: int, donors: ovs_donors):
@@ -357,8 +364,12 @@ class Context:
 
     def interpolate(self, sets, donors, fields, out=None):
         """fields: list indexed by grid id of (u, v, w, p) cuda tensors (or None)."""
+        farr, o, out = self._fields_structs(fields, donors["n"], out)
+        ovs_interpolate(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr, len(self.grids), o)
+        return out
+
+    def _fields_structs(self, fields, n, out):
         t = self.torch
-        n = donors["n"]
         dtype = None
         farr = (ovs_fields * len(self.grids))()
         for g, f in enumerate(fields):
@@ -372,8 +383,17 @@ class Context:
         o = ovs_fields_out()
         o.u, o.v, o.w, o.p = (a.data_ptr() for a in out)
         o.dtype = OVS_F64 if out[0].dtype == t.float64 else OVS_F32
-        ovs_interpolate(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr, len(self.grids), o)
-        return out
+        return farr, o, out
+
+    def assemble_interpolate(self, sets, fields, donors=None, out=None, xi_dtype: int = OVS_F32):
+        """ovs_assemble_interpolate: donors and interpolated fields in one call."""
+        n = sum(int(s[1].numel()) for s in sets)
+        if donors is None:
+            donors = self.alloc_donors(n, xi_dtype)
+        farr, o, out = self._fields_structs(fields, n, out)
+        ovs_assemble_interpolate(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr,
+                                 len(self.grids), o)
+        return donors, out
 
     def sync(self):
         ovs_sync(self.ctx)

@@ -209,3 +209,48 @@ def test_argument_errors_do_not_launch(torch_cuda):
         scene.ctx.assemble(bad)
     assert e.value.code == ovs.OVS_ERR_ARG
     scene.ctx.sync()
+
+
+# ----------------------------------------------------------------------------- fused assemble + interpolate
+def fused_step(scene, motions, fsets):
+    scene.set_motion(motions)
+    sets = scene.upload_sets(fsets)
+    d, out = scene.ctx.assemble_interpolate(sets, scene.fields, xi_dtype=scene.xi_dtype)
+    scene.ctx.sync()
+    return GpuScene.to_numpy(d, out)
+
+
+@pytest.mark.parametrize("cfg,xi_dtype", [(0, ovs.OVS_F64), (1, ovs.OVS_F32)])
+def test_fused_matches_oracle(torch_cuda, cfg, xi_dtype):
+    sc = gen.config(cfg)
+    ref = OracleScene(sc)
+    steps = [0] if cfg == 0 else [0, 1, 2, 3]
+    scene = None
+    for step in steps:
+        m = sc.motion(step)
+        fsets = sc.fringe_sets(step, m)
+        scene = scene or GpuScene(sc, max_points=800_000, xi_dtype=xi_dtype)
+        res = fused_step(scene, m, fsets)
+        parts = split(res, [len(s.node_ids) for s in fsets])
+        oref, frames = ref.step(m, fsets)
+        for k, (s, part, (od, oq)) in enumerate(zip(fsets, parts, oref)):
+            compare(part, od, oq, sc, frames, s.receiver, xi_dtype, label=f"fused cfg{cfg} step {step} set {k}")
+
+
+def test_fused_equals_separate_calls(torch_cuda):
+    sc = gen.config(1)
+    m = sc.motion(5)
+    fsets = sc.fringe_sets(5, m)
+    a = GpuScene(sc, max_points=800_000)
+    b = GpuScene(sc, max_points=800_000)
+    for step in range(5):  # same warm hints in both contexts
+        a.step(sc.motion(step), sc.fringe_sets(step), interpolate=False)
+        b.step(sc.motion(step), sc.fringe_sets(step), interpolate=False)
+    _, d, out = a.step(m, fsets)
+    sep = GpuScene.to_numpy(d, out)
+    fus = fused_step(b, m, fsets)
+    assert np.array_equal(sep["grid"], fus["grid"]) and np.array_equal(sep["cell"], fus["cell"])
+    assert np.array_equal(sep["status"], fus["status"])
+    assert np.array_equal(sep["xi"], fus["xi"], equal_nan=True)
+    # the same arithmetic on the same inputs, up to the compiler's contraction choices in two different kernels
+    assert np.allclose(sep["q"], fus["q"], rtol=1e-6, atol=1e-6)
