@@ -81,6 +81,7 @@ extern "C" {
 #define OVS_GUESS_HINT 0 /* start from the donor found for the same receiver node last call, else bins */
 #define OVS_GUESS_BINS 1 /* always start from the control-cell bin of the point */
 #define OVS_GUESS_MLP 2  /* body grids with a trained guess network: start there when no hint */
+#define OVS_GUESS_MLP_ONLY 3 /* body grids with a trained guess network: always start there (hints ignored) */
 
 typedef struct ovs_ctx ovs_ctx;
 
@@ -192,6 +193,45 @@ int ovs_assemble_interpolate(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t n
  * now.  `fields` is indexed by grid id (nfields = number of grids).  Points without a donor get 0. */
 int ovs_interpolate(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* in,
                     const ovs_fields* fields, int32_t nfields, const ovs_fields_out* out);
+
+/* ---- learned initial guess (not in the paper: the paper starts its walk from a control cell) ----
+ * Each body grid can carry a small network 3 -> H -> H -> 3 (SiLU) that maps normalised body-frame coordinates
+ * xn = (x - centre) * 2 / extent (centre and extent of the grid's bounding box) to normalised curvilinear
+ * coordinates ((i + xi)/Ci, (j + eta)/Cj, (k + zeta)/Ck).  With options.guess = OVS_GUESS_MLP, points without a
+ * usable hint start their walk at the cell the network points at (evaluated in BF16 on tensor cores with FP32
+ * accumulation); the exact in-cell test is unchanged, so donors do not depend on the network.
+ * Parameters (FP32): W1 [H x 3] row-major, b1 [H], W2 [H x H] row-major (W2[out][in]), b2 [H], W3 [3 x H],
+ * b3 [3]: H*H + 8*H + 3 values.  H is 32, 64 or 128. */
+typedef struct {
+    int32_t hidden;            /* H */
+    int32_t epochs;            /* passes over the samples */
+    int32_t batch;             /* samples per Adam step (beta 0.9 / 0.999, eps 1e-8) */
+    float lr;                  /* Adam learning rate at the first step */
+    float lr_final;            /* learning rate at the last step (cosine decay between them); 0: constant lr */
+    int32_t pad;
+    int64_t n_samples;
+    const int32_t* cells;      /* device [n_samples]: cell of each sample (the caller draws them) */
+    const float* xi;           /* device [3 n_samples] SoA: local coordinates in [0,1]^3 of each sample */
+    const float* init_params;  /* device: initial parameters (the caller draws them) */
+    void* scratch;             /* device scratch of ovs_train_workspace_size bytes (inputs and targets) */
+    size_t scratch_bytes;
+} ovs_train_desc;
+
+int ovs_guess_param_count(int32_t hidden, int64_t* count);
+int ovs_train_workspace_size(const ovs_train_desc* desc, size_t* bytes);
+/* Train grid_id's network on samples of the grid itself: input = the trilinear map of (cell, xi), target = the
+ * sample's normalised curvilinear coordinates; mean squared error, Adam.  Synchronises the stream; writes the
+ * mean loss of the last epoch to *final_loss (may be NULL). */
+int ovs_train_guess(ovs_ctx* ctx, int32_t grid_id, const ovs_train_desc* desc, float* final_loss);
+/* Checkpoint / restore of a grid's network (device FP32 parameters in the layout above). */
+int ovs_guess_get_params(ovs_ctx* ctx, int32_t grid_id, float* dparams, int32_t* hidden);
+int ovs_guess_set_params(ovs_ctx* ctx, int32_t grid_id, int32_t hidden, const float* dparams);
+/* Evaluate grid_id's network (BF16 tensor-core path) on n normalised inputs xn (device, 3n SoA) -> out (3n). */
+int ovs_guess_eval(ovs_ctx* ctx, int32_t grid_id, int64_t n, const float* xn, float* out);
+/* Mean squared error and its gradient (FP32, the training kernel) for parameters `params` on n samples with
+ * normalised inputs xn and targets (device, 3n SoA each): grads (device, param count) and *loss (device). */
+int ovs_mlp_loss_grad(ovs_ctx* ctx, int32_t hidden, int64_t n, const float* xn, const float* target,
+                      const float* params, float* grads, float* loss);
 
 /* Wait for the stream; returns OVS_ERR_DEVICE (and clears it) if a kernel flagged an error. */
 int ovs_sync(ovs_ctx* ctx);

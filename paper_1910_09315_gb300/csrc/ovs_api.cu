@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 
+#include "ovs_guess.cuh"
 #include "ovs_internal.cuh"
 
 using namespace ovs;
@@ -44,11 +45,14 @@ struct ovs_ctx {
     int32_t* d_err = nullptr;
     uint32_t* d_qcount = nullptr;
     SlowEntry* d_queue = nullptr;
+    GuessEntry* d_guess = nullptr;
+    uint32_t* d_gcount = nullptr;
     // grids
     int ngrids = 0;
     GridDev grids[OVS_MAX_GRIDS];
     GridHost gh[OVS_MAX_GRIDS];
     MotionDev motion[OVS_MAX_GRIDS];
+    int hidden[OVS_MAX_GRIDS] = {};  // width of each grid's trained guess network, 0 if none
     ovs_options opts;
     cudaEvent_t trace[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool tracing = false;
@@ -91,7 +95,7 @@ void identity_motion(MotionDev& m) {
 int64_t cells_axis(const ovs_grid_desc& d, int a) { return d.periodic[a] ? d.n[a] : d.n[a] - 1; }
 
 struct GridLayout {
-    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, xff, partials, scan, out9, total;
+    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, xff, mlp, partials, scan, out9, total;
     int64_t ncells, nnodes, nbins_max, reg_cap;
 };
 
@@ -116,6 +120,8 @@ GridLayout grid_layout(const ovs_grid_desc& d) {
     off = align_up(off + (size_t)L.nnodes * 4);
     L.xff = off;
     off = align_up(off + (size_t)L.nnodes * 6 * sizeof(float));
+    L.mlp = off;
+    off = align_up(off + mlp_region_bytes());
     L.partials = off;
     off = align_up(off + (size_t)kReduceBlocks * 9 * sizeof(double));
     L.scan = off;
@@ -296,6 +302,7 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     off = align_up(off + 4 * sizeof(int32_t));
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(GuessEntry));
     *bytes = off;
     return OVS_OK;
 }
@@ -318,8 +325,10 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     c->d_err = (int32_t*)(base + off);
     c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // two counters: near-face and stuck queues
+    c->d_gcount = (uint32_t*)(base + off + 3 * sizeof(int32_t));
     off = align_up(off + 4 * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
+    c->d_guess = (GuessEntry*)(base + off + align_up((size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry)));
     c->ws = dptr;
     c->ws_bytes = bytes;
     c->max_points = max_points;
@@ -371,7 +380,7 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
     g.bin_rep = (const int32_t*)(base + L.bin_rep);
     g.hint = (uint32_t*)(base + L.hint);
     g.xff = (const float*)(base + L.xff);
-    g.mlp = nullptr;
+    g.mlp = base + L.mlp;
     double* out9 = (double*)(base + L.out9);
     int nblk = (int)std::min<int64_t>(kReduceBlocks, (L.ncells + 255) / 256);
     OVS_CUDA(c, launch_build_records(g, (CellRec*)(base + L.rec), (float*)(base + L.xff),
@@ -431,6 +440,7 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
     }
     if (nreg == 0 && L.ncells > 0) return fail(c, OVS_ERR_WORKSPACE, "control-cell lists exceed the workspace");
     OVS_CUDA(c, cudaMemsetAsync(base + L.hint, 0xFF, (size_t)L.nnodes * 4, c->stream));
+    OVS_CUDA(c, cudaMemsetAsync(base + L.mlp, 0, sizeof(MlpHeader), c->stream));  // no guess network yet
     int id = c->ngrids;
     c->grids[id] = g;
     c->gh[id].desc = *d;
@@ -483,7 +493,7 @@ int ovs_set_options(ovs_ctx* c, const ovs_options* o) {
     if (!o) return fail(c, OVS_ERR_ARG, "options is NULL");
     if (o->velocity_mode < OVS_VEL_RELATIVE || o->velocity_mode > OVS_VEL_NONE)
         return fail(c, OVS_ERR_ARG, "velocity_mode %d", o->velocity_mode);
-    if (o->guess < OVS_GUESS_HINT || o->guess > OVS_GUESS_MLP) return fail(c, OVS_ERR_ARG, "guess %d", o->guess);
+    if (o->guess < OVS_GUESS_HINT || o->guess > OVS_GUESS_MLP_ONLY) return fail(c, OVS_ERR_ARG, "guess %d", o->guess);
     if (o->max_walk < 1 || o->max_walk > 1024) return fail(c, OVS_ERR_ARG, "max_walk %d (1..1024)", o->max_walk);
     c->opts = *o;
     return OVS_OK;
@@ -572,7 +582,9 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     P->nsets = nsets;
     P->xi_f64 = out->xi_dtype == OVS_F64;
     P->max_walk = c->opts.max_walk;
-    P->guess = c->opts.guess;
+    // the learned guess writes its cells into the hints, which the assembly then starts from
+    const bool mlp = c->opts.guess == OVS_GUESS_MLP || c->opts.guess == OVS_GUESS_MLP_ONLY;
+    P->guess = mlp ? OVS_GUESS_HINT : c->opts.guess;
     P->stats = c->opts.collect_stats;
     P->total = total;
     P->queue_cap = c->max_points;
@@ -596,8 +608,15 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
         }
         fill_interp(c, sets, nsets, out, fields, fout, total, I);
     }
-    cudaError_t e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork,
-                                    c->join);
+    cudaError_t e = cudaSuccess;
+    bool any_net = false;
+    for (int g = 0; g < c->ngrids; ++g) any_net = any_net || c->hidden[g] > 0;
+    if (mlp && any_net)
+        e = launch_guess(*P, c->d_grids, c->ngrids, c->hidden, c->opts.guess == OVS_GUESS_MLP_ONLY, c->d_guess,
+                         c->d_gcount, c->max_points, c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr,
+                         c->stream);
+    if (e == cudaSuccess)
+        e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork, c->join);
     if (e == cudaSuccess && I) e = launch_interp(*I, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
     delete P;
     delete I;
@@ -639,6 +658,163 @@ int ovs_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const
     cudaError_t e = launch_interp(*P, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
     delete P;
     if (e != cudaSuccess) return cuda_fail(c, e, "interpolate launch");
+    return OVS_OK;
+}
+
+int ovs_guess_param_count(int32_t hidden, int64_t* count) {
+    if (!count || (hidden != 32 && hidden != 64 && hidden != 128)) return OVS_ERR_ARG;
+    *count = mlp_param_count(hidden);
+    return OVS_OK;
+}
+
+int ovs_train_workspace_size(const ovs_train_desc* d, size_t* bytes) {
+    if (!d || !bytes || d->n_samples < 1) return OVS_ERR_ARG;
+    *bytes = align_up((size_t)d->n_samples * 6 * sizeof(float));
+    return OVS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int set_header(ovs_ctx* c, int gid, int H, int ready) {
+    MlpHeader h;
+    memset(&h, 0, sizeof h);
+    h.hidden = H;
+    h.ready = ready;
+    const GridDev& g = c->grids[gid];
+    for (int a = 0; a < 3; ++a) {
+        h.centre[a] = (float)(0.5 * (g.lo[a] + g.hi[a]));
+        h.inv_half[a] = (float)(2.0 / (g.hi[a] - g.lo[a]));
+    }
+    OVS_CUDA(c, cudaMemcpyAsync((void*)g.mlp, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return OVS_OK;
+}
+
+int check_grid(ovs_ctx* c, int32_t gid) {
+    if (!c) return OVS_ERR_ARG;
+    if (gid < 0 || gid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", gid);
+    return OVS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ovs_train_guess(ovs_ctx* c, int32_t gid, const ovs_train_desc* d, float* final_loss) {
+    int rc = check_grid(c, gid);
+    if (rc != OVS_OK) return rc;
+    if (!d) return fail(c, OVS_ERR_ARG, "training descriptor is NULL");
+    const int H = d->hidden;
+    if (H != 32 && H != 64 && H != 128) return fail(c, OVS_ERR_ARG, "hidden width %d (32, 64 or 128)", H);
+    if (d->n_samples < 1 || !d->cells || !d->xi || !d->init_params) return fail(c, OVS_ERR_ARG, "samples or initial parameters");
+    if (d->epochs < 1 || d->batch < 1 || !(d->lr > 0) || !(d->lr_final >= 0))
+        return fail(c, OVS_ERR_ARG, "epochs, batch and lr must be positive (lr_final >= 0)");
+    size_t need = 0;
+    ovs_train_workspace_size(d, &need);
+    if (!d->scratch || d->scratch_bytes < need)
+        return fail(c, OVS_ERR_WORKSPACE, "training scratch has %zu bytes, needs %zu", d->scratch_bytes, need);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    char* region = (char*)c->grids[gid].mlp;
+    const int np = mlp_param_count(H);
+    float* params = (float*)(region + kMlpParamsOffset);
+    float* m = (float*)(region + kMlpMOffset);
+    float* v = (float*)(region + kMlpVOffset);
+    float* grads = (float*)(region + kMlpGOffset);
+    float* loss = (float*)(region + kMlpLossOffset);
+    c->hidden[gid] = 0;
+    if ((rc = set_header(c, gid, H, 0)) != OVS_OK) return rc;
+    MlpHeader h;
+    OVS_CUDA(c, cudaMemcpy(&h, region, sizeof h, cudaMemcpyDeviceToHost));
+    OVS_CUDA(c, cudaMemcpyAsync(params, d->init_params, sizeof(float) * np, cudaMemcpyDeviceToDevice, c->stream));
+    OVS_CUDA(c, cudaMemsetAsync(m, 0, sizeof(float) * np, c->stream));
+    OVS_CUDA(c, cudaMemsetAsync(v, 0, sizeof(float) * np, c->stream));
+    OVS_CUDA(c, cudaMemsetAsync(grads, 0, sizeof(float) * np, c->stream));
+    const int64_t n = d->n_samples;
+    float* X = (float*)d->scratch;
+    float* T = X + 3 * n;
+    OVS_CUDA(c, launch_train_samples(c->grids[gid], h, d->cells, d->xi, n, X, T, c->stream));
+    int step = 0;
+    int64_t nb = 0;
+    const int64_t per_epoch = (n + d->batch - 1) / d->batch;
+    const double total_steps = (double)per_epoch * d->epochs;
+    for (int ep = 0; ep < d->epochs; ++ep) {
+        OVS_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), c->stream));
+        nb = 0;
+        for (int64_t off = 0; off < n; off += d->batch) {
+            const int64_t B = std::min<int64_t>(d->batch, n - off);
+            // cosine decay from lr to lr_final over all steps (constant when lr_final is 0)
+            double lr = d->lr;
+            if (d->lr_final > 0)
+                lr = d->lr_final + 0.5 * (d->lr - d->lr_final) * (1.0 + cos(M_PI * step / std::max(1.0, total_steps - 1)));
+            OVS_CUDA(c, launch_train_grad(H, params, X, T, n, off, B, grads, loss, 1.0f / (3.0f * (float)B), c->stream));
+            OVS_CUDA(c, launch_adam(params, grads, m, v, np, (float)lr, ++step, c->stream));
+            ++nb;
+        }
+    }
+    float lsum = 0;
+    OVS_CUDA(c, cudaMemcpyAsync(&lsum, loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    OVS_CUDA(c, launch_pack(params, H, region, c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if ((rc = set_header(c, gid, H, 1)) != OVS_OK) return rc;
+    c->hidden[gid] = H;
+    if (final_loss) *final_loss = lsum / (float)nb;
+    return OVS_OK;
+}
+
+int ovs_guess_set_params(ovs_ctx* c, int32_t gid, int32_t H, const float* dparams) {
+    int rc = check_grid(c, gid);
+    if (rc != OVS_OK) return rc;
+    if (H != 32 && H != 64 && H != 128) return fail(c, OVS_ERR_ARG, "hidden width %d (32, 64 or 128)", H);
+    if (!dparams) return fail(c, OVS_ERR_ARG, "parameters are NULL");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    char* region = (char*)c->grids[gid].mlp;
+    float* params = (float*)(region + kMlpParamsOffset);
+    c->hidden[gid] = 0;
+    if ((rc = set_header(c, gid, H, 0)) != OVS_OK) return rc;
+    OVS_CUDA(c, cudaMemcpyAsync(params, dparams, sizeof(float) * mlp_param_count(H), cudaMemcpyDeviceToDevice,
+                                c->stream));
+    OVS_CUDA(c, launch_pack(params, H, region, c->stream));
+    if ((rc = set_header(c, gid, H, 1)) != OVS_OK) return rc;
+    c->hidden[gid] = H;
+    return OVS_OK;
+}
+
+int ovs_guess_get_params(ovs_ctx* c, int32_t gid, float* dparams, int32_t* hidden) {
+    int rc = check_grid(c, gid);
+    if (rc != OVS_OK) return rc;
+    if (!hidden) return fail(c, OVS_ERR_ARG, "hidden is NULL");
+    *hidden = c->hidden[gid];
+    if (!c->hidden[gid]) return OVS_OK;
+    if (!dparams) return fail(c, OVS_ERR_ARG, "parameters are NULL");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    const char* region = (const char*)c->grids[gid].mlp;
+    OVS_CUDA(c, cudaMemcpyAsync(dparams, region + kMlpParamsOffset, sizeof(float) * mlp_param_count(c->hidden[gid]),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    return OVS_OK;
+}
+
+int ovs_guess_eval(ovs_ctx* c, int32_t gid, int64_t n, const float* xn, float* out) {
+    int rc = check_grid(c, gid);
+    if (rc != OVS_OK) return rc;
+    if (!c->hidden[gid]) return fail(c, OVS_ERR_STATE, "grid %d has no guess network", gid);
+    if (n < 0 || (n > 0 && (!xn || !out))) return fail(c, OVS_ERR_ARG, "inputs or outputs");
+    if (n == 0) return OVS_OK;
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    OVS_CUDA(c, launch_guess_eval(c->hidden[gid], c->grids[gid].mlp, xn, n, out, c->stream));
+    return OVS_OK;
+}
+
+int ovs_mlp_loss_grad(ovs_ctx* c, int32_t H, int64_t n, const float* xn, const float* target, const float* params,
+                      float* grads, float* loss) {
+    if (!c) return OVS_ERR_ARG;
+    if (H != 32 && H != 64 && H != 128) return fail(c, OVS_ERR_ARG, "hidden width %d (32, 64 or 128)", H);
+    if (n < 1 || !xn || !target || !params || !grads || !loss) return fail(c, OVS_ERR_ARG, "arguments");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    OVS_CUDA(c, cudaMemsetAsync(grads, 0, sizeof(float) * mlp_param_count(H), c->stream));
+    OVS_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), c->stream));
+    OVS_CUDA(c, launch_train_grad(H, params, xn, target, n, 0, n, grads, loss, 1.0f / (3.0f * (float)n), c->stream));
     return OVS_OK;
 }
 

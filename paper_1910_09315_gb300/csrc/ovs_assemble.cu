@@ -72,7 +72,12 @@ __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t&
             if (applied != 0) moved = true;
             q[m] = conv ? fminf(fmaxf(q[m] - (float)applied, -1.f), 2.f) : 0.5f;
         }
-        if (!moved) return kWalkStuck;
+        if (!moved) {
+            // converged and blocked by the grid's boundary: the point is outside (the exhaustive search decides);
+            // not converged yet: keep iterating in this cell from where Newton got to
+            if (conv) return kWalkStuck;
+            continue;
+        }
         i = nxt[0];
         j = nxt[1];
         k = nxt[2];

@@ -42,12 +42,15 @@ OVS_VEL_NONE = 2
 OVS_GUESS_HINT = 0
 OVS_GUESS_BINS = 1
 OVS_GUESS_MLP = 2
+OVS_GUESS_MLP_ONLY = 3
 
 EXPORTS = [
     "ovs_ctx_create", "ovs_ctx_destroy", "ovs_last_error", "ovs_set_stream", "ovs_workspace_size",
     "ovs_workspace_attach", "ovs_grid_workspace_size", "ovs_create_grid", "ovs_set_motion", "ovs_set_options",
     "ovs_get_options", "ovs_assemble", "ovs_interpolate", "ovs_sync", "ovs_get_stats", "ovs_reset_hints",
-    "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate",
+    "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate", "ovs_guess_param_count",
+    "ovs_train_workspace_size", "ovs_train_guess", "ovs_guess_get_params", "ovs_guess_set_params",
+    "ovs_guess_eval", "ovs_mlp_loss_grad",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -86,6 +89,14 @@ class ovs_options(ctypes.Structure):
 class ovs_stats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("refined", ctypes.c_int64),
                 ("fallback", ctypes.c_int64), ("guess_used", ctypes.c_int64)]
+
+
+class ovs_train_desc(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("lr_final", ctypes.c_float), ("pad", ctypes.c_int32),
+                ("n_samples", ctypes.c_int64), ("cells", ctypes.c_void_p),
+                ("xi", ctypes.c_void_p), ("init_params", ctypes.c_void_p), ("scratch", ctypes.c_void_p),
+                ("scratch_bytes", ctypes.c_size_t)]
 
 
 class OvsError(RuntimeError):
@@ -129,6 +140,13 @@ def load(path: Optional[str] = None):
         "ovs_assemble_noalloc": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors)],
         "ovs_assemble_interpolate": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors),
                                      ctypes.POINTER(ovs_fields), I32, ctypes.POINTER(ovs_fields_out)],
+        "ovs_guess_param_count": [I32, ctypes.POINTER(I64)],
+        "ovs_train_workspace_size": [ctypes.POINTER(ovs_train_desc), ctypes.POINTER(SZ)],
+        "ovs_train_guess": [V, I32, ctypes.POINTER(ovs_train_desc), ctypes.POINTER(ctypes.c_float)],
+        "ovs_guess_get_params": [V, I32, V, ctypes.POINTER(I32)],
+        "ovs_guess_set_params": [V, I32, I32, V],
+        "ovs_guess_eval": [V, I32, I64, V, V],
+        "ovs_mlp_loss_grad": [V, I32, I64, V, V, V, V, V],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -224,6 +242,49 @@ def ovs_assemble_noalloc(ctx, sets, nsets: int, donors: ovs_donors):
 def ovs_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
     _check(ctx, load().ovs_interpolate(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
                                        ctypes.byref(out)))
+
+
+def ovs_guess_param_count(hidden: int) -> int:
+    n = ctypes.c_int64()
+    rc = load().ovs_guess_param_count(int(hidden), ctypes.byref(n))
+    if rc != OVS_OK:
+        raise OvsError(rc, f"hidden width {hidden}")
+    return n.value
+
+
+def ovs_train_workspace_size(desc: ovs_train_desc) -> int:
+    b = ctypes.c_size_t()
+    rc = load().ovs_train_workspace_size(ctypes.byref(desc), ctypes.byref(b))
+    if rc != OVS_OK:
+        raise OvsError(rc, "invalid training descriptor")
+    return b.value
+
+
+def ovs_train_guess(ctx, grid_id: int, desc: ovs_train_desc) -> float:
+    loss = ctypes.c_float()
+    _check(ctx, load().ovs_train_guess(ctx, int(grid_id), ctypes.byref(desc), ctypes.byref(loss)))
+    return loss.value
+
+
+def ovs_guess_get_params(ctx, grid_id: int, dptr: int) -> int:
+    h = ctypes.c_int32()
+    _check(ctx, load().ovs_guess_get_params(ctx, int(grid_id), ctypes.c_void_p(dptr), ctypes.byref(h)))
+    return h.value
+
+
+def ovs_guess_set_params(ctx, grid_id: int, hidden: int, dptr: int):
+    _check(ctx, load().ovs_guess_set_params(ctx, int(grid_id), int(hidden), ctypes.c_void_p(dptr)))
+
+
+def ovs_guess_eval(ctx, grid_id: int, n: int, xn_ptr: int, out_ptr: int):
+    _check(ctx, load().ovs_guess_eval(ctx, int(grid_id), int(n), ctypes.c_void_p(xn_ptr), ctypes.c_void_p(out_ptr)))
+
+
+def ovs_mlp_loss_grad(ctx, hidden: int, n: int, xn_ptr: int, t_ptr: int, params_ptr: int, grads_ptr: int,
+                      loss_ptr: int):
+    _check(ctx, load().ovs_mlp_loss_grad(ctx, int(hidden), int(n), *[ctypes.c_void_p(p) for p in
+                                                                      (xn_ptr, t_ptr, params_ptr, grads_ptr,
+                                                                       loss_ptr)]))
 
 
 def ovs_sync(ctx):
@@ -394,6 +455,24 @@ class Context:
         ovs_assemble_interpolate(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr,
                                  len(self.grids), o)
         return donors, out
+
+    def train_guess(self, gid: int, cells, xi, init_params, hidden: int = 64, epochs: int = 5, batch: int = 8192,
+                    lr: float = 3e-3, lr_final: float = 0.0) -> float:
+        """Train grid gid's guess network (cells int32 [n], xi float32 [n,3] or [3n] SoA, init_params float32)."""
+        t = self.torch
+        cells = t.as_tensor(cells, dtype=t.int32).to(self.device).contiguous()
+        xi = t.as_tensor(xi, dtype=t.float32).to(self.device)
+        if xi.dim() == 2:
+            xi = xi.t().contiguous().reshape(-1)
+        init = t.as_tensor(init_params, dtype=t.float32).to(self.device).contiguous()
+        d = ovs_train_desc()
+        d.hidden, d.epochs, d.batch, d.lr, d.lr_final = int(hidden), int(epochs), int(batch), float(lr), float(lr_final)
+        d.n_samples = int(cells.numel())
+        d.cells, d.xi, d.init_params = cells.data_ptr(), xi.data_ptr(), init.data_ptr()
+        nbytes = ovs_train_workspace_size(d)
+        scratch = t.empty(nbytes, dtype=t.uint8, device=self.device)
+        d.scratch, d.scratch_bytes = scratch.data_ptr(), nbytes
+        return ovs_train_guess(self.ctx, gid, d)
 
     def sync(self):
         ovs_sync(self.ctx)
