@@ -262,6 +262,7 @@ def run_ovs(args, rank, world, local):
     for s in range(W):
         one_step(s, dev_sets[s], fused=False)
     _, sep_ms, _, sep_slow, sep_int = timed(False)
+    learned = learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, W, ovs, torch)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
     host_out = [torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)]
     host_status = torch.empty(max_pts, dtype=torch.uint8).pin_memory()
@@ -322,10 +323,66 @@ def run_ovs(args, rank, world, local):
         "gpu_launches": 4 * K,  # per step: k_assemble, k_slow_near, k_slow_stuck, k_interp
         "clocks": ck,
         "walk_stats": stats,
+        "learned_vs_plain": learned,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, inputs[W], args.cpu_sample)
     return line
+
+
+def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, W, ovs, torch):
+    """Train each body grid's guess network (3-64-64-3, 2M samples of the grid itself), then time the same step
+    with the plain start (previous donor, else control cell) and the learned one, cold (no previous donors) and
+    warm (a time loop)."""
+    import gen
+
+    out = {"network": "3-64-64-3 SiLU, BF16 tensor-core inference, trained by the library's kernels"}
+    t0 = time.perf_counter()
+    losses = []
+    for gi, g in enumerate(sc.grids):
+        if g.role != 1:
+            continue
+        cells, xi = gen.mlp_training_samples(config_index(args.workload), g, 2_000_000)
+        rng = np.random.default_rng(100 + gi)
+        H = 64
+        init = np.concatenate([rng.normal(0, 0.8, 3 * H), np.zeros(H), rng.normal(0, 1 / np.sqrt(H), H * H),
+                               np.zeros(H), rng.normal(0, 1 / np.sqrt(H), 3 * H), np.zeros(3)]).astype(np.float32)
+        losses.append(ctx.train_guess(gids[gi], cells, xi.astype(np.float32), init, hidden=H, epochs=60, batch=8192,
+                                      lr=3e-3, lr_final=1e-5))
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t0
+    out["train_mse"] = losses
+
+    def run(mode, steps, cold):
+        ctx.set_options(guess=mode, collect_stats=1)
+        ctx.stats(reset=True)
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in steps]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in steps]
+        for k, s in enumerate(steps):
+            flush.zero_()
+            if cold:
+                ovs.ovs_reset_hints(ctx.ctx)
+            e0[k].record(stream)
+            one_step(s, dev_sets[s])
+            e1[k].record(stream)
+        torch.cuda.synchronize()
+        st = ctx.stats(reset=True)
+        ctx.set_options(collect_stats=0)
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)])), st["walk_steps"] / len(steps)
+
+    cold_steps = list(range(W, W + 5))
+    warm = list(range(W, W + min(K, 50)))
+    res = {}
+    for name, mode, steps, cold in (("cold_plain_control_cell", ovs.OVS_GUESS_BINS, cold_steps, True),
+                                    ("cold_learned_network", ovs.OVS_GUESS_MLP_ONLY, cold_steps, True),
+                                    ("warm_plain_previous_donor", ovs.OVS_GUESS_HINT, warm, False),
+                                    ("warm_learned_previous_donor_else_network", ovs.OVS_GUESS_MLP, warm, False),
+                                    ("warm_learned_network_only", ovs.OVS_GUESS_MLP_ONLY, warm, False)):
+        ms, ws = run(mode, steps, cold)
+        res[name] = {"ms_per_step": ms, "walk_steps_per_step": ws}
+    ctx.set_options(guess=ovs.OVS_GUESS_HINT)
+    out.update(res)
+    return out
 
 
 # ----------------------------------------------------------------------------------------------------- oracle
