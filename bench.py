@@ -358,17 +358,29 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
         ctx.stats(reset=True)
         e0 = [torch.cuda.Event(enable_timing=True) for _ in steps]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in steps]
+        tr = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in steps]
+        for row in tr:
+            for e in row:
+                e.record(stream)
+        torch.cuda.synchronize()
         for k, s in enumerate(steps):
             flush.zero_()
             if cold:
                 ovs.ovs_reset_hints(ctx.ctx)
+            ovs.ovs_set_trace_events(ctx.ctx, tr[k])
             e0[k].record(stream)
             one_step(s, dev_sets[s])
             e1[k].record(stream)
         torch.cuda.synchronize()
+        ovs.ovs_set_trace_events(ctx.ctx, [])
         st = ctx.stats(reset=True)
         ctx.set_options(collect_stats=0)
-        return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)])), st["walk_steps"] / len(steps)
+        learned_mode = mode in (ovs.OVS_GUESS_MLP, ovs.OVS_GUESS_MLP_ONLY)
+        phases = {"guess_kernels_ms": float(np.mean([r[5].elapsed_time(r[6]) for r in tr])) if learned_mode else 0.0,
+                  "k_assemble_ms": float(np.mean([r[0].elapsed_time(r[1]) for r in tr])),
+                  "slow_kernels_ms": float(np.mean([r[1].elapsed_time(r[2]) for r in tr])),
+                  "fallbacks": st["fallback"] / len(steps)}
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)])), st["walk_steps"] / len(steps), phases
 
     cold_steps = list(range(W, W + 5))
     warm = list(range(W, W + min(K, 50)))
@@ -378,8 +390,8 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
                                     ("warm_plain_previous_donor", ovs.OVS_GUESS_HINT, warm, False),
                                     ("warm_learned_previous_donor_else_network", ovs.OVS_GUESS_MLP, warm, False),
                                     ("warm_learned_network_only", ovs.OVS_GUESS_MLP_ONLY, warm, False)):
-        ms, ws = run(mode, steps, cold)
-        res[name] = {"ms_per_step": ms, "walk_steps_per_step": ws}
+        ms, ws, ph = run(mode, steps, cold)
+        res[name] = {"ms_per_step": ms, "walk_steps_per_step": ws, **ph}
     ctx.set_options(guess=ovs.OVS_GUESS_HINT)
     out.update(res)
     return out

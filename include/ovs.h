@@ -243,7 +243,8 @@ int ovs_reset_hints(ovs_ctx* ctx);
 
 /* Tracing: record caller-created CUDA events (cudaEvent_t, NULL to skip one) on the context's stream at
  * fixed points of later calls: ev[0] before the fast assembly kernel, ev[1] after it, ev[2] after the
- * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it.
+ * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it, ev[5] before
+ * the learned-guess pass and ev[6] after it (OVS_GUESS_MLP / OVS_GUESS_MLP_ONLY only).
  * n = 0 (or ev = NULL) switches tracing off.  The events must outlive their use. */
 int ovs_set_trace_events(ovs_ctx* ctx, void* const* ev, int32_t n);
 

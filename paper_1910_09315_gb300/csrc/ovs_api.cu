@@ -54,7 +54,7 @@ struct ovs_ctx {
     MotionDev motion[OVS_MAX_GRIDS];
     int hidden[OVS_MAX_GRIDS] = {};  // width of each grid's trained guess network, 0 if none
     ovs_options opts;
-    cudaEvent_t trace[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t trace[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool tracing = false;
     // a second stream and two events to run the two slow-path kernels side by side (fork / join on `stream`)
     cudaStream_t side = nullptr;
@@ -303,6 +303,7 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     off = align_up(off + 4 * sizeof(int32_t));
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(GuessEntry));
+    off = align_up(off + sizeof(uint32_t) * OVS_MAX_GRIDS);
     *bytes = off;
     return OVS_OK;
 }
@@ -325,10 +326,12 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     c->d_err = (int32_t*)(base + off);
     c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // two counters: near-face and stuck queues
-    c->d_gcount = (uint32_t*)(base + off + 3 * sizeof(int32_t));
     off = align_up(off + 4 * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
-    c->d_guess = (GuessEntry*)(base + off + align_up((size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry)));
+    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    c->d_guess = (GuessEntry*)(base + off);
+    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(GuessEntry));
+    c->d_gcount = (uint32_t*)(base + off);  // one counter per donor grid's segment of the guess queue
     c->ws = dptr;
     c->ws_bytes = bytes;
     c->max_points = max_points;
@@ -611,10 +614,12 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     cudaError_t e = cudaSuccess;
     bool any_net = false;
     for (int g = 0; g < c->ngrids; ++g) any_net = any_net || c->hidden[g] > 0;
+    if (mlp && any_net && c->tracing && c->trace[5]) cudaEventRecord(c->trace[5], c->stream);
     if (mlp && any_net)
         e = launch_guess(*P, c->d_grids, c->ngrids, c->hidden, c->opts.guess == OVS_GUESS_MLP_ONLY, c->d_guess,
                          c->d_gcount, c->max_points, c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr,
                          c->stream);
+    if (mlp && any_net && c->tracing && c->trace[6]) cudaEventRecord(c->trace[6], c->stream);
     if (e == cudaSuccess)
         e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork, c->join);
     if (e == cudaSuccess && I) e = launch_interp(*I, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
@@ -853,8 +858,8 @@ int ovs_get_stats(ovs_ctx* c, ovs_stats* out, int reset) {
 
 int ovs_set_trace_events(ovs_ctx* c, void* const* ev, int32_t n) {
     if (!c) return OVS_ERR_ARG;
-    if (n < 0 || n > 5) return fail(c, OVS_ERR_ARG, "n = %d (0..5)", n);
-    for (int q = 0; q < 5; ++q) c->trace[q] = (ev && q < n) ? (cudaEvent_t)ev[q] : nullptr;
+    if (n < 0 || n > 7) return fail(c, OVS_ERR_ARG, "n = %d (0..7)", n);
+    for (int q = 0; q < 7; ++q) c->trace[q] = (ev && q < n) ? (cudaEvent_t)ev[q] : nullptr;
     c->tracing = ev && n > 0;
     return OVS_OK;
 }

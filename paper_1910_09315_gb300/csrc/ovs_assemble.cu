@@ -56,8 +56,9 @@ __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t&
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
             int jm = 0;
-            if (q[m] < -kAccept32) jm = max(-kMaxJump, (int)floorf(fmaxf(q[m], -1e6f)));
-            else if (q[m] > 1.f + kAccept32) jm = min(kMaxJump, (int)floorf(fminf(q[m], 1e6f)));
+            const int jmax = g.per[m] ? kMaxJumpPeriodic : kMaxJump;
+            if (q[m] < -kAccept32) jm = max(-jmax, (int)floorf(fmaxf(q[m], -1e6f)));
+            else if (q[m] > 1.f + kAccept32) jm = min(jmax, (int)floorf(fminf(q[m], 1e6f)));
             int t = cur[m] + jm;
             int applied;
             if (g.per[m]) {
@@ -198,18 +199,30 @@ __global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const _
                 if (h != kNoHint && (int)(h >> kCellBits) == gd) cell = h & ((1u << kCellBits) - 1);
                 if (cell >= g.ncells) cell = -1;
             }
-            if (cell < 0) {
-                // cold start: the lowest registered cell of the point's control cell.  Outside the bins' box
-                // or in an empty control cell (rep >= ncells), no cell of this grid can hold the point.
+            const bool from_hint = cell >= 0;
+            // cold start: the lowest registered cell of the point's control cell.  Outside the bins' box or in
+            // an empty control cell (rep >= ncells), no cell of this grid can hold the point.
+            auto control_cell = [&]() -> int64_t {
                 double3 p = make_double3((double)xd[0].hi + (double)xd[0].lo, (double)xd[1].hi + (double)xd[1].lo,
                                          (double)xd[2].hi + (double)xd[2].lo);
                 int64_t b = point_bin(g, p);
-                if (b < 0) continue;
-                cell = __ldg(g.bin_rep + b);
-                if (cell < 0 || cell >= g.ncells) continue;
+                if (b < 0) return -1;
+                int64_t rep = __ldg(g.bin_rep + b);
+                return (rep < 0 || rep >= g.ncells) ? -1 : rep;
+            };
+            if (cell < 0) {
+                cell = control_cell();
+                if (cell < 0) continue;
             }
             float u, v, w, tau = 0.25f;
-            int r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps);
+            int r = walk32(g, xd, cell, u, v, w, tau, from_hint ? min(P.max_walk, kHintWalk) : P.max_walk, steps);
+            if (r != kWalkFound && from_hint) {
+                // a walk from the previous donor or the learned guess that got stuck (on the grid's boundary, or
+                // after kHintWalk steps) starts again from the control cell before the exhaustive search
+                cell = control_cell();
+                if (cell < 0) continue;
+                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps);
+            }
             e.t = (int32_t)t;
             e.di = di;
             if (r == kWalkFound) {

@@ -182,12 +182,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// W2 fragments for mma.m16n8k16 with B[k][n] = W2[n][k]: per (n-tile, k-step, lane) two 32-bit registers:
-// b0 = rows k = 2t, 2t+1; b1 = rows k = 2t+8, 2t+9 (t = lane % 4), column n = lane / 4.
-__global__ void k_pack(const float* __restrict__ params, int H, float* __restrict__ fw, uint2* __restrict__ w2frag) {
+// B fragments for mma.m16n8k16 (B[k][n], k = 2t, 2t+1 in b0 and 2t+8, 2t+9 in b1, n = lane / 4, t = lane % 4):
+//   layer 2: B[k][n] = W2[n][k], per (n-tile, k-step, lane);  layer 3: B[k][n] = W3[n][k] for n < 3, else 0.
+__global__ void k_pack(const float* __restrict__ params, int H, float* __restrict__ fw, uint2* __restrict__ w2frag,
+                       uint2* __restrict__ w3frag) {
     const int NP = H * H + 8 * H + 3;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NP; q += gridDim.x * blockDim.x) fw[q] = params[q];
     const float* W2 = params + 4 * H;
+    const float* W3 = params + 5 * H + H * H;
     const int nt = H / 8, ks = H / 16;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt * ks * 32; q += gridDim.x * blockDim.x) {
         int lane = q % 32, kk = (q / 32) % ks, n8 = q / (32 * ks);
@@ -195,6 +197,18 @@ __global__ void k_pack(const float* __restrict__ params, int H, float* __restric
         int n = 8 * n8 + g, k0 = 16 * kk + 2 * t;
         w2frag[q] = make_uint2(pack_bf16(W2[n * H + k0], W2[n * H + k0 + 1]),
                                pack_bf16(W2[n * H + k0 + 8], W2[n * H + k0 + 9]));
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ks * 32; q += gridDim.x * blockDim.x) {
+        int lane = q % 32, kk = q / 32;
+        int g = lane >> 2, t = lane & 3, k0 = 16 * kk + 2 * t;
+        float w[4] = {0.f, 0.f, 0.f, 0.f};
+        if (g < 3) {
+            w[0] = W3[g * H + k0];
+            w[1] = W3[g * H + k0 + 1];
+            w[2] = W3[g * H + k0 + 8];
+            w[3] = W3[g * H + k0 + 9];
+        }
+        w3frag[q] = make_uint2(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]));
     }
 }
 
@@ -206,31 +220,57 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint2 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-// The network on 16 inputs held by one warp (row r of the tile: inputs xr[0..2] are read by the lanes that need
-// them from `xin`, rows >= rows_valid are zero); returns y for rows g and g+8 in lanes with t == 0.
+// One grid's network, staged in shared memory by a block
 template <int H>
-__device__ __forceinline__ void mlp_tile(const MlpHeader& hd, const float* __restrict__ fw,
-                                         const uint2* __restrict__ w2frag, const float xin[16][3], float y[2][3]) {
+struct MlpSmem {
+    float W1[3 * H];
+    float b1[H];
+    float b2[H];
+    float W3[3 * H];
+    float b3[4];
+    uint2 w2[(H / 8) * (H / 16) * 32];
+};
+
+template <int H>
+__device__ __forceinline__ void stage_mlp(MlpSmem<H>& S, const void* region) {
+    const float* fw = (const float*)((const char*)region + kMlpFwOffset);
+    const uint2* w2 = (const uint2*)((const char*)region + kMlpFragOffset);
+    for (int q = threadIdx.x; q < 3 * H; q += blockDim.x) {
+        S.W1[q] = fw[q];
+        S.W3[q] = fw[5 * H + H * H + q];
+    }
+    for (int q = threadIdx.x; q < H; q += blockDim.x) {
+        S.b1[q] = fw[3 * H + q];
+        S.b2[q] = fw[4 * H + H * H + q];
+    }
+    if (threadIdx.x < 3) S.b3[threadIdx.x] = fw[8 * H + H * H + threadIdx.x];
+    for (int q = threadIdx.x; q < (H / 8) * (H / 16) * 32; q += blockDim.x) S.w2[q] = w2[q];
+}
+
+// The network on a tile of 16 inputs (xin, one row per point) held by one warp.  Layer 1 in FP32 straight into
+// the A fragments of layer 2; layer 2 on tensor cores (BF16 operands, FP32 accumulation); layer 3 in FP32 from
+// the accumulator fragments, reduced over the 4 lanes of a row group.  On return, lanes with t = lane % 4 == 0
+// hold y for rows g and g + 8 (g = lane / 4).
+template <int H>
+__device__ __forceinline__ void mlp_tile(const MlpSmem<H>& S, const float (*xin)[3], float y[2][3]) {
     const int lane = (int)lane_id(), g = lane >> 2, t = lane & 3;
-    const float* W1 = fw;
-    const float* b1 = W1 + 3 * H;
-    const float* b2 = b1 + H + H * H;
-    const float* W3 = b2 + H;
-    const float* b3 = W3 + 3 * H;
     constexpr int KS = H / 16, NT = H / 8;
-    // layer 1 straight into A fragments (rows g, g+8; columns 16kk + 2t + {0,1,8,9}), SiLU, BF16
+    float xr[2][3];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xr[rr][c] = xin[g + 8 * rr][c];
     uint32_t A[KS][4];
 #pragma unroll
     for (int kk = 0; kk < KS; ++kk) {
         float h[2][4];
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const float* xr = xin[g + 8 * rr];
+        for (int e = 0; e < 4; ++e) {
+            const int col = 16 * kk + 2 * t + (e & 1) + (e >> 1) * 8;
+            const float w0 = S.W1[3 * col], w1 = S.W1[3 * col + 1], w2 = S.W1[3 * col + 2], bb = S.b1[col];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                int col = 16 * kk + 2 * t + (e & 1) + (e >> 1) * 8;
-                float z = __ldg(b1 + col) + __ldg(W1 + 3 * col) * xr[0] + __ldg(W1 + 3 * col + 1) * xr[1] +
-                          __ldg(W1 + 3 * col + 2) * xr[2];
+            for (int rr = 0; rr < 2; ++rr) {
+                float z = bb + w0 * xr[rr][0] + w1 * xr[rr][1] + w2 * xr[rr][2];
                 h[rr][e] = z / (1.f + __expf(-z));
             }
         }
@@ -239,21 +279,22 @@ __device__ __forceinline__ void mlp_tile(const MlpHeader& hd, const float* __res
         A[kk][2] = pack_bf16(h[0][2], h[0][3]);
         A[kk][3] = pack_bf16(h[1][2], h[1][3]);
     }
-    // layer 2 on tensor cores, then SiLU and layer 3 partial sums over this lane's columns
-    float part[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    // layer 2 on tensor cores; SiLU and the 64 -> 3 output layer in FP32 (its weights are large and its terms
+    // cancel, so BF16 operands there would cost the guess its accuracy)
+    float part[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
     for (int n8 = 0; n8 < NT; ++n8) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int kk = 0; kk < KS; ++kk) mma_bf16(c, A[kk], __ldg(w2frag + (n8 * KS + kk) * 32 + lane));
+        for (int kk = 0; kk < KS; ++kk) mma_bf16(c, A[kk], S.w2[(n8 * KS + kk) * 32 + lane]);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            int col = 8 * n8 + 2 * t + (e & 1);
-            float z = c[e] + __ldg(b2 + col);
+            const int col = 8 * n8 + 2 * t + (e & 1);
+            float z = c[e] + S.b2[col];
             float h2 = z / (1.f + __expf(-z));
-            int rr = e >> 1;
+            const int rr = e >> 1;
 #pragma unroll
-            for (int o = 0; o < 3; ++o) part[rr][o] += __ldg(W3 + o * H + col) * h2;
+            for (int o = 0; o < 3; ++o) part[rr][o] += S.W3[o * H + col] * h2;
         }
     }
 #pragma unroll
@@ -263,16 +304,18 @@ __device__ __forceinline__ void mlp_tile(const MlpHeader& hd, const float* __res
             float v = part[rr][o];
             v += __shfl_xor_sync(0xffffffffu, v, 1);
             v += __shfl_xor_sync(0xffffffffu, v, 2);
-            y[rr][o] = v + __ldg(b3 + o);
+            y[rr][o] = v + S.b3[o];
         }
 }
 
-// network evaluation on arbitrary inputs (normalised), for tests and direct use
+// network evaluation on arbitrary normalised inputs (tests and direct use)
 template <int H>
-__global__ void __launch_bounds__(128) k_guess_eval(MlpHeader hd, const float* __restrict__ fw,
-                                                    const uint2* __restrict__ w2frag, const float* __restrict__ xn,
+__global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ region, const float* __restrict__ xn,
                                                     int64_t n, float* __restrict__ out) {
+    __shared__ MlpSmem<H> S;
     __shared__ float xs[4][16][3];
+    stage_mlp<H>(S, region);
+    __syncthreads();
     const int w = threadIdx.x >> 5, lane = (int)lane_id();
     const int64_t tiles = (n + 15) / 16;
     for (int64_t tile = blockIdx.x * 4 + w; tile < tiles; tile += (int64_t)gridDim.x * 4) {
@@ -283,7 +326,7 @@ __global__ void __launch_bounds__(128) k_guess_eval(MlpHeader hd, const float* _
         }
         __syncwarp();
         float y[2][3];
-        mlp_tile<H>(hd, fw, w2frag, xs[w], y);
+        mlp_tile<H>(S, xs[w], y);
         if ((lane & 3) == 0) {
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
@@ -297,17 +340,18 @@ __global__ void __launch_bounds__(128) k_guess_eval(MlpHeader hd, const float* _
     }
 }
 
-// points without a usable hint whose first donor has a trained network -> guess queue
+// points without a usable hint whose first donor has a trained network -> that grid's segment of the queue
 __global__ void __launch_bounds__(256) k_guess_select(const __grid_constant__ AsmParams P,
                                                       const GridDev* __restrict__ G, GuessEntry* __restrict__ queue,
-                                                      uint32_t* __restrict__ count, int64_t cap, int always) {
+                                                      uint32_t* __restrict__ counts, GuessSeg seg, int always) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool want = false;
+    int gd = -1;
     GuessEntry e;
     if (t < P.total) {
         const int si = find_set(P.s, P.nsets, t);
         const SetDev& s = P.s[si];
-        const int gd = s.donors[0];
+        gd = s.donors[0];
         const GridDev& g = G[gd];
         const MlpHeader* hd = (const MlpHeader*)g.mlp;
         if (hd && hd->ready) {
@@ -331,68 +375,63 @@ __global__ void __launch_bounds__(256) k_guess_select(const __grid_constant__ As
                         inside = inside && v >= (float)g.lo[c] && v <= (float)g.hi[c];
                         e.x[c] = (v - hd->centre[c]) * hd->inv_half[c];
                     }
-                    e.t = (int32_t)t;
+                    e.node = node;
+                    e.receiver = s.receiver;
+                    e.pad = 0;
                     want = inside;
                 }
             }
         }
     }
-    unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (mask) {
-        const unsigned lane = lane_id();
-        int leader = __ffs(mask) - 1;
-        uint32_t base = 0;
-        if ((int)lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (want) {
-            uint32_t idx = base + __popc(mask & ((1u << lane) - 1u));
-            if (idx < cap) queue[idx] = e;
-        }
-    }
+    // one atomic per (warp, donor grid)
+    const unsigned lane = lane_id();
+    const unsigned group = __match_any_sync(0xffffffffu, want ? gd : -1);
+    const int leader = __ffs(group) - 1;
+    uint32_t base = 0;
+    if (want && (int)lane == leader) base = atomicAdd(counts + gd, (uint32_t)__popc(group));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) queue[seg.off[gd] + base + __popc(group & ((1u << lane) - 1u))] = e;
 }
 
-// guess queue -> hints (the network's cell), 16 points per warp
+// one donor grid's segment of the queue -> hints (the network's cell), 16 points per warp
 template <int H>
-__global__ void __launch_bounds__(128) k_guess_mma(const __grid_constant__ AsmParams P, const GridDev* __restrict__ G,
-                                                   const GuessEntry* __restrict__ queue,
-                                                   const uint32_t* __restrict__ count, int64_t cap, int gd,
+__global__ void __launch_bounds__(128) k_guess_mma(const GridDev* __restrict__ G, int gd,
+                                                   const GuessEntry* __restrict__ queue, const uint32_t* __restrict__ count,
                                                    unsigned long long* __restrict__ used) {
+    __shared__ MlpSmem<H> S;
     __shared__ float xs[4][16][3];
-    __shared__ int32_t ts[4][16];
+    __shared__ int32_t nodes[4][16], recs[4][16];
     const GridDev& g = G[gd];
-    const MlpHeader hd = *(const MlpHeader*)g.mlp;
-    const float* fw = (const float*)((const char*)g.mlp + kMlpFwOffset);
-    const uint2* w2frag = (const uint2*)((const char*)g.mlp + kMlpFragOffset);
+    stage_mlp<H>(S, g.mlp);
+    __syncthreads();
     const int w = threadIdx.x >> 5, lane = (int)lane_id();
-    const int64_t n = min((int64_t)*count, cap);
+    const int64_t n = *count;
     const int64_t tiles = (n + 15) / 16;
     unsigned nused = 0;
     for (int64_t tile = blockIdx.x * 4 + w; tile < tiles; tile += (int64_t)gridDim.x * 4) {
         if (lane < 16) {
             int64_t q = tile * 16 + lane;
-            bool ok = false;
             if (q < n) {
                 const GuessEntry e = queue[q];
-                const int si = find_set(P.s, P.nsets, e.t);
-                ok = P.s[si].donors[0] == gd;  // this launch handles donor grid gd
-                ts[w][lane] = ok ? e.t : -1;
+                nodes[w][lane] = e.node;
+                recs[w][lane] = e.receiver;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) xs[w][lane][c] = ok ? e.x[c] : 0.f;
+                for (int c = 0; c < 3; ++c) xs[w][lane][c] = e.x[c];
             } else {
-                ts[w][lane] = -1;
+                nodes[w][lane] = -1;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) xs[w][lane][c] = 0.f;
             }
         }
         __syncwarp();
         float y[2][3];
-        mlp_tile<H>(hd, fw, w2frag, xs[w], y);
+        mlp_tile<H>(S, xs[w], y);
         if ((lane & 3) == 0) {
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 const int row = (lane >> 2) + 8 * rr;
-                const int32_t t = ts[w][row];
-                if (t < 0) continue;
+                const int32_t node = nodes[w][row];
+                if (node < 0) continue;
                 int ijk[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -406,10 +445,7 @@ __global__ void __launch_bounds__(128) k_guess_mma(const __grid_constant__ AsmPa
                     }
                     ijk[c] = ci;
                 }
-                const int si = find_set(P.s, P.nsets, t);
-                const SetDev& s = P.s[si];
-                const int32_t node = __ldg(s.node_ids + (t - s.begin));
-                G[s.receiver].hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell_id(g, ijk[0], ijk[1], ijk[2]);
+                G[recs[w][row]].hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell_id(g, ijk[0], ijk[1], ijk[2]);
                 ++nused;
             }
         }
@@ -460,44 +496,50 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr
 cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t st) {
     float* fw = (float*)((char*)region + kMlpFwOffset);
     uint2* w2 = (uint2*)((char*)region + kMlpFragOffset);
-    k_pack<<<64, 256, 0, st>>>(params, H, fw, w2);
+    uint2* w3 = (uint2*)((char*)region + kMlpW3FragOffset);
+    k_pack<<<64, 256, 0, st>>>(params, H, fw, w2, w3);
     return cudaGetLastError();
 }
 
 cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_t n, float* out, cudaStream_t st) {
-    MlpHeader hd = {};
-    const float* fw = (const float*)((const char*)region + kMlpFwOffset);
-    const uint2* w2 = (const uint2*)((const char*)region + kMlpFragOffset);
     int64_t tiles = (n + 15) / 16;
     unsigned blocks = (unsigned)std::min<int64_t>((tiles + 3) / 4, 152 * 8);
     if (blocks == 0) return cudaSuccess;
     switch (H) {
-        case 32: k_guess_eval<32><<<blocks, 128, 0, st>>>(hd, fw, w2, xn, n, out); break;
-        case 64: k_guess_eval<64><<<blocks, 128, 0, st>>>(hd, fw, w2, xn, n, out); break;
-        case 128: k_guess_eval<128><<<blocks, 128, 0, st>>>(hd, fw, w2, xn, n, out); break;
+        case 32: k_guess_eval<32><<<blocks, 128, 0, st>>>(region, xn, n, out); break;
+        case 64: k_guess_eval<64><<<blocks, 128, 0, st>>>(region, xn, n, out); break;
+        case 128: k_guess_eval<128><<<blocks, 128, 0, st>>>(region, xn, n, out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, int ngrids, const int* hidden, int always,
-                         GuessEntry* queue, uint32_t* count, int64_t cap, unsigned long long* used, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
+                         GuessEntry* queue, uint32_t* counts, int64_t cap, unsigned long long* used, cudaStream_t st) {
+    // segment of each donor grid: the points of the sets whose first donor it is (host knows the set sizes)
+    GuessSeg seg;
+    int64_t size[OVS_MAX_GRIDS] = {};
+    for (int s = 0; s < P.nsets; ++s)
+        if (hidden[P.s[s].donors[0]] > 0) size[P.s[s].donors[0]] += P.s[s].n;
+    int64_t off = 0;
+    for (int gd = 0; gd < OVS_MAX_GRIDS; ++gd) {
+        seg.off[gd] = off;
+        off += size[gd];
+    }
+    if (off > cap) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * OVS_MAX_GRIDS, st);
     if (e != cudaSuccess) return e;
     int64_t blocks = (P.total + 255) / 256;
-    k_guess_select<<<(unsigned)blocks, 256, 0, st>>>(P, dgrids, queue, count, cap, always);
+    k_guess_select<<<(unsigned)blocks, 256, 0, st>>>(P, dgrids, queue, counts, seg, always);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // one launch per donor grid with a network (the queue holds the points of all of them)
-    unsigned gblocks = (unsigned)std::min<int64_t>((P.total / 16 + 3) / 4 + 1, 152 * 8);
     for (int gd = 0; gd < ngrids; ++gd) {
-        if (hidden[gd] <= 0) continue;
-        bool listed = false;
-        for (int s = 0; s < P.nsets; ++s) listed = listed || P.s[s].donors[0] == gd;
-        if (!listed) continue;
+        if (hidden[gd] <= 0 || size[gd] == 0) continue;
+        unsigned gb = (unsigned)std::min<int64_t>((size[gd] / 16 + 3) / 4 + 1, 152 * 8);
+        const GuessEntry* q = queue + seg.off[gd];
         switch (hidden[gd]) {
-            case 32: k_guess_mma<32><<<gblocks, 128, 0, st>>>(P, dgrids, queue, count, cap, gd, used); break;
-            case 64: k_guess_mma<64><<<gblocks, 128, 0, st>>>(P, dgrids, queue, count, cap, gd, used); break;
-            case 128: k_guess_mma<128><<<gblocks, 128, 0, st>>>(P, dgrids, queue, count, cap, gd, used); break;
+            case 32: k_guess_mma<32><<<gb, 128, 0, st>>>(dgrids, gd, q, counts + gd, used); break;
+            case 64: k_guess_mma<64><<<gb, 128, 0, st>>>(dgrids, gd, q, counts + gd, used); break;
+            case 128: k_guess_mma<128><<<gb, 128, 0, st>>>(dgrids, gd, q, counts + gd, used); break;
             default: break;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

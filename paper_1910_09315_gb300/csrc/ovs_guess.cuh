@@ -18,8 +18,15 @@ struct MlpHeader {
 };
 
 struct GuessEntry {
-    int32_t t;    // point index of the call
-    float x[3];   // normalised body-frame input
+    int32_t node;      // receiver node whose hint gets the guess
+    int32_t receiver;  // receiver grid
+    float x[3];        // normalised body-frame input
+    int32_t pad;
+};
+
+// per donor grid, the start of its segment of the guess queue
+struct GuessSeg {
+    int64_t off[OVS_MAX_GRIDS];
 };
 
 constexpr int kMlpMaxHidden = 128;
@@ -27,7 +34,8 @@ constexpr int kMlpMaxParams = kMlpMaxHidden * kMlpMaxHidden + 8 * kMlpMaxHidden 
 constexpr size_t kMlpAlign(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kMlpFwOffset = 256;
 constexpr size_t kMlpFragOffset = kMlpFwOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
-constexpr size_t kMlpParamsOffset = kMlpFragOffset + kMlpAlign(8 * (kMlpMaxHidden / 8) * (kMlpMaxHidden / 16) * 32);
+constexpr size_t kMlpW3FragOffset = kMlpFragOffset + kMlpAlign(8 * (kMlpMaxHidden / 8) * (kMlpMaxHidden / 16) * 32);
+constexpr size_t kMlpParamsOffset = kMlpW3FragOffset + kMlpAlign(8 * (kMlpMaxHidden / 16) * 32);
 constexpr size_t kMlpMOffset = kMlpParamsOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpVOffset = kMlpMOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpGOffset = kMlpVOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
@@ -44,8 +52,9 @@ cudaError_t launch_train_grad(int H, const float* params, const float* X, const 
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr, int step, cudaStream_t st);
 cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t st);
 cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_t n, float* out, cudaStream_t st);
-// always = 1: every point of a set whose first donor has a network gets its guess (hints ignored)
+// always = 1: every point of a set whose first donor has a network gets its guess (hints ignored).
+// counts: OVS_MAX_GRIDS counters (one per donor grid's segment of the queue).
 cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, int ngrids, const int* hidden, int always,
-                         GuessEntry* queue, uint32_t* count, int64_t cap, unsigned long long* used, cudaStream_t st);
+                         GuessEntry* queue, uint32_t* counts, int64_t cap, unsigned long long* used, cudaStream_t st);
 
 }  // namespace ovs

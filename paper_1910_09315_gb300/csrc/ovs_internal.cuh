@@ -28,7 +28,9 @@ constexpr int kNewtonMaxIt32 = 8;
 // accurate to ~1e-10 plus FP32 rounding (~1e-7), and a tighter test would stall at the rounding floor of
 // thin cells
 constexpr float kNewtonTol32 = 1e-5f;
-constexpr int kMaxJump = 4;
+constexpr int kMaxJump = 4;           // cells per walk step along a non-periodic axis
+constexpr int kMaxJumpPeriodic = 12;  // along a periodic (angular) axis, where the extrapolation stays good
+constexpr int kHintWalk = 8;          // walk steps from a previous donor or a learned guess before restarting
 constexpr uint32_t kNoHint = 0xFFFFFFFFu;
 constexpr int kCellBits = 27;
 

@@ -104,7 +104,7 @@ def test_tensor_core_inference_matches_oracle(torch_cuda, H):
     ovs.ovs_guess_eval(scene.ctx.ctx, 1, n, xs.data_ptr(), out.data_ptr())
     scene.ctx.sync()
     got = out.cpu().double().numpy().reshape(3, n).T
-    # reference: FP32 parameters, BF16 hidden layer-1 activations and W2, FP32/FP64 everywhere else
+    # reference: FP32 parameters; layer 2 takes BF16 operands (layer-1 activations and W2); FP64 elsewhere
     Pf = unflat(ps.cpu().double().numpy(), H)
     xf = xs.cpu().double().numpy().reshape(3, n).T
     h1 = bf16(oracle.silu(xf @ Pf["W1"].T + Pf["b1"]))
