@@ -336,7 +336,7 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
     warm (a time loop)."""
     import gen
 
-    out = {"network": "3-64-64-3 SiLU, BF16 tensor-core inference, trained by the library's kernels"}
+    out = {"network": "3-64-64-3 SiLU, FP16 tensor-core inference, trained by the library's kernels"}
     t0 = time.perf_counter()
     losses = []
     for gi, g in enumerate(sc.grids):

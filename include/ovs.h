@@ -198,8 +198,8 @@ int ovs_interpolate(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, con
  * Each body grid can carry a small network 3 -> H -> H -> 3 (SiLU) that maps normalised body-frame coordinates
  * xn = (x - centre) * 2 / extent (centre and extent of the grid's bounding box) to normalised curvilinear
  * coordinates ((i + xi)/Ci, (j + eta)/Cj, (k + zeta)/Ck).  With options.guess = OVS_GUESS_MLP, points without a
- * usable hint start their walk at the cell the network points at (evaluated in BF16 on tensor cores with FP32
- * accumulation); the exact in-cell test is unchanged, so donors do not depend on the network.
+ * usable hint start their walk at the cell the network points at (evaluated with FP16 operands on tensor cores,
+ * FP32 accumulation); the exact in-cell test is unchanged, so donors do not depend on the network.
  * Parameters (FP32): W1 [H x 3] row-major, b1 [H], W2 [H x H] row-major (W2[out][in]), b2 [H], W3 [3 x H],
  * b3 [3]: H*H + 8*H + 3 values.  H is 32, 64 or 128. */
 typedef struct {
@@ -226,7 +226,7 @@ int ovs_train_guess(ovs_ctx* ctx, int32_t grid_id, const ovs_train_desc* desc, f
 /* Checkpoint / restore of a grid's network (device FP32 parameters in the layout above). */
 int ovs_guess_get_params(ovs_ctx* ctx, int32_t grid_id, float* dparams, int32_t* hidden);
 int ovs_guess_set_params(ovs_ctx* ctx, int32_t grid_id, int32_t hidden, const float* dparams);
-/* Evaluate grid_id's network (BF16 tensor-core path) on n normalised inputs xn (device, 3n SoA) -> out (3n). */
+/* Evaluate grid_id's network (the FP16 tensor-core path) on n normalised inputs xn (device, 3n SoA) -> out (3n). */
 int ovs_guess_eval(ovs_ctx* ctx, int32_t grid_id, int64_t n, const float* xn, float* out);
 /* Mean squared error and its gradient (FP32, the training kernel) for parameters `params` on n samples with
  * normalised inputs xn and targets (device, 3n SoA each): grads (device, param count) and *loss (device). */

@@ -34,6 +34,7 @@ struct GridHost {
 
 struct ovs_ctx {
     int device = 0;
+    int nsm = 1;  // streaming multiprocessors of the device (persistent grids)
     cudaStream_t stream = nullptr;
     std::string err;
     // context workspace
@@ -45,8 +46,6 @@ struct ovs_ctx {
     int32_t* d_err = nullptr;
     uint32_t* d_qcount = nullptr;
     SlowEntry* d_queue = nullptr;
-    GuessEntry* d_guess = nullptr;
-    uint32_t* d_gcount = nullptr;
     // grids
     int ngrids = 0;
     GridDev grids[OVS_MAX_GRIDS];
@@ -254,7 +253,9 @@ int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
     c->opts.guess = OVS_GUESS_HINT;
     c->opts.max_walk = 48;
     c->opts.collect_stats = 0;
-    if (cudaSetDevice(device) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
         delete c;
         return OVS_ERR_NO_DEVICE;
     }
@@ -302,8 +303,6 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     off = align_up(off + 4 * sizeof(int32_t));
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
-    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(GuessEntry));
-    off = align_up(off + sizeof(uint32_t) * OVS_MAX_GRIDS);
     *bytes = off;
     return OVS_OK;
 }
@@ -329,9 +328,6 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     off = align_up(off + 4 * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
-    c->d_guess = (GuessEntry*)(base + off);
-    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(GuessEntry));
-    c->d_gcount = (uint32_t*)(base + off);  // one counter per donor grid's segment of the guess queue
     c->ws = dptr;
     c->ws_bytes = bytes;
     c->max_points = max_points;
@@ -616,9 +612,8 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     for (int g = 0; g < c->ngrids; ++g) any_net = any_net || c->hidden[g] > 0;
     if (mlp && any_net && c->tracing && c->trace[5]) cudaEventRecord(c->trace[5], c->stream);
     if (mlp && any_net)
-        e = launch_guess(*P, c->d_grids, c->ngrids, c->hidden, c->opts.guess == OVS_GUESS_MLP_ONLY, c->d_guess,
-                         c->d_gcount, c->max_points, c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr,
-                         c->stream);
+        e = launch_guess(*P, c->d_grids, c->hidden, c->opts.guess == OVS_GUESS_MLP_ONLY, c->nsm,
+                         c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr, c->stream);
     if (mlp && any_net && c->tracing && c->trace[6]) cudaEventRecord(c->trace[6], c->stream);
     if (e == cudaSuccess)
         e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork, c->join);

@@ -7,15 +7,14 @@
 //   k_train_grad     forward + backward of a mini-batch, one thread per sample, activations staged in shared
 //                    memory, weight gradients reduced per block (FP32)
 //   k_adam           Adam update of the FP32 parameters
-//   k_pack           BF16 copy of the weights for inference, W2 in mma.sync fragment order
-//   k_guess_select   points of a call that have no usable hint and a donor grid with a trained network ->
-//                    compact queue of normalised body-frame inputs (warp ballot)
-//   k_guess_mma      the network in BF16 on tensor cores (mma.sync m16n8k16, FP32 accumulation), 16 points per
-//                    warp; writes the guessed cell into the receiver node's hint
+//   k_pack           FP32 copy of the biases and FP16 mma.sync fragments of the three layers for inference
+//   k_guess          points of a call that have no usable hint and a donor grid with a trained network, gathered
+//                    per chunk into 16-row tiles -> the network (all layers in FP16 on tensor cores, mma.sync
+//                    m16n8k16, FP32 accumulation) -> the guessed cell becomes the receiver node's hint
 //
 // Parameter layout (FP32): W1 [H x 3] row-major, b1 [H], W2 [H x H] row-major (W2[out][in]), b2 [H], W3 [3 x H],
 // b3 [3]: H*H + 8*H + 3 values.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ovs_guess.cuh"
 
@@ -177,135 +176,189 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __re
 }
 
 // ---------------------------------------------------------------------------------------------- inference
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
+// FP16 pair, low half = first argument
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// B fragments for mma.m16n8k16 (B[k][n], k = 2t, 2t+1 in b0 and 2t+8, 2t+9 in b1, n = lane / 4, t = lane % 4):
-//   layer 2: B[k][n] = W2[n][k], per (n-tile, k-step, lane);  layer 3: B[k][n] = W3[n][k] for n < 3, else 0.
-__global__ void k_pack(const float* __restrict__ params, int H, float* __restrict__ fw, uint2* __restrict__ w2frag,
-                       uint2* __restrict__ w3frag) {
+// B fragments for mma.m16n8k16 (B[k][n]: k = 2t, 2t+1 in b0 and 2t+8, 2t+9 in b1, n = 8 * tile + lane / 4,
+// t = lane % 4), FP16:
+//   layer 1, one k-step per n-tile: rows k = 2c W1hi[n][c], 2c+1 W1hi[n][c], 6 b1hi[n], 7 b1lo[n], 8+2c W1lo[n][c],
+//     9+2c and 14-15 zero, against A = (x_hi c, x_lo c) in columns 2c, 2c+1, ones in 6-7, (x_hi c, 0) in 8+2c, 9+2c
+//     (c = 0..2), so layer 1 keeps about FP32 accuracy and lane t of a row group needs component t only;
+//   layer 2: W2[n][k], two consecutive k-steps per 16-byte entry, per (n-tile, k-step pair, lane), accumulated in
+//     FP16 (its outputs feed the next FP16 operand directly);
+//   layer 3, one n-tile: n = 0-2 W3hi[n][k], 3-5 W3lo[n - 3][k], 6-7 zero; output o is column o plus column o + 3.
+__global__ void k_pack(const float* __restrict__ params, int H, float* __restrict__ fw, uint2* __restrict__ w1frag,
+                       uint4* __restrict__ w2frag, uint2* __restrict__ w3frag) {
     const int NP = H * H + 8 * H + 3;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NP; q += gridDim.x * blockDim.x) fw[q] = params[q];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int q = tid; q < NP; q += nth) fw[q] = params[q];
+    const float* W1 = params;
+    const float* b1 = params + 3 * H;
     const float* W2 = params + 4 * H;
     const float* W3 = params + 5 * H + H * H;
-    const int nt = H / 8, ks = H / 16;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt * ks * 32; q += gridDim.x * blockDim.x) {
-        int lane = q % 32, kk = (q / 32) % ks, n8 = q / (32 * ks);
-        int g = lane >> 2, t = lane & 3;
-        int n = 8 * n8 + g, k0 = 16 * kk + 2 * t;
-        w2frag[q] = make_uint2(pack_bf16(W2[n * H + k0], W2[n * H + k0 + 1]),
-                               pack_bf16(W2[n * H + k0 + 8], W2[n * H + k0 + 9]));
+    const int nt = H / 8, kp = H / 32, ks = H / 16;
+    auto hi = [](float v) { return __half2float(__float2half_rn(v)); };
+    auto b1row = [&](int k, int n) -> float {
+        if (k < 6) return hi(W1[3 * n + k / 2]);  // against x_hi (even k) and x_lo (odd k) of component k / 2
+        if (k == 6) return hi(b1[n]);
+        if (k == 7) return b1[n] - hi(b1[n]);
+        if (k < 14 && k % 2 == 0) return W1[3 * n + (k - 8) / 2] - hi(W1[3 * n + (k - 8) / 2]);  // against x_hi
+        return 0.f;
+    };
+    for (int q = tid; q < nt * 32; q += nth) {
+        const int lane = q % 32, n = 8 * (q / 32) + lane / 4, t = lane % 4;
+        w1frag[q] = make_uint2(pack_f16(b1row(2 * t, n), b1row(2 * t + 1, n)),
+                               pack_f16(b1row(2 * t + 8, n), b1row(2 * t + 9, n)));
     }
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ks * 32; q += gridDim.x * blockDim.x) {
-        int lane = q % 32, kk = q / 32;
-        int g = lane >> 2, t = lane & 3, k0 = 16 * kk + 2 * t;
-        float w[4] = {0.f, 0.f, 0.f, 0.f};
-        if (g < 3) {
-            w[0] = W3[g * H + k0];
-            w[1] = W3[g * H + k0 + 1];
-            w[2] = W3[g * H + k0 + 8];
-            w[3] = W3[g * H + k0 + 9];
+    for (int q = tid; q < nt * kp * 32; q += nth) {
+        const int lane = q % 32, pp = (q / 32) % kp, n8 = q / (32 * kp);
+        const int n = 8 * n8 + lane / 4, t = lane % 4;
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k0 = 16 * (2 * pp + h) + 2 * t;
+            w[2 * h] = pack_f16(W2[n * H + k0], W2[n * H + k0 + 1]);
+            w[2 * h + 1] = pack_f16(W2[n * H + k0 + 8], W2[n * H + k0 + 9]);
         }
-        w3frag[q] = make_uint2(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]));
+        w2frag[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    auto b3row = [&](int k, int n) -> float {
+        if (n < 3) return hi(W3[n * H + k]);
+        if (n < 6) return W3[(n - 3) * H + k] - hi(W3[(n - 3) * H + k]);
+        return 0.f;
+    };
+    for (int q = tid; q < ks * 32; q += nth) {
+        const int lane = q % 32, kk = q / 32, n = lane / 4, k0 = 16 * kk + 2 * (lane % 4);
+        w3frag[q] = make_uint2(pack_f16(b3row(k0, n), b3row(k0 + 1, n)), pack_f16(b3row(k0 + 8, n), b3row(k0 + 9, n)));
     }
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint2 b) {
+__device__ __forceinline__ void mma_f16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint2 b) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
 }
 
-// One grid's network, staged in shared memory by a block
+// FP16 accumulators: d (rows g, g+8 as FP16 pairs) += A B
+__device__ __forceinline__ void mma_f16_acc16(uint32_t d[2], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                              uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f16.f16.f16.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, {%0,%1};\n"
+                 : "+r"(d[0]), "+r"(d[1])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// SiLU of an FP16 pair: z * sigmoid(z) = z/2 * (1 + tanh(z/2)), one hardware tanh for both (its error, about
+// 2^-11, is that of the FP16 rounding itself; the guess only picks the walk's start, donors do not depend on it)
+__device__ __forceinline__ uint32_t silu_h2(uint32_t zb) {
+    const __half2 h = __hmul2(*reinterpret_cast<const __half2*>(&zb), __float2half2_rn(0.5f));
+    const uint32_t hb = *reinterpret_cast<const uint32_t*>(&h);
+    uint32_t tb;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(hb));
+    const __half2 r = __hfma2(h, *reinterpret_cast<const __half2*>(&tb), h);
+    return *reinterpret_cast<const uint32_t*>(&r);
+}
+
+// One grid's network in shared memory: the FP16 fragments k_pack wrote, b2 as FP16 pairs (the layer-2
+// accumulators start from it) and b3
 template <int H>
 struct MlpSmem {
-    float W1[3 * H];
-    float b1[H];
-    float b2[H];
-    float W3[3 * H];
-    float b3[4];
-    uint2 w2[(H / 8) * (H / 16) * 32];
+    uint2 w1[(H / 8) * 32];
+    uint4 w2[(H / 8) * (H / 32) * 32];
+    uint2 w3[(H / 16) * 32];
+    uint32_t b2[H / 2];
+    float4 b3;
 };
 
 template <int H>
 __device__ __forceinline__ void stage_mlp(MlpSmem<H>& S, const void* region) {
     const float* fw = (const float*)((const char*)region + kMlpFwOffset);
-    const uint2* w2 = (const uint2*)((const char*)region + kMlpFragOffset);
-    for (int q = threadIdx.x; q < 3 * H; q += blockDim.x) {
-        S.W1[q] = fw[q];
-        S.W3[q] = fw[5 * H + H * H + q];
+    const uint2* w1 = (const uint2*)((const char*)region + kMlpW1FragOffset);
+    const uint4* w2 = (const uint4*)((const char*)region + kMlpW2FragOffset);
+    const uint2* w3 = (const uint2*)((const char*)region + kMlpW3FragOffset);
+    for (int q = threadIdx.x; q < (H / 8) * 32; q += blockDim.x) S.w1[q] = w1[q];
+    for (int q = threadIdx.x; q < (H / 8) * (H / 32) * 32; q += blockDim.x) S.w2[q] = w2[q];
+    for (int q = threadIdx.x; q < (H / 16) * 32; q += blockDim.x) S.w3[q] = w3[q];
+    for (int q = threadIdx.x; q < H / 2; q += blockDim.x)
+        S.b2[q] = pack_f16(fw[4 * H + H * H + 2 * q], fw[4 * H + H * H + 2 * q + 1]);
+    if (threadIdx.x == 0) {
+        const float* b3 = fw + 8 * H + H * H;
+        S.b3 = make_float4(b3[0], b3[1], b3[2], 0.f);
     }
-    for (int q = threadIdx.x; q < H; q += blockDim.x) {
-        S.b1[q] = fw[3 * H + q];
-        S.b2[q] = fw[4 * H + H * H + q];
-    }
-    if (threadIdx.x < 3) S.b3[threadIdx.x] = fw[8 * H + H * H + threadIdx.x];
-    for (int q = threadIdx.x; q < (H / 8) * (H / 16) * 32; q += blockDim.x) S.w2[q] = w2[q];
 }
 
-// The network on a tile of 16 inputs (xin, one row per point) held by one warp.  Layer 1 in FP32 straight into
-// the A fragments of layer 2; layer 2 on tensor cores (BF16 operands, FP32 accumulation); layer 3 in FP32 from
-// the accumulator fragments, reduced over the 4 lanes of a row group.  On return, lanes with t = lane % 4 == 0
-// hold y for rows g and g + 8 (g = lane / 4).
+// The network on a tile of 16 inputs (xin[r].xyz, one row per point) held by one warp, all three layers on tensor
+// cores (mma.sync m16n8k16, FP16 operands).  An m16n8 accumulator pair (n-tiles 2k, 2k + 1) has the layout of the
+// m16k16 A operand of the next layer's k-step k, so activations stay in registers:
+//   layer 1: x split into FP16 hi/lo against (W1hi, W1lo, b1hi, b1lo), FP32 accumulation -> z1 to ~FP32;
+//   layer 2: SiLU(z1) in FP16 against W2 in FP16, FP16 accumulators starting from b2;
+//   layer 3: SiLU(z2) in FP16 against W3 split into hi and lo columns, FP32 accumulation; y_o = column o +
+//   column o + 3 + b3_o.
+// On return, lanes with t = lane % 4 == 0 hold y for rows g and g + 8 (g = lane / 4).
 template <int H>
-__device__ __forceinline__ void mlp_tile(const MlpSmem<H>& S, const float (*xin)[3], float y[2][3]) {
+__device__ __forceinline__ void mlp_tile(const MlpSmem<H>& S, const float4* xin, float y[2][3]) {
     const int lane = (int)lane_id(), g = lane >> 2, t = lane & 3;
     constexpr int KS = H / 16, NT = H / 8;
-    float xr[2][3];
+    // layer-1 A fragment (columns 2t, 2t+1 in a0 row g / a1 row g+8; 2t+8, 2t+9 in a2 / a3): component t's
+    // (x_hi, x_lo) and (x_hi, 0) for t < 3, (1, 1) and (0, 0) for t = 3
+    uint32_t a1f[4];
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) xr[rr][c] = xin[g + 8 * rr][c];
-    uint32_t A[KS][4];
-#pragma unroll
-    for (int kk = 0; kk < KS; ++kk) {
-        float h[2][4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int col = 16 * kk + 2 * t + (e & 1) + (e >> 1) * 8;
-            const float w0 = S.W1[3 * col], w1 = S.W1[3 * col + 1], w2 = S.W1[3 * col + 2], bb = S.b1[col];
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                float z = bb + w0 * xr[rr][0] + w1 * xr[rr][1] + w2 * xr[rr][2];
-                h[rr][e] = z / (1.f + __expf(-z));
-            }
-        }
-        A[kk][0] = pack_bf16(h[0][0], h[0][1]);
-        A[kk][1] = pack_bf16(h[1][0], h[1][1]);
-        A[kk][2] = pack_bf16(h[0][2], h[0][3]);
-        A[kk][3] = pack_bf16(h[1][2], h[1][3]);
+    for (int rr = 0; rr < 2; ++rr) {
+        const float4 r = xin[g + 8 * rr];
+        const float xt = t == 0 ? r.x : (t == 1 ? r.y : r.z);
+        const float xh = __half2float(__float2half_rn(xt));
+        const float xl = xt - xh;
+        a1f[rr] = t == 3 ? pack_f16(1.f, 1.f) : pack_f16(xh, xl);
+        a1f[2 + rr] = t == 3 ? 0u : pack_f16(xh, 0.f);
     }
-    // layer 2 on tensor cores; SiLU and the 64 -> 3 output layer in FP32 (its weights are large and its terms
-    // cancel, so BF16 operands there would cost the guess its accuracy)
-    float part[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    // layer 1 -> SiLU -> A fragments of layer 2
+    uint32_t A[KS][4];
 #pragma unroll
     for (int n8 = 0; n8 < NT; ++n8) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kk = 0; kk < KS; ++kk) mma_bf16(c, A[kk], S.w2[(n8 * KS + kk) * 32 + lane]);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int col = 8 * n8 + 2 * t + (e & 1);
-            float z = c[e] + S.b2[col];
-            float h2 = z / (1.f + __expf(-z));
-            const int rr = e >> 1;
-#pragma unroll
-            for (int o = 0; o < 3; ++o) part[rr][o] += S.W3[o * H + col] * h2;
-        }
+        mma_f16(c, a1f[0], a1f[1], a1f[2], a1f[3], S.w1[n8 * 32 + lane]);
+        A[n8 >> 1][(n8 & 1) * 2] = silu_h2(pack_f16(c[0], c[1]));
+        A[n8 >> 1][(n8 & 1) * 2 + 1] = silu_h2(pack_f16(c[2], c[3]));
     }
+    // layer 2 -> SiLU -> layer 3: n-tiles 2k and 2k + 1 of layer 2 make the A fragment of layer 3's k-step k
+    float c3[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
+    for (int kk = 0; kk < KS; ++kk) {
+        uint32_t a3[4];
 #pragma unroll
-        for (int o = 0; o < 3; ++o) {
-            float v = part[rr][o];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            y[rr][o] = v + S.b3[o];
+        for (int h = 0; h < 2; ++h) {
+            const int n8 = 2 * kk + h;
+            const uint32_t bb = S.b2[4 * n8 + t];
+            uint32_t d[2] = {bb, bb};
+#pragma unroll
+            for (int kp = 0; kp < KS / 2; ++kp) {
+                const uint4 b = S.w2[(n8 * (KS / 2) + kp) * 32 + lane];
+                mma_f16_acc16(d, A[2 * kp][0], A[2 * kp][1], A[2 * kp][2], A[2 * kp][3], b.x, b.y);
+                mma_f16_acc16(d, A[2 * kp + 1][0], A[2 * kp + 1][1], A[2 * kp + 1][2], A[2 * kp + 1][3], b.z, b.w);
+            }
+            a3[2 * h] = silu_h2(d[0]);
+            a3[2 * h + 1] = silu_h2(d[1]);
         }
+        mma_f16(c3, a3[0], a3[1], a3[2], a3[3], S.w3[kk * 32 + lane]);
+    }
+    // lane t holds columns 2t, 2t+1 of rows g (c3[0], c3[1]) and g+8 (c3[2], c3[3])
+    float s1[4], s2[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        s1[e] = __shfl_down_sync(0xffffffffu, c3[e], 1);  // columns 2, 3
+        s2[e] = __shfl_down_sync(0xffffffffu, c3[e], 2);  // columns 4, 5
+    }
+    const float4 b3 = S.b3;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        y[rr][0] = c3[2 * rr] + s1[2 * rr + 1] + b3.x;
+        y[rr][1] = c3[2 * rr + 1] + s2[2 * rr] + b3.y;
+        y[rr][2] = s1[2 * rr] + s2[2 * rr + 1] + b3.z;
+    }
 }
 
 // network evaluation on arbitrary normalised inputs (tests and direct use)
@@ -313,7 +366,7 @@ template <int H>
 __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ region, const float* __restrict__ xn,
                                                     int64_t n, float* __restrict__ out) {
     __shared__ MlpSmem<H> S;
-    __shared__ float xs[4][16][3];
+    __shared__ float4 xs[4][16];
     stage_mlp<H>(S, region);
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = (int)lane_id();
@@ -321,8 +374,7 @@ __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ reg
     for (int64_t tile = blockIdx.x * 4 + w; tile < tiles; tile += (int64_t)gridDim.x * 4) {
         if (lane < 16) {
             int64_t q = tile * 16 + lane;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) xs[w][lane][c] = q < n ? xn[c * n + q] : 0.f;
+            xs[w][lane] = q < n ? make_float4(xn[q], xn[n + q], xn[2 * n + q], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();
         float y[2][3];
@@ -340,118 +392,136 @@ __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ reg
     }
 }
 
-// points without a usable hint whose first donor has a trained network -> that grid's segment of the queue
-__global__ void __launch_bounds__(256) k_guess_select(const __grid_constant__ AsmParams P,
-                                                      const GridDev* __restrict__ G, GuessEntry* __restrict__ queue,
-                                                      uint32_t* __restrict__ counts, GuessSeg seg, int always) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool want = false;
-    int gd = -1;
-    GuessEntry e;
-    if (t < P.total) {
-        const int si = find_set(P.s, P.nsets, t);
+// Persistent blocks over the chunks of the sets that take a guess.  Per chunk, phase A (every thread, four points
+// each, independent loads): the points without a usable hint whose position lies in the donor grid's box are
+// gathered into shared memory (network input and receiver node); phase B (warps, 16 rows a tile): the network
+// on the gathered rows, and the guessed cell becomes the receiver node's hint.  A block stages a network only
+// when its chunk's donor grid changes.
+template <int H>
+__global__ void __launch_bounds__(128, 6) k_guess(const __grid_constant__ AsmParams P, const __grid_constant__ GuessWork W,
+                                                  const GridDev* __restrict__ G, int always,
+                                                  unsigned long long* __restrict__ used) {
+    constexpr int kPer = kGuessChunk / 128;
+    __shared__ MlpSmem<H> S;
+    __shared__ float4 rows[kGuessChunk + 16];  // xyz = network input, w = receiver node (bits)
+    __shared__ int nrows;
+    __shared__ struct {
+        float lo[3], hi[3], centre[3], inv_half[3], Cf[3], invC[3];
+        int C[3], per[3];
+    } K;  // the chunk's donor grid: box, input normalisation, cell counts
+    const int wp = threadIdx.x >> 5, lane = (int)lane_id();
+    const int64_t nchunks = W.chunk_begin[W.nsets];
+    int staged = -1;
+    unsigned nused = 0;
+    for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        int w = 0;
+        while (w + 1 < W.nsets && W.chunk_begin[w + 1] <= chunk) ++w;
+        const int si = W.set[w];
         const SetDev& s = P.s[si];
-        gd = s.donors[0];
+        const int gd = s.donors[0];
         const GridDev& g = G[gd];
-        const MlpHeader* hd = (const MlpHeader*)g.mlp;
-        if (hd && hd->ready) {
-            const int32_t node = __ldg(s.node_ids + (t - s.begin));
-            const GridDev& gr = G[s.receiver];
-            if (node >= 0 && node < gr.nnodes) {
-                uint32_t h = gr.hint[node];
-                bool valid = !always && h != kNoHint && (int)(h >> kCellBits) == gd &&
-                             (h & ((1u << kCellBits) - 1)) < g.ncells;
-                if (!valid) {
-                    const int64_t nn = gr.nnodes;
-                    ff x[3], xd[3];
+        const GridDev& gr = G[s.receiver];
+        __syncthreads();  // the previous chunk's rows (and network) are no longer read
+        if (gd != staged) {
+            stage_mlp<H>(S, g.mlp);
+            staged = gd;
+        }
+        if (threadIdx.x == 0) {
+            nrows = 0;
+            const MlpHeader* hd = (const MlpHeader*)g.mlp;
+            for (int c = 0; c < 3; ++c) {
+                K.lo[c] = (float)g.lo[c];
+                K.hi[c] = (float)g.hi[c];
+                K.centre[c] = hd->centre[c];
+                K.inv_half[c] = hd->inv_half[c];
+                K.Cf[c] = (float)g.C[c];
+                K.invC[c] = 1.f / (float)g.C[c];
+                K.C[c] = g.C[c];
+                K.per[c] = g.per[c];
+            }
+        }
+        __syncthreads();
+        const int64_t nn = gr.nnodes;
+        const uint32_t ncells = (uint32_t)g.ncells;
+        uint32_t* __restrict__ hint = gr.hint;
+        const int64_t c0 = (chunk - W.chunk_begin[w]) * kGuessChunk;
+        const int64_t c1 = min(c0 + (int64_t)kGuessChunk, s.n);
+        // phase A
+        int32_t node[kPer];
+        uint32_t h[kPer];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        x[c] = {__ldg(gr.xff + 2 * c * nn + node), __ldg(gr.xff + (2 * c + 1) * nn + node)};
-                    xf_apply(P.xf[si], x, xd);
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t q = c0 + 128 * k + threadIdx.x;
+            node[k] = q < c1 ? __ldg(s.node_ids + q) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) h[k] = (node[k] >= 0 && node[k] < nn) ? hint[node[k]] : 0u;
+        const XfFF& xf = P.xf[si];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            bool want = false;
+            float4 r;
+            if (node[k] >= 0 && node[k] < nn) {
+                const bool valid = !always && h[k] != kNoHint && (int)(h[k] >> kCellBits) == gd &&
+                                   (h[k] & ((1u << kCellBits) - 1)) < ncells;
+                if (!valid) {
+                    // the network's input needs no more than FP32: the high parts of position and map
+                    float x[3], v[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) x[c] = __ldg(gr.xff + 2 * c * nn + node[k]);
                     bool inside = true;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        float v = __fadd_rn(xd[c].hi, xd[c].lo);
-                        inside = inside && v >= (float)g.lo[c] && v <= (float)g.hi[c];
-                        e.x[c] = (v - hd->centre[c]) * hd->inv_half[c];
+                        v[c] = fmaf(xf.Mh[3 * c + 2], x[2],
+                                    fmaf(xf.Mh[3 * c + 1], x[1], fmaf(xf.Mh[3 * c], x[0], xf.th[c])));
+                        inside = inside && v[c] >= K.lo[c] && v[c] <= K.hi[c];
+                        v[c] = (v[c] - K.centre[c]) * K.inv_half[c];
                     }
-                    e.node = node;
-                    e.receiver = s.receiver;
-                    e.pad = 0;
+                    r = make_float4(v[0], v[1], v[2], __int_as_float(node[k]));
                     want = inside;
                 }
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, want);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&nrows, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (want) rows[base + __popc(bal & ((1u << lane) - 1u))] = r;
         }
-    }
-    // one atomic per (warp, donor grid)
-    const unsigned lane = lane_id();
-    const unsigned group = __match_any_sync(0xffffffffu, want ? gd : -1);
-    const int leader = __ffs(group) - 1;
-    uint32_t base = 0;
-    if (want && (int)lane == leader) base = atomicAdd(counts + gd, (uint32_t)__popc(group));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) queue[seg.off[gd] + base + __popc(group & ((1u << lane) - 1u))] = e;
-}
-
-// one donor grid's segment of the queue -> hints (the network's cell), 16 points per warp
-template <int H>
-__global__ void __launch_bounds__(128) k_guess_mma(const GridDev* __restrict__ G, int gd,
-                                                   const GuessEntry* __restrict__ queue, const uint32_t* __restrict__ count,
-                                                   unsigned long long* __restrict__ used) {
-    __shared__ MlpSmem<H> S;
-    __shared__ float xs[4][16][3];
-    __shared__ int32_t nodes[4][16], recs[4][16];
-    const GridDev& g = G[gd];
-    stage_mlp<H>(S, g.mlp);
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = (int)lane_id();
-    const int64_t n = *count;
-    const int64_t tiles = (n + 15) / 16;
-    unsigned nused = 0;
-    for (int64_t tile = blockIdx.x * 4 + w; tile < tiles; tile += (int64_t)gridDim.x * 4) {
-        if (lane < 16) {
-            int64_t q = tile * 16 + lane;
-            if (q < n) {
-                const GuessEntry e = queue[q];
-                nodes[w][lane] = e.node;
-                recs[w][lane] = e.receiver;
+        __syncthreads();
+        const int n = nrows;
+        if ((int)threadIdx.x < ((n + 15) & ~15) - n) rows[n + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        // phase B
+        const int t = lane & 3, gq = lane >> 2;
+        for (int t0 = 16 * wp; t0 < n; t0 += 64) {
+            float y[2][3];
+            mlp_tile<H>(S, rows + t0, y);
+            // lane 4g keeps row g, lane 4g + 1 takes row g + 8
+            float yr[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) xs[w][lane][c] = e.x[c];
-            } else {
-                nodes[w][lane] = -1;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) xs[w][lane][c] = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                const float o = __shfl_up_sync(0xffffffffu, y[1][c], 1);
+                yr[c] = t == 0 ? y[0][c] : o;
             }
-        }
-        __syncwarp();
-        float y[2][3];
-        mlp_tile<H>(S, xs[w], y);
-        if ((lane & 3) == 0) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int row = (lane >> 2) + 8 * rr;
-                const int32_t node = nodes[w][row];
-                if (node < 0) continue;
+            const int row = t0 + gq + 8 * t;
+            if (t < 2 && row < n) {
                 int ijk[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float I = y[rr][c] * (float)g.C[c];
-                    int ci = (int)floorf(fminf(fmaxf(I, -1e6f), 1e6f));
-                    if (g.per[c]) {
-                        ci %= g.C[c];
-                        if (ci < 0) ci += g.C[c];
-                    } else {
-                        ci = min(max(ci, 0), g.C[c] - 1);
-                    }
-                    ijk[c] = ci;
+                    float f = fminf(fmaxf(yr[c] * K.Cf[c], -1e6f), 1e6f);
+                    if (K.per[c]) f -= K.Cf[c] * floorf(f * K.invC[c]);
+                    ijk[c] = min(max((int)floorf(f), 0), K.C[c] - 1);
                 }
-                G[recs[w][row]].hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell_id(g, ijk[0], ijk[1], ijk[2]);
+                hint[__float_as_int(rows[row].w)] =
+                    ((uint32_t)gd << kCellBits) | (uint32_t)(ijk[0] + K.C[0] * (ijk[1] + K.C[1] * ijk[2]));
                 ++nused;
             }
         }
-        __syncwarp();
     }
-    if (used && nused) atomicAdd(used, (unsigned long long)nused);
+    if (used) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, nused);
+        if (lane == 0 && tot) atomicAdd(used, (unsigned long long)tot);
+    }
 }
 
 }  // namespace
@@ -495,9 +565,10 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr
 
 cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t st) {
     float* fw = (float*)((char*)region + kMlpFwOffset);
-    uint2* w2 = (uint2*)((char*)region + kMlpFragOffset);
+    uint2* w1 = (uint2*)((char*)region + kMlpW1FragOffset);
+    uint4* w2 = (uint4*)((char*)region + kMlpW2FragOffset);
     uint2* w3 = (uint2*)((char*)region + kMlpW3FragOffset);
-    k_pack<<<64, 256, 0, st>>>(params, H, fw, w2, w3);
+    k_pack<<<64, 256, 0, st>>>(params, H, fw, w1, w2, w3);
     return cudaGetLastError();
 }
 
@@ -514,35 +585,31 @@ cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, int ngrids, const int* hidden, int always,
-                         GuessEntry* queue, uint32_t* counts, int64_t cap, unsigned long long* used, cudaStream_t st) {
-    // segment of each donor grid: the points of the sets whose first donor it is (host knows the set sizes)
-    GuessSeg seg;
-    int64_t size[OVS_MAX_GRIDS] = {};
-    for (int s = 0; s < P.nsets; ++s)
-        if (hidden[P.s[s].donors[0]] > 0) size[P.s[s].donors[0]] += P.s[s].n;
-    int64_t off = 0;
-    for (int gd = 0; gd < OVS_MAX_GRIDS; ++gd) {
-        seg.off[gd] = off;
-        off += size[gd];
-    }
-    if (off > cap) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * OVS_MAX_GRIDS, st);
-    if (e != cudaSuccess) return e;
-    int64_t blocks = (P.total + 255) / 256;
-    k_guess_select<<<(unsigned)blocks, 256, 0, st>>>(P, dgrids, queue, counts, seg, always);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    for (int gd = 0; gd < ngrids; ++gd) {
-        if (hidden[gd] <= 0 || size[gd] == 0) continue;
-        unsigned gb = (unsigned)std::min<int64_t>((size[gd] / 16 + 3) / 4 + 1, 152 * 8);
-        const GuessEntry* q = queue + seg.off[gd];
-        switch (hidden[gd]) {
-            case 32: k_guess_mma<32><<<gb, 128, 0, st>>>(dgrids, gd, q, counts + gd, used); break;
-            case 64: k_guess_mma<64><<<gb, 128, 0, st>>>(dgrids, gd, q, counts + gd, used); break;
-            case 128: k_guess_mma<128><<<gb, 128, 0, st>>>(dgrids, gd, q, counts + gd, used); break;
-            default: break;
+cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, const int* hidden, int always, int nsm,
+                         unsigned long long* used, cudaStream_t st) {
+    // one launch per network width present; blocks over the chunks of the sets whose first donor has one
+    for (int H : {32, 64, 128}) {
+        GuessWork W;
+        W.nsets = 0;
+        int64_t chunks = 0;
+        for (int s = 0; s < P.nsets; ++s) {
+            if (hidden[P.s[s].donors[0]] != H || P.s[s].n <= 0) continue;
+            W.set[W.nsets] = s;
+            W.chunk_begin[W.nsets] = chunks;
+            chunks += (P.s[s].n + kGuessChunk - 1) / kGuessChunk;
+            ++W.nsets;
         }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        W.chunk_begin[W.nsets] = chunks;
+        if (chunks == 0) continue;
+        // persistent: as many blocks as fit at once (six per SM at the launch bound), or fewer when there are fewer chunks
+        const unsigned blocks = (unsigned)std::min<int64_t>(chunks, (int64_t)nsm * 6);
+        switch (H) {
+            case 32: k_guess<32><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
+            case 64: k_guess<64><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
+            default: k_guess<128><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

@@ -7,8 +7,8 @@
 namespace ovs {
 
 // Per-grid region (inside the grid workspace), sized for the widest network (H = 128):
-//   header | inference copy of the FP32 parameters | W2 as BF16 mma fragments | training: FP32 parameters,
-//   Adam first and second moments, gradients, loss accumulator
+//   header | inference copy of the FP32 parameters | FP16 mma fragments of the three layers | training: FP32
+//   parameters, Adam first and second moments, gradients, loss accumulator
 struct MlpHeader {
     int32_t hidden;     // 0: no network
     int32_t ready;      // 1 once trained (or set) and packed
@@ -17,25 +17,24 @@ struct MlpHeader {
     int32_t pad[8];
 };
 
-struct GuessEntry {
-    int32_t node;      // receiver node whose hint gets the guess
-    int32_t receiver;  // receiver grid
-    float x[3];        // normalised body-frame input
-    int32_t pad;
-};
-
-// per donor grid, the start of its segment of the guess queue
-struct GuessSeg {
-    int64_t off[OVS_MAX_GRIDS];
+// The sets of a call whose first donor grid has a network of one width, cut into chunks of kGuessChunk points
+// (a chunk never crosses a set): chunk b is chunk b - chunk_begin[w] of set set[w].
+constexpr int kGuessChunk = 512;
+struct GuessWork {
+    int32_t nsets;
+    int32_t set[OVS_MAX_SETS];
+    int64_t chunk_begin[OVS_MAX_SETS + 1];
 };
 
 constexpr int kMlpMaxHidden = 128;
 constexpr int kMlpMaxParams = kMlpMaxHidden * kMlpMaxHidden + 8 * kMlpMaxHidden + 3;
 constexpr size_t kMlpAlign(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kMlpFwOffset = 256;
-constexpr size_t kMlpFragOffset = kMlpFwOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
-constexpr size_t kMlpW3FragOffset = kMlpFragOffset + kMlpAlign(8 * (kMlpMaxHidden / 8) * (kMlpMaxHidden / 16) * 32);
-constexpr size_t kMlpParamsOffset = kMlpW3FragOffset + kMlpAlign(8 * (kMlpMaxHidden / 16) * 32);
+// FP16 mma fragments for inference (k_pack): W2 (2 H^2 bytes), layer 1 (32 H bytes), layer 3 (16 H bytes)
+constexpr size_t kMlpW2FragOffset = kMlpFwOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
+constexpr size_t kMlpW1FragOffset = kMlpW2FragOffset + kMlpAlign(2 * kMlpMaxHidden * kMlpMaxHidden);
+constexpr size_t kMlpW3FragOffset = kMlpW1FragOffset + kMlpAlign(32 * kMlpMaxHidden);
+constexpr size_t kMlpParamsOffset = kMlpW3FragOffset + kMlpAlign(16 * kMlpMaxHidden);
 constexpr size_t kMlpMOffset = kMlpParamsOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpVOffset = kMlpMOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpGOffset = kMlpVOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
@@ -53,8 +52,7 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr
 cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t st);
 cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_t n, float* out, cudaStream_t st);
 // always = 1: every point of a set whose first donor has a network gets its guess (hints ignored).
-// counts: OVS_MAX_GRIDS counters (one per donor grid's segment of the queue).
-cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, int ngrids, const int* hidden, int always,
-                         GuessEntry* queue, uint32_t* counts, int64_t cap, unsigned long long* used, cudaStream_t st);
+cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, const int* hidden, int always, int nsm,
+                         unsigned long long* used, cudaStream_t st);
 
 }  // namespace ovs
