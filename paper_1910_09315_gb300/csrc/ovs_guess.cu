@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ reg
 // on the gathered rows, and the guessed cell becomes the receiver node's hint.  A block stages a network only
 // when its chunk's donor grid changes.
 template <int H>
-__global__ void __launch_bounds__(128, 6) k_guess(const __grid_constant__ AsmParams P, const __grid_constant__ GuessWork W,
+__global__ void __launch_bounds__(128, kGuessBlocksPerSM) k_guess(const __grid_constant__ AsmParams P, const __grid_constant__ GuessWork W,
                                                   const GridDev* __restrict__ G, int always,
                                                   unsigned long long* __restrict__ used) {
     constexpr int kPer = kGuessChunk / 128;
@@ -601,8 +601,9 @@ cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, const int* h
         }
         W.chunk_begin[W.nsets] = chunks;
         if (chunks == 0) continue;
-        // persistent: as many blocks as fit at once (six per SM at the launch bound), or fewer when there are fewer chunks
-        const unsigned blocks = (unsigned)std::min<int64_t>(chunks, (int64_t)nsm * 6);
+        // persistent: as many blocks as fit at once (the launch bound's blocks per SM), or fewer when there are
+        // fewer chunks
+        const unsigned blocks = (unsigned)std::min<int64_t>(chunks, (int64_t)nsm * kGuessBlocksPerSM);
         switch (H) {
             case 32: k_guess<32><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
             case 64: k_guess<64><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;

@@ -19,7 +19,8 @@ struct MlpHeader {
 
 // The sets of a call whose first donor grid has a network of one width, cut into chunks of kGuessChunk points
 // (a chunk never crosses a set): chunk b is chunk b - chunk_begin[w] of set set[w].
-constexpr int kGuessChunk = 512;
+constexpr int kGuessChunk = 256;
+constexpr int kGuessBlocksPerSM = 8;  // k_guess: 128 threads at up to 64 registers
 struct GuessWork {
     int32_t nsets;
     int32_t set[OVS_MAX_SETS];
