@@ -203,15 +203,38 @@ def stretched_background(n: Sequence[int], lo: Sequence[float], hi: Sequence[flo
     (s_k = index/(n_k-1), h = 1/(n_min-1) scaled by the box size; it vanishes on the boundary)."""
     s = [np.arange(n[d]) / (n[d] - 1) for d in range(3)]
     u = [tanh_cluster_centre(n[d], beta) if d == cluster_axis else s[d] for d in range(3)]
-    U = np.meshgrid(*u, indexing="ij")
-    S = np.meshgrid(*s, indexing="ij")
-    bump = np.sin(2 * np.pi * S[0]) * np.sin(2 * np.pi * S[1]) * np.sin(2 * np.pi * S[2])
+    # arrays shaped (nk, nj, ni) in C order, so that ravel() is the i-fastest node order
+    shape = [(1, 1, n[0]), (1, n[1], 1), (n[2], 1, 1)]
+    sb = [np.sin(2 * np.pi * s[d]).reshape(shape[d]) for d in range(3)]
+    bump = (sb[0] * sb[1]) * sb[2]
     coords = []
+    axes, pert = [], []
     for d in range(3):
         L = hi[d] - lo[d]
         h = L / (n[d] - 1)
-        coords.append(flat(lo[d] + L * U[d] + pert_h * h * bump))
-    return Grid(name, tuple(n), (False, False, False), *coords, role=0)
+        c = lo[d] + L * u[d].reshape(shape[d])
+        coords.append(np.ascontiguousarray((c + pert_h * h * bump).ravel()))
+        axes.append(lo[d] + L * u[d])
+        pert.append(abs(pert_h) * h)
+    return Grid(name, tuple(n), (False, False, False), *coords, role=0, meta=dict(axes=axes, pert=pert))
+
+
+def box_candidates(bg: Grid, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """Node ids of a stretched background whose position lies in the axis-aligned box [lo, hi]: index ranges
+    from the unperturbed axes (every node lies within ``pert`` of its axis value), then the exact test."""
+    rng = []
+    for d in range(3):
+        ax = bg.meta["axes"][d]
+        a = int(np.searchsorted(ax, lo[d] - bg.meta["pert"][d], side="left"))
+        b = int(np.searchsorted(ax, hi[d] + bg.meta["pert"][d], side="right"))
+        rng.append(np.arange(a, b, dtype=np.int64))
+    ni, nj, _ = bg.dims
+    ids = (rng[0][:, None, None] + ni * (rng[1][None, :, None] + nj * rng[2][None, None, :])).ravel()
+    if ids.size == 0:
+        return ids
+    m = ((bg.x[ids] >= lo[0]) & (bg.x[ids] <= hi[0]) & (bg.y[ids] >= lo[1]) & (bg.y[ids] <= hi[1]) &
+         (bg.z[ids] >= lo[2]) & (bg.z[ids] <= hi[2]))
+    return np.sort(ids[m])
 
 
 def ellipsoid_ogrid(na: int, npol: int, nr: int, semi: Sequence[float], r_out: float, beta_r: float) -> Grid:
@@ -363,6 +386,204 @@ def moving_ellipsoid(config_index: int, nbg: int, nsteps: int = 100, dt: float =
                     meta=dict(axis=axis, vdir=vdir))
 
 
+# ----------------------------------------------------------------------------
+# school of fish (Sec. 3.5 geometry, synthetic bodies)
+# ----------------------------------------------------------------------------
+FISH_WAVELENGTH = 0.95  # lambda / L (Sec. 3.5)
+FISH_TAIL_BEAT = 1.0 / (240 * 1.39e-3)  # 240 time steps of dt = 1.39e-3 per tail beat (Sec. 3.5)
+
+
+def naca0012_half_thickness(s: np.ndarray) -> np.ndarray:
+    """Half-thickness of the NACA 4-digit section of 12% thickness at chord fraction s in [0,1] (closed
+    trailing edge variant of the last coefficient)."""
+    s = np.clip(s, 0.0, 1.0)
+    return 0.6 * (0.2969 * np.sqrt(s) - 0.1260 * s - 0.3516 * s ** 2 + 0.2843 * s ** 3 - 0.1036 * s ** 4)
+
+
+def fish_envelope(s: np.ndarray) -> np.ndarray:
+    """Amplitude envelope a(s) = a0 + a1 s + a2 s^2 with (a0, a1, a2) = (0.02, -0.08, 0.16), so that the tail
+    (s = 1) reaches the maximum excursion 0.1 L that Sec. 3.5 states."""
+    return 0.02 - 0.08 * s + 0.16 * s ** 2
+
+
+def fish_midline(s: np.ndarray, phase: float) -> np.ndarray:
+    """Frozen lateral excursion of the midline, h(s) = a(s) sin(2 pi s / lambda - phase) (Sec. 3.5 at one
+    instant)."""
+    return fish_envelope(s) * np.sin(2 * np.pi * s / FISH_WAVELENGTH - phase)
+
+
+# In body lengths.  The hull's axial semi-axis equals the body's (A = 1/2): radial and azimuthal grid edges then
+# lie in planes x = const, where the midline shear y += h(x) leaves every corner Jacobian unchanged.
+FISH_HULL = dict(A=0.5, B=0.25, C=0.2, height=1.6, beta_r=2.0)
+
+
+def fish_ogrid(name: str, na: int, npol: int, nr: int, phase: float) -> Grid:
+    """Body-fitted O-grid around a fish-like body of length 1 (head at body x = -1/2, tail at +1/2).
+
+    Body: at chord fraction s (head 0, tail 1) the cross-section is an ellipse centred on the midline
+    h(s) (lateral, body y) with lateral half-width the NACA0012 half-thickness w(s) and vertical half-height
+    1.6 w(s).  Outer boundary: an ellipsoid of semi-axes (A = 1/2, B, C).  The grid of the straight body (h = 0) is
+    sheared laterally, y += h(clip(x + 1/2, 0, 1)), at each node's own x: a map of unit Jacobian, so the bent
+    grid is as regular as the straight one, and the body surface keeps its cross-sections on the midline.
+    i: azimuth th_i = 2 pi i/na (periodic); j: polar angle ph_j = pi (j+1/2)/npol with s = (1 - cos ph)/2 (the
+    head and tail caps of half-angle pi/(2 npol) are not covered); k: radial fraction f_k tanh-clustered toward
+    the body.  Node = (X, h(X + 1/2) + Bf cos th, Cf sin th) with X = -((1-f)/2 + f A) cos ph, Bf = (1-f) w(s) +
+    f B sin ph, Cf = (1-f) 1.6 w(s) + f C sin ph: every k-layer is a surface of ellipses at fixed x, which makes
+    the hull test below exact."""
+    P = FISH_HULL
+    th = 2 * np.pi * np.arange(na) / na
+    ph = np.pi * (np.arange(npol) + 0.5) / npol
+    f = tanh_cluster_wall(nr, P["beta_r"])
+    TH, PH, F = np.meshgrid(th, ph, f, indexing="ij")
+    s = 0.5 * (1 - np.cos(PH))
+    w = naca0012_half_thickness(s)
+    X = -((1 - F) * 0.5 + F * P["A"]) * np.cos(PH)
+    Bf = (1 - F) * w + F * P["B"] * np.sin(PH)
+    Cf = (1 - F) * P["height"] * w + F * P["C"] * np.sin(PH)
+    hx = fish_midline(np.clip(X + 0.5, 0.0, 1.0), phase)
+    meta = dict(kind="fish", phase=phase, t=f, npol=npol)
+    return Grid(name, (na, npol, nr), (True, False, False), flat(X), flat(hx + Bf * np.cos(TH)),
+                flat(Cf * np.sin(TH)), 1, meta)
+
+
+def inside_fish_layer(p: np.ndarray, phase: float, frac: float) -> np.ndarray:
+    """Body-frame points strictly inside the k-layer surface of radial fraction ``frac`` of a fish O-grid
+    (frac = 0: the body itself)."""
+    P = FISH_HULL
+    Af = (1 - frac) * 0.5 + frac * P["A"]
+    cph = -p[:, 0] / Af
+    ok = np.abs(cph) < 1
+    cph = np.clip(cph, -1, 1)
+    sph = np.sqrt(1 - cph ** 2)
+    s = 0.5 * (1 - cph)
+    w = naca0012_half_thickness(s)
+    Bf = (1 - frac) * w + frac * P["B"] * sph
+    Cf = (1 - frac) * P["height"] * w + frac * P["C"] * sph
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = ((p[:, 1] - fish_midline(np.clip(p[:, 0] + 0.5, 0.0, 1.0), phase)) / Bf) ** 2 + (p[:, 2] / Cf) ** 2
+    return ok & (Bf > 0) & (Cf > 0) & (q < 1)
+
+
+def fish_sizes(n: int, lo: Sequence[int], hi: Sequence[int]) -> List[tuple]:
+    """n grid sizes linearly spaced from lo to hi (azimuth rounded to a multiple of 8, the others to 4)."""
+    out = []
+    for q in range(n):
+        a = q / max(1, n - 1)
+        d = [lo[k] + (hi[k] - lo[k]) * a for k in range(3)]
+        out.append((int(round(d[0] / 8) * 8), int(round(d[1] / 4) * 4), int(round(d[2] / 4) * 4)))
+    return out
+
+
+def fish_school(config_index: int, nfish: int, bg_dims: Sequence[int], size_lo: Sequence[int],
+                size_hi: Sequence[int], layers: Sequence[float], nsteps: int, dt: float = 1.39e-3) -> Scenario:
+    """Diamond school of fish-like O-grids in a stretched curvilinear background (Sec. 3.5 geometry).
+
+    Diamonds of four (front; two sides 0.45 L lateral and 1.45 L posterior; last 2.9 L behind), two side by side
+    1.2 L apart (so the hulls of the two inner side fish overlap), one such pair per vertical ``layers`` entry;
+    seeded jitter of 0.03 L.  All fish share the
+    seeded phase of the frozen midline (no phase difference between swimmers, Sec. 3.5).  Each swims rigidly
+    toward -x at a seeded speed U in [0.9, 1.1] with a seeded yaw oscillation of 0.05 rad at the tail-beat
+    frequency.  Body grid sizes are spread linearly between ``size_lo`` and ``size_hi`` and assigned in seeded
+    order.  Background: box around the school's path, x streamwise, y lateral (tanh clustering beta = 2 toward
+    the centre plane, 0.1 h sinusoidal perturbation), z vertical.  Fringe sets per step:
+      * each body's outer two radial layers: points inside another body's hull (shrunk to its layer nk-3, outside
+        its body) search [those bodies in id order, background], the rest [background];
+      * background nodes inside a body's shrunk hull and outside every body, grouped by the bodies containing
+        them, search those bodies in id order.
+    FP32 fields."""
+    rng = rng_for(config_index)
+    base = [(0.0, 0.0), (1.45, 0.45), (1.45, -0.45), (2.9, 0.0)]
+    pos = []
+    for zc in layers:
+        for yc in (-0.6, 0.6):
+            for (px, py) in base:
+                if len(pos) < nfish:
+                    pos.append(np.array([px, yc + py, zc]) + rng.uniform(-0.03, 0.03, size=3))
+    pos = np.array(pos)
+    speed = rng.uniform(0.9, 1.1, size=nfish)
+    yaw0 = rng.uniform(-0.05, 0.05, size=nfish)
+    yaw_phase = rng.uniform(0, 2 * np.pi, size=nfish)
+    phase = float(rng.uniform(0, 2 * np.pi))
+    sizes = fish_sizes(nfish, size_lo, size_hi)
+    order = rng.permutation(nfish)
+    T = nsteps * dt
+    P = FISH_HULL
+    reach = P["A"] + 0.05
+    lo = np.array([pos[:, 0].min() - speed.max() * T - reach - 0.3, pos[:, 1].min() - P["B"] - 0.45,
+                   pos[:, 2].min() - P["C"] - 0.3])
+    hi = np.array([pos[:, 0].max() + reach + 0.3, pos[:, 1].max() + P["B"] + 0.45, pos[:, 2].max() + P["C"] + 0.3])
+    bg = stretched_background(tuple(bg_dims), lo, hi, beta=2.0, cluster_axis=1, pert_h=0.1,
+                              name="bg%dx%dx%d" % tuple(bg_dims))
+    bodies = [fish_ogrid("fish%d" % q, *sizes[order[q]], phase) for q in range(nfish)]
+    grids = [bg] + bodies
+    fields = make_fields(rng, grids, np.float32)
+    fringes = [radial_layers(b, 2) for b in bodies]
+    # inertial half-extents of a hull under yaw |psi| <= 0.1 (|x_b| <= A, |y_b| <= B + max|h| = B + 0.1, |z_b| <= C)
+    half = np.array([P["A"] + (P["B"] + 0.1) * 0.1 + 0.01, P["B"] + 0.1 + P["A"] * 0.1 + 0.01, P["C"] + 0.01])
+    frac_in = [b.meta["t"][-3] for b in bodies]
+    amp = 0.05
+
+    def motion_fn(step: int) -> List[Motion]:
+        t = step * dt
+        out = [Motion.identity()]
+        for q in range(nfish):
+            arg = 2 * np.pi * FISH_TAIL_BEAT * t + yaw_phase[q]
+            psi = yaw0[q] + amp * np.sin(arg)
+            dpsi = amp * 2 * np.pi * FISH_TAIL_BEAT * np.cos(arg)
+            R = axis_angle(np.array([0.0, 0.0, 1.0]), psi)
+            V = np.array([-speed[q], 0.0, 0.0])
+            out.append(Motion(R, pos[q] + V * t, V, np.array([0.0, 0.0, dpsi])))
+        return out
+
+    def sets_fn(step: int, motions: List[Motion]) -> List[FringeSet]:
+        ms = motions[1:]
+        sets: List[FringeSet] = []
+        # body fringe: inside other bodies' hulls -> those bodies first, then the background
+        for q, b in enumerate(bodies):
+            ids = fringes[q]
+            pts = (b.xyz()[ids] @ ms[q].R.T) + ms[q].c
+            keys = np.zeros(len(ids), dtype=np.int64)
+            for r in range(nfish):
+                if r == q or np.linalg.norm(ms[r].c - ms[q].c) > 2 * reach:
+                    continue
+                pb = to_body(ms[r], pts)
+                hit = inside_fish_layer(pb, phase, frac_in[r])
+                hit[hit] &= ~inside_fish_layer(pb[hit], phase, 0.0)
+                keys |= hit.astype(np.int64) << r
+            for key in np.unique(keys):
+                sel = ids[keys == key]
+                don = [1 + r for r in range(nfish) if (int(key) >> r) & 1][:7] + [0]
+                sets.append(FringeSet(1 + q, sel.astype(np.int32), don, "body->bg" if key == 0 else "body->body"))
+        # background nodes inside hulls, outside every body, grouped by the hulls that hold them
+        nodes, bits, solid = [], [], []
+        for q in range(nfish):
+            cand = box_candidates(bg, ms[q].c - half, ms[q].c + half)
+            pb = to_body(ms[q], np.stack([bg.x[cand], bg.y[cand], bg.z[cand]], axis=1))
+            hit = inside_fish_layer(pb, phase, frac_in[q])
+            body_hit = np.zeros_like(hit)
+            body_hit[hit] = inside_fish_layer(pb[hit], phase, 0.0)
+            nodes.append(cand[hit])
+            bits.append(np.full(int(hit.sum()), 1 << q, dtype=np.int64))
+            solid.append(cand[body_hit])
+        nodes = np.concatenate(nodes)
+        bits = np.concatenate(bits)
+        order = np.argsort(nodes, kind="stable")
+        nodes, bits = nodes[order], bits[order]
+        uniq, start = np.unique(nodes, return_index=True)
+        keys = np.bitwise_or.reduceat(bits, start) if len(uniq) else bits
+        keep = ~np.isin(uniq, np.concatenate(solid))
+        uniq, keys = uniq[keep], keys[keep]
+        for key in np.unique(keys):
+            sel = uniq[keys == key]
+            don = [1 + r for r in range(nfish) if (int(key) >> r) & 1][:8]
+            sets.append(FringeSet(0, sel.astype(np.int32), don, "bg->body"))
+        return sets
+
+    return Scenario(f"cfg{config_index}: school of {nfish} fish O-grids in a stretched bg "
+                    "%dx%dx%d" % tuple(bg_dims), grids, fields, np.float32, dt=dt, nsteps=nsteps,
+                    motion_fn=motion_fn, sets_fn=sets_fn, meta=dict(phase=phase, positions=pos, sizes=sizes))
+
+
 def config1() -> Scenario:
     return moving_ellipsoid(1, 128)
 
@@ -380,7 +601,18 @@ def mlp_training_samples(config_index: int, grid: Grid, n_samples: int):
     return cells, xi
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2}
+def config3() -> Scenario:
+    """8 fish of 48x32x32 .. 128x64x64 in a 384x256x128 background, 200 steps."""
+    return fish_school(3, 8, (384, 256, 128), (48, 32, 32), (128, 64, 64), layers=(0.0,), nsteps=200)
+
+
+def config4() -> Scenario:
+    """16 fish of 64^3 .. 160x96x96 (two layers of the 8-fish school 0.6 L apart) in a 512x384x256 background
+    (~50M nodes), 1000 steps."""
+    return fish_school(4, 16, (512, 384, 256), (64, 64, 64), (160, 96, 96), layers=(-0.3, 0.3), nsteps=1000)
+
+
+CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3, 4: config4}
 
 
 def config(i: int) -> Scenario:

@@ -68,3 +68,89 @@ def test_cfg1_motion_matches_stated_rates():
     ang = np.arccos((np.trace(dR) - 1) / 2)
     assert ang == pytest.approx(2 * np.pi * 1e-3, rel=1e-9)
     assert np.allclose(m1.c - m0.c, m0.V * 1e-3, atol=1e-15)
+
+
+@pytest.mark.parametrize("dims", [(48, 32, 32), (160, 96, 96)])
+def test_fish_grids_valid(dims):
+    g = gen.fish_ogrid("fish", *dims, phase=1.3)
+    d = corner_jacobians(g)
+    sgn = np.sign(d.mean())
+    assert np.all(d * sgn > 0)
+
+
+def test_fish_layer_test_matches_grid():
+    """The analytic layer test agrees with the grid's own k-layers: nodes inside layer nk-3 for k < nk-3,
+    outside for k > nk-3; outside the body for k >= 1; the midline itself is inside the body."""
+    phase = 0.7
+    g = gen.fish_ogrid("fish", 64, 40, 40, phase)
+    ni, nj, nk = g.dims
+    p = g.xyz()
+    k = np.arange(g.n_nodes) // (ni * nj)
+    f = g.meta["t"][-3]
+    inside = gen.inside_fish_layer(p, phase, f)
+    assert np.all(inside[k < nk - 3]) and not np.any(inside[k > nk - 3])
+    body = gen.inside_fish_layer(p, phase, 0.0)
+    assert not np.any(body[k >= 1])
+    s = np.linspace(0.05, 0.95, 50)
+    mid = np.stack([s - 0.5, gen.fish_midline(s, phase), np.zeros_like(s)], axis=1)
+    assert np.all(gen.inside_fish_layer(mid, phase, 0.0))
+
+
+def test_fish_envelope_reading():
+    """a(s) = 0.02 - 0.08 s + 0.16 s^2 reaches the stated tail excursion 0.1 L at s = 1."""
+    assert gen.fish_envelope(np.array([1.0]))[0] == pytest.approx(0.10)
+    assert gen.fish_envelope(np.array([0.0]))[0] == pytest.approx(0.02)
+
+
+@pytest.fixture(scope="module")
+def school():
+    return gen.config(3)
+
+
+def test_school_sets(school):
+    sc = school
+    nfish = len(sc.grids) - 1
+    for step in (0, sc.nsteps - 1):
+        m = sc.motion(step)
+        sets = sc.fringe_sets(step, m)
+        assert len(sets) <= 64
+        kinds = {s.kind for s in sets}
+        assert {"body->bg", "body->body", "bg->body"} <= kinds
+        seen = {}
+        for s in sets:
+            g = sc.grids[s.receiver]
+            assert s.node_ids.dtype == np.int32 and len(s.node_ids) > 0
+            assert s.node_ids.min() >= 0 and s.node_ids.max() < g.n_nodes
+            assert np.all(np.diff(s.node_ids) > 0)
+            assert 1 <= len(s.donors) <= 8 and s.receiver not in s.donors
+            if s.receiver > 0:
+                assert s.donors[-1] == 0  # body fringe falls back to the background
+            else:
+                assert all(1 <= d <= nfish for d in s.donors) and s.donors == sorted(s.donors)
+            prev = seen.setdefault(s.receiver, set())
+            ids = set(s.node_ids.tolist())
+            assert not (prev & ids)  # a receiver node is in one set only
+            prev |= ids
+        # background receivers lie inside the hull of their first donor and outside every body
+        bgset = [s for s in sets if s.receiver == 0]
+        bg = sc.grids[0]
+        phase = sc.meta["phase"]
+        for s in bgset[:4]:
+            pts = bg.xyz()[s.node_ids[:2000]]
+            q = s.donors[0]
+            b = gen.to_body(m[q], pts)
+            assert np.all(gen.inside_fish_layer(b, phase, sc.grids[q].meta["t"][-3]))
+            for r in range(1, nfish + 1):
+                assert not np.any(gen.inside_fish_layer(gen.to_body(m[r], pts), phase, 0.0))
+
+
+def test_school_motion(school):
+    sc = school
+    dt = sc.dt
+    m0, m1 = sc.motion(10), sc.motion(11)
+    for a, b in zip(m0[1:], m1[1:]):
+        assert np.allclose(b.c - a.c, a.V * dt, atol=1e-15)
+        dR = b.R @ a.R.T
+        ang = np.arctan2(dR[1, 0], dR[0, 0])
+        assert ang == pytest.approx(0.5 * (a.omega[2] + b.omega[2]) * dt, rel=1e-3, abs=1e-9)
+        assert np.abs(a.R.T @ a.R - np.eye(3)).max() < 1e-14
