@@ -81,6 +81,17 @@ extern "C" {
 #define OVS_GUESS_HINT 0 /* start from the donor found for the same receiver node last call, else bins */
 #define OVS_GUESS_BINS 1 /* always start from the control-cell bin of the point */
 #define OVS_GUESS_MLP 2  /* body grids with a trained guess network: start there when no hint */
+/* How a call's kernels reach the GPU.  Every call first copies its parameters (sets, frame maps, motions,
+ * output pointers: one block) from a double-buffered pinned staging area to the context workspace; the
+ * kernels read them there, and their grids are persistent (a multiple of the SM count), so the launch
+ * sequence of a call depends only on which kernels it needs.
+ *   GRAPH:  that sequence is captured once per kind of call (assemble, assemble+interpolate in FP32 or FP64,
+ *           the set of guess-network widths, the no-allocation queue) as a CUDA graph, two instances (one per
+ *           staging buffer), and every later call of the same kind is one cudaGraphLaunch on the context stream.
+ *   DIRECT: the same copy and kernels launched one by one (always the case while trace events are set).
+ * A call that reuses a staging buffer first waits (host) for the call that used it two calls earlier. */
+#define OVS_LAUNCH_DIRECT 0
+#define OVS_LAUNCH_GRAPH 1
 #define OVS_GUESS_MLP_ONLY 3 /* body grids with a trained guess network: always start there (hints ignored) */
 
 typedef struct ovs_ctx ovs_ctx;
@@ -132,6 +143,7 @@ typedef struct {
     int32_t guess;         /* OVS_GUESS_* (default HINT) */
     int32_t max_walk;      /* walk steps before the exhaustive fallback (default 48, 1..1024) */
     int32_t collect_stats; /* 1: count walk steps / slow-path points (small atomic cost) */
+    int32_t launch;        /* OVS_LAUNCH_* (default GRAPH) */
 } ovs_options;
 
 typedef struct {
@@ -240,6 +252,28 @@ int ovs_get_stats(ovs_ctx* ctx, ovs_stats* out, int reset);
 
 /* Forget all per-node donor hints (next assemble starts cold). */
 int ovs_reset_hints(ovs_ctx* ctx);
+
+/* Launch shapes of the persistent kernels: blocks per SM of each grid (a kernel's grid is this many blocks
+ * times the SM count, whatever the call's size).  0 = the default: assembly 3 (its launch bound), interpolation
+ * the occupancy calculator's figure, slow path 1, learned guess 8. */
+typedef struct {
+    int32_t assemble_blocks_per_sm; /* k_assemble, 256 threads a block: 1..12 */
+    int32_t interp_blocks_per_sm;   /* k_interp, 256 threads a block: 1..32 */
+    int32_t slow_blocks_per_sm;     /* k_slow_near and k_slow_stuck, 256 threads a block: 1..8 */
+    int32_t guess_blocks_per_sm;    /* k_guess, 128 threads a block: 1..32 */
+} ovs_tuning;
+
+/* Set (NULL or all zero: defaults) / read the launch shapes.  Drops the context's captured graphs. */
+int ovs_set_tuning(ovs_ctx* ctx, const ovs_tuning* t);
+int ovs_get_tuning(const ovs_ctx* ctx, ovs_tuning* t);
+/* Autotuner: times the call ovs_assemble_interpolate(sets, nsets, out, fields, nfields, fout) (fout may be NULL:
+ * ovs_assemble) under candidate launch shapes, one knob at a time (each knob over a few values around its
+ * default, the others held), `reps` timed calls per candidate after one untimed call, with CUDA events on the
+ * context stream; keeps the fastest and writes it to *best (may be NULL).  The calls run for real: their
+ * outputs and the donor hints are those of the last one.  Synchronises the stream. */
+int ovs_autotune(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                 const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t reps,
+                 ovs_tuning* best);
 
 /* Tracing: record caller-created CUDA events (cudaEvent_t, NULL to skip one) on the context's stream at
  * fixed points of later calls: ev[0] before the fast assembly kernel, ev[1] after it, ev[2] after the

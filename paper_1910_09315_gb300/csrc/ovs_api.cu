@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "ovs_guess.cuh"
 #include "ovs_internal.cuh"
@@ -59,6 +60,21 @@ struct ovs_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr;
     cudaEvent_t join = nullptr;
+    // step parameters: the device copy (context workspace) and two pinned staging buffers, each with the event
+    // that marks the end of the last call that read it
+    StepParams* d_step = nullptr;
+    StepParams* h_step[2] = {nullptr, nullptr};
+    cudaEvent_t step_done[2] = {nullptr, nullptr};
+    bool step_used[2] = {false, false};
+    int stage = 0;
+    // CUDA graphs of the launch sequences, one pair (per staging buffer) for each kind of call
+    cudaStream_t gstream = nullptr;  // capture stream
+    struct GraphEntry {
+        uint32_t kind;
+        cudaGraphExec_t exec[2];
+    };
+    std::vector<GraphEntry> graphs;
+    ovs_tuning tune = {0, 0, 0, 0};  // launch shapes (0: defaults)
 };
 
 namespace {
@@ -235,6 +251,22 @@ void fill_motion_f32(const ovs_ctx* c, MotionF* out) {
 
 extern "C" {
 
+// frees what a context owns on the host and the device (its streams, events, graphs, staging buffers)
+static void release(ovs_ctx* c) {
+    for (auto& g : c->graphs)
+        for (auto& x : g.exec)
+            if (x) cudaGraphExecDestroy(x);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
+    for (int b = 0; b < 2; ++b) {
+        if (c->step_done[b]) cudaEventDestroy(c->step_done[b]);
+        if (c->h_step[b]) cudaFreeHost(c->h_step[b]);
+    }
+    delete c;
+}
+
 int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
     if (!out) return OVS_ERR_ARG;
     *out = nullptr;
@@ -253,6 +285,7 @@ int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
     c->opts.guess = OVS_GUESS_HINT;
     c->opts.max_walk = 48;
     c->opts.collect_stats = 0;
+    c->opts.launch = OVS_LAUNCH_GRAPH;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
@@ -260,12 +293,15 @@ int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
         return OVS_ERR_NO_DEVICE;
     }
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->step_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->step_done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->h_step[0], sizeof(StepParams), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->h_step[1], sizeof(StepParams), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
-        if (c->side) cudaStreamDestroy(c->side);
-        if (c->fork) cudaEventDestroy(c->fork);
-        delete c;
+        release(c);
         return OVS_ERR_CUDA;
     }
     *out = c;
@@ -276,13 +312,8 @@ int ovs_ctx_destroy(ovs_ctx* c) {
     if (!c) return OVS_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    if (c->side) {
-        cudaStreamSynchronize(c->side);
-        cudaStreamDestroy(c->side);
-    }
-    if (c->fork) cudaEventDestroy(c->fork);
-    if (c->join) cudaEventDestroy(c->join);
-    delete c;
+    if (c->side) cudaStreamSynchronize(c->side);
+    release(c);
     return OVS_OK;
 }
 
@@ -303,6 +334,7 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     off = align_up(off + 4 * sizeof(int32_t));
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    off = align_up(off + sizeof(StepParams));
     *bytes = off;
     return OVS_OK;
 }
@@ -324,10 +356,12 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     c->d_counters = (unsigned long long*)(base + off);
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     c->d_err = (int32_t*)(base + off);
-    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // two counters: near-face and stuck queues
+    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // near-face queue, stuck queue, work counter
     off = align_up(off + 4 * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
     off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    c->d_step = (StepParams*)(base + off);
+    off = align_up(off + sizeof(StepParams));
     c->ws = dptr;
     c->ws_bytes = bytes;
     c->max_points = max_points;
@@ -494,6 +528,7 @@ int ovs_set_options(ovs_ctx* c, const ovs_options* o) {
         return fail(c, OVS_ERR_ARG, "velocity_mode %d", o->velocity_mode);
     if (o->guess < OVS_GUESS_HINT || o->guess > OVS_GUESS_MLP_ONLY) return fail(c, OVS_ERR_ARG, "guess %d", o->guess);
     if (o->max_walk < 1 || o->max_walk > 1024) return fail(c, OVS_ERR_ARG, "max_walk %d (1..1024)", o->max_walk);
+    if (o->launch != OVS_LAUNCH_DIRECT && o->launch != OVS_LAUNCH_GRAPH) return fail(c, OVS_ERR_ARG, "launch %d", o->launch);
     c->opts = *o;
     return OVS_OK;
 }
@@ -556,6 +591,96 @@ void fill_interp(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
     }
 }
 
+// Kinds of call (bit set): which kernels a call launches.  Bits 4-6: guess-network widths 32 / 64 / 128.
+constexpr uint32_t kStepAssemble = 1, kStepInterp = 2, kStepInterpF64 = 4, kStepNoAlloc = 8;
+
+int guess_width_mask(const ovs_ctx* c) {
+    int m = 0;
+    for (int g = 0; g < c->ngrids; ++g) m |= c->hidden[g] == 32 ? 1 : c->hidden[g] == 64 ? 2 : c->hidden[g] == 128 ? 4 : 0;
+    return m;
+}
+
+// The staging buffer for the next call, once the call that last read it has finished.
+cudaError_t acquire_stage(ovs_ctx* c, int* b) {
+    const int k = c->stage;
+    if (c->step_used[k]) {
+        cudaError_t e = cudaEventSynchronize(c->step_done[k]);
+        if (e != cudaSuccess) return e;
+    }
+    c->stage ^= 1;
+    *b = k;
+    return cudaSuccess;
+}
+
+// The launch sequence of one call on stream st: the parameter copy from staging buffer b, then the kernels.
+cudaError_t enqueue_step(ovs_ctx* c, int b, uint32_t kind, uint32_t* qcount, cudaStream_t st, bool trace) {
+    cudaError_t e = cudaMemcpyAsync(c->d_step, c->h_step[b], sizeof(StepParams), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const int hmask = (int)((kind >> 4) & 7);
+    if (hmask) {
+        if (trace && c->trace[5]) cudaEventRecord(c->trace[5], st);
+        if ((e = launch_guess(c->d_step, c->d_grids, hmask, c->nsm, c->tune.guess_blocks_per_sm, st)) != cudaSuccess)
+            return e;
+        if (trace && c->trace[6]) cudaEventRecord(c->trace[6], st);
+    }
+    if (kind & kStepAssemble) {
+        e = launch_assemble(&c->d_step->a, qcount, c->d_grids, c->nsm, c->tune.assemble_blocks_per_sm,
+                            c->tune.slow_blocks_per_sm, st, trace ? c->trace : nullptr, c->side, c->fork, c->join);
+        if (e != cudaSuccess) return e;
+    }
+    if (kind & kStepInterp)
+        e = launch_interp(&c->d_step->i, (kind & kStepInterpF64) != 0, c->d_grids, c->nsm,
+                          c->tune.interp_blocks_per_sm, st, trace ? c->trace + 3 : nullptr);
+    return e;
+}
+
+// Run one call whose parameters sit in staging buffer b: as the CUDA graph of its kind (captured on the kind's
+// first call, one instance per staging buffer) or as direct launches; the buffer stays busy until the call ends.
+cudaError_t run_step(ovs_ctx* c, int b, uint32_t kind, uint32_t* qcount, bool allow_graph) {
+    cudaError_t e = cudaSuccess;
+    if (allow_graph && c->opts.launch == OVS_LAUNCH_GRAPH && !c->tracing) {
+        ovs_ctx::GraphEntry* ge = nullptr;
+        for (auto& g : c->graphs)
+            if (g.kind == kind) ge = &g;
+        if (!ge) {
+            ovs_ctx::GraphEntry ng{kind, {nullptr, nullptr}};
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed);
+                if (e != cudaSuccess) break;
+                const cudaError_t e1 = enqueue_step(c, k, kind, qcount, c->gstream, false);
+                const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &graph);
+                e = e1 != cudaSuccess ? e1 : e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&ng.exec[k], graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (e != cudaSuccess) {
+                for (auto& x : ng.exec)
+                    if (x) cudaGraphExecDestroy(x);
+                return e;
+            }
+            c->graphs.push_back(ng);
+            ge = &c->graphs.back();
+        }
+        e = cudaGraphLaunch(ge->exec[b], c->stream);
+    } else {
+        e = enqueue_step(c, b, kind, qcount, c->stream, c->tracing);
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(c->step_done[b], c->stream);
+    c->step_used[b] = true;
+    return e;
+}
+
+// Forget the captured graphs (after the launch shapes change); waits for the stream first.
+void drop_graphs(ovs_ctx* c) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& g : c->graphs)
+        for (auto& x : g.exec)
+            if (x) cudaGraphExecDestroy(x);
+    c->graphs.clear();
+}
+
 int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
                   const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout) {
     if (!c) return OVS_ERR_ARG;
@@ -576,8 +701,11 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
         return fail(c, OVS_ERR_ARG, "donors.n (%lld) must equal the number of points (%lld): xi is SoA over n",
                     (long long)out->n, (long long)total);
     OVS_CUDA(c, cudaSetDevice(c->device));
-    AsmParams* P = new (std::nothrow) AsmParams();
-    if (!P) return fail(c, OVS_ERR_ARG, "host allocation failed");
+    int b = 0;
+    OVS_CUDA(c, acquire_stage(c, &b));
+    StepParams& S = *c->h_step[b];
+    AsmParams* P = &S.a;
+    memset(P, 0, offsetof(AsmParams, s));
     P->nsets = nsets;
     P->xi_f64 = out->xi_dtype == OVS_F64;
     P->max_walk = c->opts.max_walk;
@@ -595,31 +723,23 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     P->queue_count = c->d_qcount;
     P->counters = c->d_counters;
     P->err = c->d_err;
+    P->guess_used = c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr;
+    P->guess_always = c->opts.guess == OVS_GUESS_MLP_ONLY;
     fill_sets(sets, nsets, P->s);
     fill_xforms(c, sets, nsets, P->xf);
     memcpy(P->m, c->motion, sizeof P->m);
-    InterpParams* I = nullptr;
+    uint32_t kind = kStepAssemble;
     if (fout) {
-        I = new (std::nothrow) InterpParams();
-        if (!I) {
-            delete P;
-            return fail(c, OVS_ERR_ARG, "host allocation failed");
-        }
-        fill_interp(c, sets, nsets, out, fields, fout, total, I);
+        memset(&S.i, 0, offsetof(InterpParams, s));
+        fill_interp(c, sets, nsets, out, fields, fout, total, &S.i);
+        kind |= kStepInterp | (S.i.f64 ? kStepInterpF64 : 0);
     }
-    cudaError_t e = cudaSuccess;
-    bool any_net = false;
-    for (int g = 0; g < c->ngrids; ++g) any_net = any_net || c->hidden[g] > 0;
-    if (mlp && any_net && c->tracing && c->trace[5]) cudaEventRecord(c->trace[5], c->stream);
-    if (mlp && any_net)
-        e = launch_guess(*P, c->d_grids, c->hidden, c->opts.guess == OVS_GUESS_MLP_ONLY, c->nsm,
-                         c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr, c->stream);
-    if (mlp && any_net && c->tracing && c->trace[6]) cudaEventRecord(c->trace[6], c->stream);
-    if (e == cudaSuccess)
-        e = launch_assemble(*P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork, c->join);
-    if (e == cudaSuccess && I) e = launch_interp(*I, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
-    delete P;
-    delete I;
+    const int hmask = mlp ? guess_width_mask(c) : 0;
+    if (hmask) {
+        fill_guess_work(*P, c->hidden, S.w);
+        kind |= (uint32_t)hmask << 4;
+    }
+    cudaError_t e = run_step(c, b, kind, c->d_qcount, true);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble launch");
     return OVS_OK;
 }
@@ -652,11 +772,12 @@ int ovs_interpolate(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const
     if (rc != OVS_OK) return rc;
     if (!in->grid || !in->cell || !in->xi || !in->status) return fail(c, OVS_ERR_ARG, "donors array is NULL");
     OVS_CUDA(c, cudaSetDevice(c->device));
-    InterpParams* P = new (std::nothrow) InterpParams();
-    if (!P) return fail(c, OVS_ERR_ARG, "host allocation failed");
+    int b = 0;
+    OVS_CUDA(c, acquire_stage(c, &b));
+    InterpParams* P = &c->h_step[b]->i;
+    memset(P, 0, offsetof(InterpParams, s));
     fill_interp(c, sets, nsets, in, fields, out, total, P);
-    cudaError_t e = launch_interp(*P, c->d_grids, c->stream, c->tracing ? c->trace + 3 : nullptr);
-    delete P;
+    cudaError_t e = run_step(c, b, kStepInterp | (P->f64 ? kStepInterpF64 : 0), c->d_qcount, true);
     if (e != cudaSuccess) return cuda_fail(c, e, "interpolate launch");
     return OVS_OK;
 }
@@ -870,6 +991,101 @@ int ovs_reset_hints(ovs_ctx* c) {
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------------------
+// launch shapes and the autotuner
+extern "C" {
+
+int ovs_set_tuning(ovs_ctx* c, const ovs_tuning* t) {
+    if (!c) return OVS_ERR_ARG;
+    ovs_tuning v = t ? *t : ovs_tuning{0, 0, 0, 0};
+    if (v.assemble_blocks_per_sm < 0 || v.assemble_blocks_per_sm > 12 || v.interp_blocks_per_sm < 0 ||
+        v.interp_blocks_per_sm > 32 || v.slow_blocks_per_sm < 0 || v.slow_blocks_per_sm > 8 ||
+        v.guess_blocks_per_sm < 0 || v.guess_blocks_per_sm > 32)
+        return fail(c, OVS_ERR_ARG, "tuning out of range (%d, %d, %d, %d)", v.assemble_blocks_per_sm,
+                    v.interp_blocks_per_sm, v.slow_blocks_per_sm, v.guess_blocks_per_sm);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    drop_graphs(c);
+    c->tune = v;
+    return OVS_OK;
+}
+
+int ovs_get_tuning(const ovs_ctx* c, ovs_tuning* t) {
+    if (!c || !t) return OVS_ERR_ARG;
+    *t = c->tune;
+    return OVS_OK;
+}
+
+int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                 const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t reps,
+                 ovs_tuning* best) {
+    if (!c) return OVS_ERR_ARG;
+    if (reps < 1 || reps > 1000) return fail(c, OVS_ERR_ARG, "reps = %d (1..1000)", reps);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    const int saved_launch = c->opts.launch;
+    const ovs_tuning saved = c->tune;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, cudaGetLastError(), "autotune events");
+    }
+    // candidates run as direct launches (no capture per candidate)
+    c->opts.launch = OVS_LAUNCH_DIRECT;
+    auto trial = [&](const ovs_tuning& t, float* ms) -> int {
+        c->tune = t;
+        int rc = assemble_impl(c, sets, nsets, out, fields, nfields, fout);  // untimed
+        if (rc != OVS_OK) return rc;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "autotune");
+        for (int r = 0; r < reps && rc == OVS_OK; ++r) rc = assemble_impl(c, sets, nsets, out, fields, nfields, fout);
+        if (rc != OVS_OK) return rc;
+        cudaError_t e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune timing");
+        *ms /= (float)reps;
+        return OVS_OK;
+    };
+    const int occ = interp_default_blocks_per_sm(false);
+    ovs_tuning cur = {3, occ > 0 ? occ : 4, 1, kGuessBlocksPerSM};
+    const bool learned = (c->opts.guess == OVS_GUESS_MLP || c->opts.guess == OVS_GUESS_MLP_ONLY) && guess_width_mask(c);
+    float best_ms = 0.f;
+    int rc = trial(cur, &best_ms);
+    const int cand_asm[] = {1, 2, 3, 4, 6};
+    const int cand_slow[] = {1, 2, 4};
+    const int cand_guess[] = {4, 8, 16};
+    int cand_interp[4] = {std::max(1, cur.interp_blocks_per_sm / 2), cur.interp_blocks_per_sm,
+                          std::min(32, 2 * cur.interp_blocks_per_sm), std::min(32, 4 * cur.interp_blocks_per_sm)};
+    auto sweep = [&](int32_t ovs_tuning::*knob, const int* vals, int nv) {
+        for (int k = 0; k < nv && rc == OVS_OK; ++k) {
+            if (vals[k] == cur.*knob) continue;
+            ovs_tuning t = cur;
+            t.*knob = vals[k];
+            float ms = 0.f;
+            rc = trial(t, &ms);
+            if (rc == OVS_OK && ms < 0.99f * best_ms) {
+                cur = t;
+                best_ms = ms;
+            }
+        }
+    };
+    if (rc == OVS_OK) sweep(&ovs_tuning::assemble_blocks_per_sm, cand_asm, 5);
+    if (rc == OVS_OK) sweep(&ovs_tuning::slow_blocks_per_sm, cand_slow, 3);
+    if (rc == OVS_OK && fout) sweep(&ovs_tuning::interp_blocks_per_sm, cand_interp, 4);
+    if (rc == OVS_OK && learned) sweep(&ovs_tuning::guess_blocks_per_sm, cand_guess, 3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->opts.launch = saved_launch;
+    if (rc != OVS_OK) {
+        c->tune = saved;
+        return rc;
+    }
+    drop_graphs(c);
+    c->tune = cur;
+    if (best) *best = cur;
+    return OVS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------------
 // ovs_assemble_noalloc: the slow-path queue of k_assemble in a fixed device array instead of the context
 // workspace (see include/ovs.h for who needs this and its limits).
 //
@@ -931,8 +1147,12 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
         }
         base = g_noalloc_ptr[c->device];
     }
-    AsmParams P;  // on the stack: this entry point allocates nothing, not even host memory
-    memset(&P, 0, sizeof P);
+    // parameters in the context's pinned staging buffer (made with the context), launched directly: capturing a
+    // graph would allocate
+    int b = 0;
+    OVS_CUDA(c, acquire_stage(c, &b));
+    AsmParams& P = c->h_step[b]->a;
+    memset(&P, 0, offsetof(AsmParams, s));
     P.nsets = nsets;
     P.xi_f64 = out->xi_dtype == OVS_F64;
     P.max_walk = c->opts.max_walk;
@@ -944,15 +1164,14 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     P.out_cell = out->cell;
     P.out_xi = out->xi;
     P.out_status = out->status;
-    P.queue_count = (uint32_t*)base;  // two counters, zeroed on the stream by launch_assemble before the kernels run
+    P.queue_count = (uint32_t*)base;  // three counters, zeroed on the stream by launch_assemble before the kernels
     P.queue = (SlowEntry*)((char*)base + kNoAllocHead);
     P.counters = c->d_counters;
     P.err = c->d_err;
     fill_sets(sets, nsets, P.s);
     fill_xforms(c, sets, nsets, P.xf);
     memcpy(P.m, c->motion, sizeof P.m);
-    cudaError_t e = launch_assemble(P, c->d_grids, c->stream, c->tracing ? c->trace : nullptr, c->side, c->fork,
-                                    c->join);
+    cudaError_t e = run_step(c, b, kStepAssemble | kStepNoAlloc, (uint32_t*)base, false);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble (no-alloc) launch");
     return OVS_OK;
 }

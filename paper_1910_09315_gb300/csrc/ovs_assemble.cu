@@ -137,9 +137,9 @@ __device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned v) {
     if (lane_id() == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
-__global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const __grid_constant__ AsmParams P,
-                                                                         const GridDev* __restrict__ G) {
-    const int64_t t = blockIdx.x * (int64_t)kAsmThreads + threadIdx.x;
+// One query point per thread (t may lie past the end: the lane then only takes part in the warp's collective
+// steps).  All lanes of a warp call it together.
+__device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev* __restrict__ G, const int64_t t) {
     const bool active = t < P.total;
     bool slow = false;
     SlowEntry e;
@@ -272,6 +272,23 @@ __global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const _
     if (P.stats) {
         warp_add(P.counters + kCtrPoints, active ? 1u : 0u);
         warp_add(P.counters + kCtrWalk, (unsigned)steps);
+    }
+}
+
+// Persistent: a fixed grid (a multiple of the SM count, so that a captured step graph fits every call) whose
+// warps take work items of 32 consecutive points of the call (all sets of all grids in one index space) from a
+// counter, so that uneven walks balance across the GPU.
+__global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const AsmParams* __restrict__ Pp,
+                                                                         const GridDev* __restrict__ G) {
+    const AsmParams& P = *Pp;
+    const int64_t total = P.total;
+    const unsigned lane = lane_id();
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(P.queue_count + 2, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)base >= total) break;
+        assemble_point(P, G, (int64_t)base + lane);
     }
 }
 
@@ -522,8 +539,9 @@ __device__ __forceinline__ void finish_none(const AsmParams& P, int64_t t) {
 
 // Points near a face: one warp each, one lane per candidate cell.  A point whose candidates all fail (or a
 // later donor of its list) gets the warp-level exhaustive search.
-__global__ void __launch_bounds__(kSlowThreads) k_slow_near(const __grid_constant__ AsmParams P,
+__global__ void __launch_bounds__(kSlowThreads) k_slow_near(const AsmParams* __restrict__ Pp,
                                                             const GridDev* __restrict__ G) {
+    const AsmParams& P = *Pp;
     uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
     unsigned nref = 0, nfb = 0;
@@ -574,8 +592,9 @@ constexpr int kMaxCand = 128;
 
 // Stuck walks (points outside the grid, or where the walk gave up): one block each.  All threads filter the
 // control cell's list (box, slabs, FP32 Newton); warp 0 applies the donor predicate to the survivors.
-__global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const __grid_constant__ AsmParams P,
+__global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const AsmParams* __restrict__ Pp,
                                                              const GridDev* __restrict__ G) {
+    const AsmParams& P = *Pp;
     __shared__ uint32_t cand[kMaxCand];
     __shared__ float cxi[kMaxCand][3];
     __shared__ int ncand;
@@ -682,13 +701,16 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const __grid_consta
 
 }  // namespace
 
-cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev,
-                            cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-    cudaError_t err = cudaMemsetAsync(P.queue_count, 0, 2 * sizeof(uint32_t), st);
+cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const GridDev* dgrids, int nsm,
+                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev, cudaStream_t side,
+                            cudaEvent_t fork, cudaEvent_t join) {
+    const unsigned ab = (unsigned)(nsm * (asm_bps > 0 ? asm_bps : kAsmMinBlocks));
+    const unsigned sb = (unsigned)(nsm * (slow_bps > 0 ? slow_bps : 1));
+    // the two queue counters and the work counter
+    cudaError_t err = cudaMemsetAsync(queue_count, 0, 3 * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
-    int64_t blocks = (P.total + kAsmThreads - 1) / kAsmThreads;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    k_assemble<<<(unsigned)blocks, kAsmThreads, 0, st>>>(P, dgrids);
+    k_assemble<<<ab, kAsmThreads, 0, st>>>(dP, dgrids);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
@@ -696,13 +718,13 @@ cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStrea
         // the two slow-path kernels work on disjoint queues: run them side by side
         if ((err = cudaEventRecord(fork, st)) != cudaSuccess) return err;
         if ((err = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return err;
-        k_slow_stuck<<<152, kSlowThreads, 0, side>>>(P, dgrids);
-        k_slow_near<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+        k_slow_stuck<<<sb, kSlowThreads, 0, side>>>(dP, dgrids);
+        k_slow_near<<<sb, kSlowThreads, 0, st>>>(dP, dgrids);
         if ((err = cudaEventRecord(join, side)) != cudaSuccess) return err;
         if ((err = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return err;
     } else {
-        k_slow_near<<<152, kSlowThreads, 0, st>>>(P, dgrids);
-        k_slow_stuck<<<152, kSlowThreads, 0, st>>>(P, dgrids);
+        k_slow_near<<<sb, kSlowThreads, 0, st>>>(dP, dgrids);
+        k_slow_stuck<<<sb, kSlowThreads, 0, st>>>(dP, dgrids);
     }
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();

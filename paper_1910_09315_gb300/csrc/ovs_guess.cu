@@ -398,9 +398,12 @@ __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ reg
 // on the gathered rows, and the guessed cell becomes the receiver node's hint.  A block stages a network only
 // when its chunk's donor grid changes.
 template <int H>
-__global__ void __launch_bounds__(128, kGuessBlocksPerSM) k_guess(const __grid_constant__ AsmParams P, const __grid_constant__ GuessWork W,
-                                                  const GridDev* __restrict__ G, int always,
-                                                  unsigned long long* __restrict__ used) {
+__global__ void __launch_bounds__(128, kGuessBlocksPerSM) k_guess(const StepParams* __restrict__ Sp,
+                                                                   const GridDev* __restrict__ G) {
+    const AsmParams& P = Sp->a;
+    const GuessWork& W = Sp->w[H == 32 ? 0 : (H == 64 ? 1 : 2)];
+    const int always = P.guess_always;
+    unsigned long long* __restrict__ used = P.guess_used;
     constexpr int kPer = kGuessChunk / 128;
     __shared__ MlpSmem<H> S;
     __shared__ float4 rows[kGuessChunk + 16];  // xyz = network input, w = receiver node (bits)
@@ -585,34 +588,30 @@ cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, const int* hidden, int always, int nsm,
-                         unsigned long long* used, cudaStream_t st) {
-    // one launch per network width present; blocks over the chunks of the sets whose first donor has one
-    for (int H : {32, 64, 128}) {
-        GuessWork W;
+void fill_guess_work(const AsmParams& P, const int* hidden, GuessWork Wk[3]) {
+    const int widths[3] = {32, 64, 128};
+    for (int h = 0; h < 3; ++h) {
+        GuessWork& W = Wk[h];
         W.nsets = 0;
         int64_t chunks = 0;
         for (int s = 0; s < P.nsets; ++s) {
-            if (hidden[P.s[s].donors[0]] != H || P.s[s].n <= 0) continue;
+            if (hidden[P.s[s].donors[0]] != widths[h] || P.s[s].n <= 0) continue;
             W.set[W.nsets] = s;
             W.chunk_begin[W.nsets] = chunks;
             chunks += (P.s[s].n + kGuessChunk - 1) / kGuessChunk;
             ++W.nsets;
         }
         W.chunk_begin[W.nsets] = chunks;
-        if (chunks == 0) continue;
-        // persistent: as many blocks as fit at once (the launch bound's blocks per SM), or fewer when there are
-        // fewer chunks
-        const unsigned blocks = (unsigned)std::min<int64_t>(chunks, (int64_t)nsm * kGuessBlocksPerSM);
-        switch (H) {
-            case 32: k_guess<32><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
-            case 64: k_guess<64><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
-            default: k_guess<128><<<blocks, 128, 0, st>>>(P, W, dgrids, always, used); break;
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+}
+
+cudaError_t launch_guess(const StepParams* dS, const GridDev* dgrids, int hmask, int nsm, int bps, cudaStream_t st) {
+    // one persistent launch per network width present; its blocks walk that width's chunk list (possibly empty)
+    const unsigned blocks = (unsigned)(nsm * (bps > 0 ? bps : kGuessBlocksPerSM));
+    if (hmask & 1) k_guess<32><<<blocks, 128, 0, st>>>(dS, dgrids);
+    if (hmask & 2) k_guess<64><<<blocks, 128, 0, st>>>(dS, dgrids);
+    if (hmask & 4) k_guess<128><<<blocks, 128, 0, st>>>(dS, dgrids);
+    return cudaGetLastError();
 }
 
 }  // namespace ovs

@@ -17,16 +17,6 @@ struct MlpHeader {
     int32_t pad[8];
 };
 
-// The sets of a call whose first donor grid has a network of one width, cut into chunks of kGuessChunk points
-// (a chunk never crosses a set): chunk b is chunk b - chunk_begin[w] of set set[w].
-constexpr int kGuessChunk = 256;
-constexpr int kGuessBlocksPerSM = 8;  // k_guess: 128 threads at up to 64 registers
-struct GuessWork {
-    int32_t nsets;
-    int32_t set[OVS_MAX_SETS];
-    int64_t chunk_begin[OVS_MAX_SETS + 1];
-};
-
 constexpr int kMlpMaxHidden = 128;
 constexpr int kMlpMaxParams = kMlpMaxHidden * kMlpMaxHidden + 8 * kMlpMaxHidden + 3;
 constexpr size_t kMlpAlign(size_t v) { return (v + 255) / 256 * 256; }
@@ -53,7 +43,9 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr
 cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t st);
 cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_t n, float* out, cudaStream_t st);
 // always = 1: every point of a set whose first donor has a network gets its guess (hints ignored).
-cudaError_t launch_guess(const AsmParams& P, const GridDev* dgrids, const int* hidden, int always, int nsm,
-                         unsigned long long* used, cudaStream_t st);
+// hmask: bit 0/1/2 for networks of width 32/64/128 present on some grid (one launch each)
+cudaError_t launch_guess(const StepParams* dS, const GridDev* dgrids, int hmask, int nsm, int bps, cudaStream_t st);
+// host side: the work lists of a call, from the set table and the grids' network widths
+void fill_guess_work(const AsmParams& P, const int* hidden, GuessWork W[3]);
 
 }  // namespace ovs

@@ -165,9 +165,12 @@ struct AsmParams {
     void* out_xi;
     uint8_t* out_status;
     SlowEntry* queue;
-    uint32_t* queue_count;
+    uint32_t* queue_count;  // [0] near-face queue, [1] stuck queue, [2] work counter of k_assemble
     unsigned long long* counters;
     int32_t* err;
+    unsigned long long* guess_used;  // learned-guess statistics counter, or NULL
+    int32_t guess_always;            // 1: every point of a set with a network gets a guess (hints ignored)
+    int32_t pad2;
     SetDev s[OVS_MAX_SETS];
     XfFF xf[OVS_MAX_SETS];
     MotionDev m[OVS_MAX_GRIDS];
@@ -191,6 +194,25 @@ struct InterpParams {
     MotionDev m[OVS_MAX_GRIDS];
     MotionF mf[OVS_MAX_GRIDS];
     FieldsDev fields[OVS_MAX_GRIDS];
+};
+
+// The sets of a call whose first donor grid has a network of one width, cut into chunks of kGuessChunk points
+// (a chunk never crosses a set): chunk b is chunk b - chunk_begin[w] of set set[w].
+constexpr int kGuessChunk = 256;
+constexpr int kGuessBlocksPerSM = 8;  // k_guess: 128 threads at up to 64 registers
+struct GuessWork {
+    int32_t nsets;
+    int32_t set[OVS_MAX_SETS];
+    int64_t chunk_begin[OVS_MAX_SETS + 1];
+};
+
+// Everything a step's kernels read, in one block of device memory written by one host-to-device copy per step
+// (so that a captured step graph stays valid from one step to the next): the assembly's and the interpolation's
+// parameters and the learned guess's work lists for hidden widths 32, 64 and 128.
+struct StepParams {
+    AsmParams a;
+    InterpParams i;
+    GuessWork w[3];
 };
 
 // error bits of the device status word
@@ -606,8 +628,14 @@ size_t scan_scratch_elems(int64_t n);
 // ev: 3 optional events (before the fast kernel, after it, after the slow kernels); 2 for interpolation.
 // side/fork/join: a second stream and two events for running the two slow-path kernels concurrently (null:
 // everything on st).
-cudaError_t launch_assemble(const AsmParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev,
-                            cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
-cudaError_t launch_interp(const InterpParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev);
+// asm_bps / slow_bps: blocks per SM of the persistent assembly and slow-path grids (0: defaults)
+cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const GridDev* dgrids, int nsm,
+                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev, cudaStream_t side,
+                            cudaEvent_t fork, cudaEvent_t join);
+// blocks of k_interp resident per SM (occupancy calculator), or a negative CUDA error
+int interp_default_blocks_per_sm(bool f64);
+// bps: blocks per SM of the persistent grid (0: the occupancy calculator's figure)
+cudaError_t launch_interp(const InterpParams* dI, bool f64, const GridDev* dgrids, int nsm, int bps, cudaStream_t st,
+                          cudaEvent_t const* ev);
 
 }  // namespace ovs

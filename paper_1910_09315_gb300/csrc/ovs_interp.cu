@@ -50,21 +50,44 @@ __device__ __forceinline__ void interp_one(const InterpParams& P, const GridDev*
                     cell, u, v, w, P.out, t);
 }
 
+// Persistent grid (a multiple of the SM count), grid-stride over the call's points.
 template <typename T>
-__global__ void __launch_bounds__(kInterpThreads) k_interp(const __grid_constant__ InterpParams P,
+__global__ void __launch_bounds__(kInterpThreads) k_interp(const InterpParams* __restrict__ Pp,
                                                            const GridDev* __restrict__ G) {
-    const int64_t t = blockIdx.x * (int64_t)kInterpThreads + threadIdx.x;
-    if (t >= P.total) return;
-    interp_one<T>(P, G, t, __ldg(P.in_status + t));
+    const InterpParams& P = *Pp;
+    const int64_t total = P.total;
+    for (int64_t t = blockIdx.x * (int64_t)kInterpThreads + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * kInterpThreads)
+        interp_one<T>(P, G, t, __ldg(P.in_status + t));
 }
 
 }  // namespace
 
-cudaError_t launch_interp(const InterpParams& P, const GridDev* dgrids, cudaStream_t st, cudaEvent_t const* ev) {
-    int64_t blocks = (P.total + kInterpThreads - 1) / kInterpThreads;
+int interp_default_blocks_per_sm(bool f64) {
+    // blocks resident per SM at once, from the occupancy calculator (the same for every call on a device)
+    static int per_sm[2] = {0, 0};
+    int& bps = per_sm[f64 ? 1 : 0];
+    if (bps <= 0) {
+        int v = 0;
+        cudaError_t e = f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_interp<double>, kInterpThreads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_interp<float>, kInterpThreads, 0);
+        if (e != cudaSuccess) return -(int)e;
+        bps = v < 1 ? 1 : v;
+    }
+    return bps;
+}
+
+cudaError_t launch_interp(const InterpParams* dI, bool f64, const GridDev* dgrids, int nsm, int tuned_bps,
+                          cudaStream_t st, cudaEvent_t const* ev) {
+    int bps = tuned_bps;
+    if (bps <= 0) {
+        bps = interp_default_blocks_per_sm(f64);
+        if (bps < 0) return (cudaError_t)(-bps);
+    }
+    const unsigned blocks = (unsigned)(nsm * bps);
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    if (P.f64) k_interp<double><<<(unsigned)blocks, kInterpThreads, 0, st>>>(P, dgrids);
-    else k_interp<float><<<(unsigned)blocks, kInterpThreads, 0, st>>>(P, dgrids);
+    if (f64) k_interp<double><<<blocks, kInterpThreads, 0, st>>>(dI, dgrids);
+    else k_interp<float><<<blocks, kInterpThreads, 0, st>>>(dI, dgrids);
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
     return cudaGetLastError();
 }

@@ -43,6 +43,8 @@ OVS_GUESS_HINT = 0
 OVS_GUESS_BINS = 1
 OVS_GUESS_MLP = 2
 OVS_GUESS_MLP_ONLY = 3
+OVS_LAUNCH_DIRECT = 0
+OVS_LAUNCH_GRAPH = 1
 
 EXPORTS = [
     "ovs_ctx_create", "ovs_ctx_destroy", "ovs_last_error", "ovs_set_stream", "ovs_workspace_size",
@@ -50,7 +52,7 @@ EXPORTS = [
     "ovs_get_options", "ovs_assemble", "ovs_interpolate", "ovs_sync", "ovs_get_stats", "ovs_reset_hints",
     "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate", "ovs_guess_param_count",
     "ovs_train_workspace_size", "ovs_train_guess", "ovs_guess_get_params", "ovs_guess_set_params",
-    "ovs_guess_eval", "ovs_mlp_loss_grad",
+    "ovs_guess_eval", "ovs_mlp_loss_grad", "ovs_set_tuning", "ovs_get_tuning", "ovs_autotune",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -83,7 +85,12 @@ class ovs_fields_out(ctypes.Structure):
 
 class ovs_options(ctypes.Structure):
     _fields_ = [("velocity_mode", ctypes.c_int32), ("guess", ctypes.c_int32), ("max_walk", ctypes.c_int32),
-                ("collect_stats", ctypes.c_int32)]
+                ("collect_stats", ctypes.c_int32), ("launch", ctypes.c_int32)]
+
+
+class ovs_tuning(ctypes.Structure):
+    _fields_ = [("assemble_blocks_per_sm", ctypes.c_int32), ("interp_blocks_per_sm", ctypes.c_int32),
+                ("slow_blocks_per_sm", ctypes.c_int32), ("guess_blocks_per_sm", ctypes.c_int32)]
 
 
 class ovs_stats(ctypes.Structure):
@@ -147,6 +154,10 @@ def load(path: Optional[str] = None):
         "ovs_guess_set_params": [V, I32, I32, V],
         "ovs_guess_eval": [V, I32, I64, V, V],
         "ovs_mlp_loss_grad": [V, I32, I64, V, V, V, V, V],
+        "ovs_set_tuning": [V, ctypes.POINTER(ovs_tuning)],
+        "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
+        "ovs_autotune": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors), ctypes.POINTER(ovs_fields),
+                         I32, ctypes.POINTER(ovs_fields_out), I32, ctypes.POINTER(ovs_tuning)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -231,6 +242,25 @@ def ovs_assemble(ctx, sets, nsets: int, donors: ovs_donors):
 def ovs_assemble_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
     _check(ctx, load().ovs_assemble_interpolate(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
                                                 ctypes.byref(out)))
+
+
+def ovs_set_tuning(ctx, t):
+    """t: ovs_tuning or None (defaults)."""
+    _check(ctx, load().ovs_set_tuning(ctx, ctypes.byref(t) if t is not None else None))
+
+
+def ovs_get_tuning(ctx) -> ovs_tuning:
+    t = ovs_tuning()
+    _check(ctx, load().ovs_get_tuning(ctx, ctypes.byref(t)))
+    return t
+
+
+def ovs_autotune(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out, reps: int) -> ovs_tuning:
+    """out: ovs_fields_out or None (tune ovs_assemble alone)."""
+    best = ovs_tuning()
+    _check(ctx, load().ovs_autotune(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
+                                    ctypes.byref(out) if out is not None else None, int(reps), ctypes.byref(best)))
+    return best
 
 
 def ovs_assemble_noalloc(ctx, sets, nsets: int, donors: ovs_donors):
@@ -455,6 +485,25 @@ class Context:
         ovs_assemble_interpolate(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr,
                                  len(self.grids), o)
         return donors, out
+
+    def autotune(self, sets, fields=None, donors=None, out=None, reps: int = 5, xi_dtype: int = OVS_F32) -> dict:
+        """ovs_autotune on this call (with interpolation when fields are given); returns the chosen shapes."""
+        n = sum(int(s[1].numel()) for s in sets)
+        if donors is None:
+            donors = self.alloc_donors(n, xi_dtype)
+        if fields is not None:
+            farr, o, out = self._fields_structs(fields, n, out)
+            best = ovs_autotune(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr,
+                                len(self.grids), o, reps)
+        else:
+            best = ovs_autotune(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), None, 0, None, reps)
+        return {k: getattr(best, k) for k, _ in ovs_tuning._fields_}
+
+    def set_tuning(self, **kw):
+        t = ovs_get_tuning(self.ctx)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        ovs_set_tuning(self.ctx, t)
 
     def train_guess(self, gid: int, cells, xi, init_params, hidden: int = 64, epochs: int = 5, batch: int = 8192,
                     lr: float = 3e-3, lr_final: float = 0.0) -> float:

@@ -40,14 +40,15 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_header(tmp_path):
     structs = {"ovs_grid_desc": ovs.ovs_grid_desc, "ovs_fringe_set": ovs.ovs_fringe_set, "ovs_donors": ovs.ovs_donors,
                "ovs_fields": ovs.ovs_fields, "ovs_fields_out": ovs.ovs_fields_out, "ovs_options": ovs.ovs_options,
-               "ovs_stats": ovs.ovs_stats, "ovs_train_desc": ovs.ovs_train_desc}
+               "ovs_stats": ovs.ovs_stats, "ovs_train_desc": ovs.ovs_train_desc, "ovs_tuning": ovs.ovs_tuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ovs.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for fname, _ in cls._fields_:
             lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
     for macro in ("OVS_MAX_GRIDS", "OVS_MAX_SETS", "OVS_MAX_DONORS", "OVS_STATUS_FALLBACK", "OVS_STATUS_REFINED",
-                  "OVS_ERR_NO_DEVICE", "OVS_GUESS_MLP", "OVS_GUESS_MLP_ONLY", "OVS_VEL_NONE"):
+                  "OVS_ERR_NO_DEVICE", "OVS_GUESS_MLP", "OVS_GUESS_MLP_ONLY", "OVS_VEL_NONE", "OVS_LAUNCH_DIRECT",
+                  "OVS_LAUNCH_GRAPH"):
         lines.append(f'printf("{macro} %d\\n", (int)({macro}));')
     lines.append("return 0;}")
     c = tmp_path / "probe.c"
@@ -60,7 +61,8 @@ def test_struct_layout_matches_header(tmp_path):
         for fname, _ in cls._fields_:
             assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
     for macro in ("OVS_MAX_GRIDS", "OVS_MAX_SETS", "OVS_MAX_DONORS", "OVS_STATUS_FALLBACK", "OVS_STATUS_REFINED",
-                  "OVS_ERR_NO_DEVICE", "OVS_GUESS_MLP", "OVS_GUESS_MLP_ONLY", "OVS_VEL_NONE"):
+                  "OVS_ERR_NO_DEVICE", "OVS_GUESS_MLP", "OVS_GUESS_MLP_ONLY", "OVS_VEL_NONE", "OVS_LAUNCH_DIRECT",
+                  "OVS_LAUNCH_GRAPH"):
         assert int(got[macro]) == getattr(ovs, macro), macro
 
 
