@@ -45,7 +45,12 @@ WORKLOADS = {
     "cfg1": "moving ellipsoid: stretched curvilinear bg 128^3 + O-grid 96x64x64, 100 steps dt=1e-3, FP32 fields",
     "cfg0": "tiny: Cartesian bg 64^3 + rotated perturbed box 32^3, FP64 fields",
     "cfg2": "moving ellipsoid with bg 256^3 (plain guess), FP32 fields",
+    "cfg3": "school of 8 fish O-grids (48x32x32..128x64x64) in a stretched bg 384x256x128, dt=1.39e-3, FP32 fields",
+    "cfg4": "school of 16 fish O-grids (64^3..160x96x96) in a stretched bg 512x384x256 (~50M nodes), FP32 fields",
 }
+# distinct time steps a run cycles through (a triangle wave over the first ones): building the fringe sets of a
+# step takes seconds on the host for the school workloads
+DISTINCT_STEPS = {"cfg3": 16, "cfg4": 8}
 
 
 def parse():
@@ -55,6 +60,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ovs", choices=["ovs", "reference"])
     ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points per CPU-baseline sample (0: auto)")
     return ap.parse_args()
@@ -160,12 +166,13 @@ def build_workload(name: str):
     return sc
 
 
-def step_inputs(sc, nsteps_total: int):
+def step_inputs(sc, nsteps_total: int, distinct: int = 0):
     """Motions and fringe sets of every step the run visits (host, precomputed outside the timed region)."""
     cache = {}
     out = []
+    n = min(sc.nsteps, distinct) if distinct else sc.nsteps
     for s in range(nsteps_total):
-        ts = schedule(sc.nsteps, s)
+        ts = schedule(n, s)
         if ts not in cache:
             m = sc.motion(ts)
             cache[ts] = (m, sc.fringe_sets(ts, m))
@@ -185,7 +192,7 @@ def run_ovs(args, rank, world, local):
     torch.cuda.set_device(dev)
     sc = build_workload(args.workload)
     K, W = args.steps, args.warmup
-    inputs = step_inputs(sc, W + K)
+    inputs = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0))
     max_pts = max(sum(len(s.node_ids) for s in fs) for _, fs in inputs)
     xi_dtype = ovs.OVS_F64 if sc.field_dtype == np.float64 else ovs.OVS_F32
     stream = torch.cuda.current_stream(dev)
@@ -230,39 +237,56 @@ def run_ovs(args, rank, world, local):
             e.record(stream)  # torch creates the CUDA event on its first record
         return out
 
-    def timed(fused: bool):
+    def timed(fused: bool, trace: bool):
         """K steps enqueued back to back (the host runs ahead as in a time loop); an L2 flush before each step
-        sits outside its events; one synchronisation at the end."""
-        e0, e1, tr = events(K), events(K), [events(5) for _ in range(K)]
+        sits outside its events; one synchronisation at the end.  trace: the library's trace events around its
+        kernels (per-kernel times; launches are then direct, not the captured graph)."""
+        e0, e1 = events(K), events(K)
+        tr = [events(5) for _ in range(K)] if trace else None
         torch.cuda.synchronize()
         n = 0
         for k, s in enumerate(range(W, W + K)):
             flush.zero_()
-            ovs.ovs_set_trace_events(ctx.ctx, tr[k])
+            if trace:
+                ovs.ovs_set_trace_events(ctx.ctx, tr[k])
             e0[k].record(stream)
             n += one_step(s, dev_sets[s], fused=fused)
             e1[k].record(stream)
         torch.cuda.synchronize()
         ovs.ovs_set_trace_events(ctx.ctx, [])
         step = [e0[k].elapsed_time(e1[k]) for k in range(K)]
+        if not trace:
+            return n, step, None, None, None
         fast = [tr[k][0].elapsed_time(tr[k][1]) for k in range(K)]
         slow = [tr[k][1].elapsed_time(tr[k][2]) for k in range(K)]
         interp = [tr[k][3].elapsed_time(tr[k][4]) for k in range(K)]
         return n, step, fast, slow, interp
 
+    # launch shapes: the library's autotuner on the last warm-up step (its calls run for real)
+    nw = sum(int(x[1].numel()) for x in dev_sets[W - 1])
+    tuning = ctx.autotune(dev_sets[W - 1], fields, donors=donors_view(nw), out=[o[:nw] for o in outs], reps=3,
+                          xi_dtype=xi_dtype)
+    for s in range(W):
+        one_step(s, dev_sets[s])
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    pts, step_ms, fast_ms, slow_ms, interp_ms = timed(True)
+    pts, step_ms, _, _, _ = timed(True, trace=False)
     ck = clocks.stop()
     total_ms = float(np.sum(step_ms))
-    # the same steps through the two separate calls (ovs_assemble, then ovs_interpolate), for comparison
+    # the same steps again with per-kernel events (direct launches): breakdown and roofline
+    _, traced_ms, fast_ms, slow_ms, interp_ms = timed(True, trace=True)
+    # direct launches without tracing, and the two separate calls (ovs_assemble, then ovs_interpolate)
+    ctx.set_options(launch=ovs.OVS_LAUNCH_DIRECT)
+    _, direct_ms, _, _, _ = timed(True, trace=False)
+    ctx.set_options(launch=ovs.OVS_LAUNCH_GRAPH)
     for s in range(W):
         one_step(s, dev_sets[s], fused=False)
-    _, sep_ms, _, sep_slow, sep_int = timed(False)
-    learned = learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, W, ovs, torch)
+    _, sep_ms, _, _, _ = timed(False, trace=False)
+    learned = None if args.no_learned else learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush,
+                                                            K, W, ovs, torch)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
     host_out = [torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)]
     host_status = torch.empty(max_pts, dtype=torch.uint8).pin_memory()
@@ -309,18 +333,22 @@ def run_ovs(args, rank, world, local):
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "points_per_step": pts_per_step,
                    "guess": "previous-donor hint + control-cell bins (plain)", "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MB write) between timed steps", "timing": "per-step CUDA events, steps enqueued back to back",
-                   "call": "ovs_set_motion x2 + ovs_assemble_interpolate per step"},
+                   "call": "ovs_set_motion per grid + ovs_assemble_interpolate per step",
+                   "launch": "CUDA graph per step (captured once), persistent kernels, autotuned shapes",
+                   "tuning": tuning, "grids": len(sc.grids), "sets_per_step": len(dev_sets[W])},
         "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
-        "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_slow_near || k_slow_stuck": float(np.mean(slow_ms)),
+        "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_slow (near-face || stuck halves)": float(np.mean(slow_ms)),
                                   "k_interp": float(np.mean(interp_ms))},
-        "separate_calls": {"ms_per_step": float(np.mean(sep_ms)), "value": pts_all / (float(np.sum(sep_ms)) / 1e3)},
+        "launch_modes_ms_per_step": {"graph": total_ms / K, "direct": float(np.mean(direct_ms)),
+                                     "direct_traced": float(np.mean(traced_ms)),
+                                     "separate_calls_graph": float(np.mean(sep_ms))},
         "roofline": {"kernel": "k_assemble", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)", "bytes_per_point": BYTES_ASSEMBLE,
                      "traffic": traffic},
         "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                 "d2h_bytes_per_step": d2h // K},
-        "gpu_launches": 4 * K,  # per step: k_assemble, k_slow_near, k_slow_stuck, k_interp
+        "gpu_launches": 3 * K,  # per step (one graph): k_assemble, k_slow, k_interp
         "clocks": ck,
         "walk_stats": stats,
         "learned_vs_plain": learned,
@@ -331,33 +359,53 @@ def run_ovs(args, rank, world, local):
 
 
 def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, W, ovs, torch):
-    """Train each body grid's guess network (3-64-64-3, 2M samples of the grid itself), then time the same step
-    with the plain start (previous donor, else control cell) and the learned one, cold (no previous donors) and
-    warm (a time loop)."""
+    """Train every body grid's guess network (3-H-H-3 SiLU, 2M samples of the grid itself, by the library's
+    kernels) for H = 32, 64, 128; time the same steps with the plain start (previous donor, else the control
+    cell) and the learned one, cold (no previous donors: the first step of a run) and warm (a time loop); the
+    width with the fastest cold step is kept (the MLP-width part of the autotuning).  ms_per_step: graph
+    launches; phases: a second, traced pass (direct launches)."""
     import gen
 
-    out = {"network": "3-64-64-3 SiLU, FP16 tensor-core inference, trained by the library's kernels"}
-    t0 = time.perf_counter()
-    losses = []
-    for gi, g in enumerate(sc.grids):
-        if g.role != 1:
-            continue
-        cells, xi = gen.mlp_training_samples(config_index(args.workload), g, 2_000_000)
-        rng = np.random.default_rng(100 + gi)
-        H = 64
-        init = np.concatenate([rng.normal(0, 0.8, 3 * H), np.zeros(H), rng.normal(0, 1 / np.sqrt(H), H * H),
-                               np.zeros(H), rng.normal(0, 1 / np.sqrt(H), 3 * H), np.zeros(3)]).astype(np.float32)
-        losses.append(ctx.train_guess(gids[gi], cells, xi.astype(np.float32), init, hidden=H, epochs=60, batch=8192,
-                                      lr=3e-3, lr_final=1e-5))
-    torch.cuda.synchronize()
-    out["train_s"] = time.perf_counter() - t0
-    out["train_mse"] = losses
+    out = {"network": "3-H-H-3 SiLU, FP16 tensor-core inference (FP32 accumulation in layers 1 and 3), trained by "
+                      "the library's kernels on 2M samples per body grid"}
+    bodies = [gi for gi, g in enumerate(sc.grids) if g.role == 1]
+
+    def train(H):
+        t0 = time.perf_counter()
+        losses = []
+        for gi in bodies:
+            g = sc.grids[gi]
+            cells, xi = gen.mlp_training_samples(config_index(args.workload), g, 2_000_000)
+            rng = np.random.default_rng(100 + gi)
+            init = np.concatenate([rng.normal(0, 0.8, 3 * H), np.zeros(H), rng.normal(0, 1 / np.sqrt(H), H * H),
+                                   np.zeros(H), rng.normal(0, 1 / np.sqrt(H), 3 * H), np.zeros(3)]).astype(np.float32)
+            losses.append(ctx.train_guess(gids[gi], cells, xi.astype(np.float32), init, hidden=H, epochs=60,
+                                          batch=8192, lr=3e-3, lr_final=1e-5))
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, float(np.mean(losses))
 
     def run(mode, steps, cold):
-        ctx.set_options(guess=mode, collect_stats=1)
-        ctx.stats(reset=True)
+        ctx.set_options(guess=mode)
         e0 = [torch.cuda.Event(enable_timing=True) for _ in steps]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in steps]
+        for e in e0 + e1:
+            e.record(stream)
+        torch.cuda.synchronize()
+        for k, s in enumerate(steps):
+            flush.zero_()
+            if cold:
+                ovs.ovs_reset_hints(ctx.ctx)
+            e0[k].record(stream)
+            one_step(s, dev_sets[s])
+            e1[k].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
+        # traced pass: per-phase times and walk statistics (direct launches)
+        if not cold:
+            for s in range(W):
+                one_step(s, dev_sets[s])
+        ctx.set_options(collect_stats=1)
+        ctx.stats(reset=True)
         tr = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in steps]
         for row in tr:
             for e in row:
@@ -368,32 +416,45 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
             if cold:
                 ovs.ovs_reset_hints(ctx.ctx)
             ovs.ovs_set_trace_events(ctx.ctx, tr[k])
-            e0[k].record(stream)
             one_step(s, dev_sets[s])
-            e1[k].record(stream)
         torch.cuda.synchronize()
         ovs.ovs_set_trace_events(ctx.ctx, [])
         st = ctx.stats(reset=True)
         ctx.set_options(collect_stats=0)
         learned_mode = mode in (ovs.OVS_GUESS_MLP, ovs.OVS_GUESS_MLP_ONLY)
-        phases = {"guess_kernels_ms": float(np.mean([r[5].elapsed_time(r[6]) for r in tr])) if learned_mode else 0.0,
-                  "k_assemble_ms": float(np.mean([r[0].elapsed_time(r[1]) for r in tr])),
-                  "slow_kernels_ms": float(np.mean([r[1].elapsed_time(r[2]) for r in tr])),
-                  "fallbacks": st["fallback"] / len(steps)}
-        return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)])), st["walk_steps"] / len(steps), phases
+        return {"ms_per_step": ms, "walk_steps_per_step": st["walk_steps"] / len(steps),
+                "guess_kernels_ms": float(np.mean([r[5].elapsed_time(r[6]) for r in tr])) if learned_mode else 0.0,
+                "k_assemble_ms": float(np.mean([r[0].elapsed_time(r[1]) for r in tr])),
+                "slow_kernels_ms": float(np.mean([r[1].elapsed_time(r[2]) for r in tr])),
+                "fallbacks_per_step": st["fallback"] / len(steps)}
 
     cold_steps = list(range(W, W + 5))
     warm = list(range(W, W + min(K, 50)))
-    res = {}
-    for name, mode, steps, cold in (("cold_plain_control_cell", ovs.OVS_GUESS_BINS, cold_steps, True),
-                                    ("cold_learned_network", ovs.OVS_GUESS_MLP_ONLY, cold_steps, True),
-                                    ("warm_plain_previous_donor", ovs.OVS_GUESS_HINT, warm, False),
-                                    ("warm_learned_previous_donor_else_network", ovs.OVS_GUESS_MLP, warm, False),
-                                    ("warm_learned_network_only", ovs.OVS_GUESS_MLP_ONLY, warm, False)):
-        ms, ws, ph = run(mode, steps, cold)
-        res[name] = {"ms_per_step": ms, "walk_steps_per_step": ws, **ph}
+    res = {"cold_plain_control_cell": run(ovs.OVS_GUESS_BINS, cold_steps, True)}
+    widths = {}
+    best_h, best_ms = None, None
+    for H in (32, 64, 128):
+        ts, mse = train(H)
+        r = run(ovs.OVS_GUESS_MLP_ONLY, cold_steps, True)
+        widths[H] = {"train_s": ts, "train_mse": mse, "cold_ms_per_step": r["ms_per_step"],
+                     "cold_walk_steps_per_step": r["walk_steps_per_step"], "guess_kernels_ms": r["guess_kernels_ms"]}
+        if best_ms is None or r["ms_per_step"] < best_ms:
+            best_h, best_ms = H, r["ms_per_step"]
+    out["widths"] = widths
+    out["chosen_width"] = best_h
+    if best_h != 128:
+        train(best_h)
+    res["cold_learned_network"] = run(ovs.OVS_GUESS_MLP_ONLY, cold_steps, True)
+    for name, mode in (("warm_plain_previous_donor", ovs.OVS_GUESS_HINT),
+                       ("warm_learned_previous_donor_else_network", ovs.OVS_GUESS_MLP),
+                       ("warm_learned_network_only", ovs.OVS_GUESS_MLP_ONLY)):
+        for s in range(W):
+            one_step(s, dev_sets[s])
+        res[name] = run(mode, warm, False)
     ctx.set_options(guess=ovs.OVS_GUESS_HINT)
     out.update(res)
+    cp, cl = res["cold_plain_control_cell"]["ms_per_step"], res["cold_learned_network"]["ms_per_step"]
+    out["cold_speedup_learned_over_plain"] = cp / cl
     return out
 
 
@@ -441,7 +502,7 @@ def run_reference(args, rank, world):
     oracle.build()
     sc = build_workload(args.workload)
     K, W = args.steps, args.warmup
-    inputs = step_inputs(sc, W + K)
+    inputs = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0))
     rng = np.random.default_rng(11)
     per_step = 20_000
     grids = None

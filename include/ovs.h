@@ -259,7 +259,7 @@ int ovs_reset_hints(ovs_ctx* ctx);
 typedef struct {
     int32_t assemble_blocks_per_sm; /* k_assemble, 256 threads a block: 1..12 */
     int32_t interp_blocks_per_sm;   /* k_interp, 256 threads a block: 1..32 */
-    int32_t slow_blocks_per_sm;     /* k_slow_near and k_slow_stuck, 256 threads a block: 1..8 */
+    int32_t slow_blocks_per_sm;     /* k_slow, 256 threads a block, per SM for each of its two halves: 1..8 */
     int32_t guess_blocks_per_sm;    /* k_guess, 128 threads a block: 1..32 */
 } ovs_tuning;
 

@@ -56,10 +56,6 @@ struct ovs_ctx {
     ovs_options opts;
     cudaEvent_t trace[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool tracing = false;
-    // a second stream and two events to run the two slow-path kernels side by side (fork / join on `stream`)
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr;
-    cudaEvent_t join = nullptr;
     // step parameters: the device copy (context workspace) and two pinned staging buffers, each with the event
     // that marks the end of the last call that read it
     StepParams* d_step = nullptr;
@@ -256,10 +252,7 @@ static void release(ovs_ctx* c) {
     for (auto& g : c->graphs)
         for (auto& x : g.exec)
             if (x) cudaGraphExecDestroy(x);
-    if (c->side) cudaStreamDestroy(c->side);
     if (c->gstream) cudaStreamDestroy(c->gstream);
-    if (c->fork) cudaEventDestroy(c->fork);
-    if (c->join) cudaEventDestroy(c->join);
     for (int b = 0; b < 2; ++b) {
         if (c->step_done[b]) cudaEventDestroy(c->step_done[b]);
         if (c->h_step[b]) cudaFreeHost(c->h_step[b]);
@@ -292,10 +285,7 @@ int ovs_ctx_create(ovs_ctx** out, int device, void* cuda_stream) {
         delete c;
         return OVS_ERR_NO_DEVICE;
     }
-    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->step_done[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->step_done[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaHostAlloc((void**)&c->h_step[0], sizeof(StepParams), cudaHostAllocDefault) != cudaSuccess ||
@@ -312,7 +302,6 @@ int ovs_ctx_destroy(ovs_ctx* c) {
     if (!c) return OVS_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    if (c->side) cudaStreamSynchronize(c->side);
     release(c);
     return OVS_OK;
 }
@@ -625,7 +614,7 @@ cudaError_t enqueue_step(ovs_ctx* c, int b, uint32_t kind, uint32_t* qcount, cud
     }
     if (kind & kStepAssemble) {
         e = launch_assemble(&c->d_step->a, qcount, c->d_grids, c->nsm, c->tune.assemble_blocks_per_sm,
-                            c->tune.slow_blocks_per_sm, st, trace ? c->trace : nullptr, c->side, c->fork, c->join);
+                            c->tune.slow_blocks_per_sm, st, trace ? c->trace : nullptr);
         if (e != cudaSuccess) return e;
     }
     if (kind & kStepInterp)
@@ -1049,7 +1038,7 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     float best_ms = 0.f;
     int rc = trial(cur, &best_ms);
     const int cand_asm[] = {1, 2, 3, 4, 6};
-    const int cand_slow[] = {1, 2, 4};
+    const int cand_slow[] = {1, 2, 4, 8};
     const int cand_guess[] = {4, 8, 16};
     int cand_interp[4] = {std::max(1, cur.interp_blocks_per_sm / 2), cur.interp_blocks_per_sm,
                           std::min(32, 2 * cur.interp_blocks_per_sm), std::min(32, 4 * cur.interp_blocks_per_sm)};
@@ -1067,7 +1056,7 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
         }
     };
     if (rc == OVS_OK) sweep(&ovs_tuning::assemble_blocks_per_sm, cand_asm, 5);
-    if (rc == OVS_OK) sweep(&ovs_tuning::slow_blocks_per_sm, cand_slow, 3);
+    if (rc == OVS_OK) sweep(&ovs_tuning::slow_blocks_per_sm, cand_slow, 4);
     if (rc == OVS_OK && fout) sweep(&ovs_tuning::interp_blocks_per_sm, cand_interp, 4);
     if (rc == OVS_OK && learned) sweep(&ovs_tuning::guess_blocks_per_sm, cand_guess, 3);
     cudaEventDestroy(e0);

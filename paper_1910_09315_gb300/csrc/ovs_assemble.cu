@@ -539,13 +539,12 @@ __device__ __forceinline__ void finish_none(const AsmParams& P, int64_t t) {
 
 // Points near a face: one warp each, one lane per candidate cell.  A point whose candidates all fail (or a
 // later donor of its list) gets the warp-level exhaustive search.
-__global__ void __launch_bounds__(kSlowThreads) k_slow_near(const AsmParams* __restrict__ Pp,
-                                                            const GridDev* __restrict__ G) {
-    const AsmParams& P = *Pp;
+__device__ __forceinline__ void slow_near_body(const AsmParams& P, const GridDev* __restrict__ G, unsigned bid,
+                                               unsigned nblk) {
     uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
     unsigned nref = 0, nfb = 0;
-    for (uint32_t q = blockIdx.x * kSlowWarps + (threadIdx.x >> 5); q < count; q += gridDim.x * kSlowWarps) {
+    for (uint32_t q = bid * kSlowWarps + (threadIdx.x >> 5); q < count; q += nblk * kSlowWarps) {
         const SlowEntry e = P.queue[q];
         const SlowPoint sp = slow_point(P, e);
         const SetDev& s = P.s[sp.si];
@@ -592,9 +591,10 @@ constexpr int kMaxCand = 128;
 
 // Stuck walks (points outside the grid, or where the walk gave up): one block each.  All threads filter the
 // control cell's list (box, slabs, FP32 Newton); warp 0 applies the donor predicate to the survivors.
-__global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const AsmParams* __restrict__ Pp,
-                                                             const GridDev* __restrict__ G) {
-    const AsmParams& P = *Pp;
+__device__ __forceinline__ void slow_stuck_body(const AsmParams& P, const GridDev* __restrict__ G, unsigned bid,
+                                                unsigned nblk) {
+    static_assert(kMaxCand <= kSlowThreads, "one thread per candidate");
+    constexpr long long kNoCellLL = 0x7FFFFFFFFFFFFFFFll;
     __shared__ uint32_t cand[kMaxCand];
     __shared__ float cxi[kMaxCand][3];
     __shared__ int ncand;
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const AsmParams* __
     const int lane = (int)lane_id();
     const int warp = threadIdx.x >> 5;
     unsigned nref = 0, nfb = 0;
-    for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
+    for (uint32_t q = bid; q < count; q += nblk) {
         const SlowEntry e = P.queue[P.queue_cap - 1 - q];
         const SlowPoint sp = slow_point(P, e);
         const SetDev& s = P.s[sp.si];
@@ -642,36 +642,32 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const AsmParams* __
                 }
             }
             __syncthreads();
-            if (warp == 0) {
+            const int nc = ncand;
+            if (nc <= kMaxCand) {
+                // the exact test on every survivor at once, a thread per candidate; the lowest containing id wins
+                if (threadIdx.x == 0) fcell = kNoCellLL;
+                __syncthreads();
+                double a = 0, bb = 0, cc = 0;
+                bool hit = false;
+                uint32_t c = 0xFFFFFFFFu;
+                if ((int)threadIdx.x < nc) {
+                    c = cand[threadIdx.x];
+                    hit = contains_exact(g, c, pf, [&]() { return p; }, cxi[threadIdx.x][0], cxi[threadIdx.x][1],
+                                         cxi[threadIdx.x][2], a, bb, cc);
+                    if (hit) atomicMin((unsigned long long*)&fcell, (unsigned long long)c);
+                }
+                __syncthreads();
+                if (hit && (long long)c == fcell) {
+                    found = 1;
+                    fuvw[0] = a;
+                    fuvw[1] = bb;
+                    fuvw[2] = cc;
+                }
+            } else if (warp == 0) {
+                // more survivors than the list holds: the warp-cooperative exhaustive search
                 int64_t cell = -1;
                 double u = 0, v = 0, w = 0;
-                bool ok;
-                if (ncand <= kMaxCand) {
-                    uint32_t best = 0xFFFFFFFFu;
-                    double bu = 0, bv = 0, bw = 0;
-                    for (int k = lane; k < ncand; k += 32) {
-                        uint32_t c = cand[k];
-                        if (c >= best) continue;
-                        double a, bb, cc;
-                        if (contains_exact(g, c, pf, [&]() { return p; }, cxi[k][0], cxi[k][1], cxi[k][2], a, bb, cc)) {
-                            best = c;
-                            bu = a;
-                            bv = bb;
-                            bw = cc;
-                        }
-                    }
-                    uint32_t wbest = __reduce_min_sync(0xffffffffu, best);
-                    ok = wbest != 0xFFFFFFFFu;
-                    if (ok) {
-                        int src = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
-                        cell = wbest;
-                        u = __shfl_sync(0xffffffffu, bu, src);
-                        v = __shfl_sync(0xffffffffu, bv, src);
-                        w = __shfl_sync(0xffffffffu, bw, src);
-                    }
-                } else {
-                    ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);  // more survivors than the list holds
-                }
+                const bool ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
                 if (ok && lane == 0) {
                     found = 1;
                     fcell = cell;
@@ -699,11 +695,21 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const AsmParams* __
     }
 }
 
+// The two slow paths in one launch, side by side: odd blocks take the stuck walks (a block per entry), even
+// blocks the near-face points (a warp per entry).  Interleaved, the first wave of blocks holds both kinds, so
+// the long stuck walks do not keep the near-face points waiting; one kernel keeps them concurrent without a
+// second stream (or a fork in the step graph).
+__global__ void __launch_bounds__(kSlowThreads) k_slow(const AsmParams* __restrict__ Pp, const GridDev* __restrict__ G) {
+    const AsmParams& P = *Pp;
+    const unsigned half = gridDim.x >> 1;
+    if (blockIdx.x & 1) slow_stuck_body(P, G, blockIdx.x >> 1, half);
+    else slow_near_body(P, G, blockIdx.x >> 1, half);
+}
+
 }  // namespace
 
 cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const GridDev* dgrids, int nsm,
-                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev, cudaStream_t side,
-                            cudaEvent_t fork, cudaEvent_t join) {
+                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev) {
     const unsigned ab = (unsigned)(nsm * (asm_bps > 0 ? asm_bps : kAsmMinBlocks));
     const unsigned sb = (unsigned)(nsm * (slow_bps > 0 ? slow_bps : 1));
     // the two queue counters and the work counter
@@ -714,18 +720,7 @@ cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const Gr
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    if (side && fork && join) {
-        // the two slow-path kernels work on disjoint queues: run them side by side
-        if ((err = cudaEventRecord(fork, st)) != cudaSuccess) return err;
-        if ((err = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return err;
-        k_slow_stuck<<<sb, kSlowThreads, 0, side>>>(dP, dgrids);
-        k_slow_near<<<sb, kSlowThreads, 0, st>>>(dP, dgrids);
-        if ((err = cudaEventRecord(join, side)) != cudaSuccess) return err;
-        if ((err = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return err;
-    } else {
-        k_slow_near<<<sb, kSlowThreads, 0, st>>>(dP, dgrids);
-        k_slow_stuck<<<sb, kSlowThreads, 0, st>>>(dP, dgrids);
-    }
+    k_slow<<<2 * sb, kSlowThreads, 0, st>>>(dP, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

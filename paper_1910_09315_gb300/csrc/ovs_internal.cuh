@@ -628,10 +628,10 @@ size_t scan_scratch_elems(int64_t n);
 // ev: 3 optional events (before the fast kernel, after it, after the slow kernels); 2 for interpolation.
 // side/fork/join: a second stream and two events for running the two slow-path kernels concurrently (null:
 // everything on st).
-// asm_bps / slow_bps: blocks per SM of the persistent assembly and slow-path grids (0: defaults)
+// asm_bps / slow_bps: blocks per SM of the persistent assembly grid and of each half of the slow-path grid
+// (0: defaults)
 cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const GridDev* dgrids, int nsm,
-                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev, cudaStream_t side,
-                            cudaEvent_t fork, cudaEvent_t join);
+                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev);
 // blocks of k_interp resident per SM (occupancy calculator), or a negative CUDA error
 int interp_default_blocks_per_sm(bool f64);
 // bps: blocks per SM of the persistent grid (0: the occupancy calculator's figure)
