@@ -285,6 +285,24 @@ def run_ovs(args, rank, world, local):
     for s in range(W):
         one_step(s, dev_sets[s], fused=False)
     _, sep_ms, _, _, _ = timed(False, trace=False)
+    # the interpolation as a sparse matrix (paper Sec. 2.2.6): build it from the donors of one step and time
+    # one matrix-vector product per field component (as an implicit solve would apply it)
+    nW = one_step(W, dev_sets[W])
+    dW = donors_view(nW)
+    ev_m = events(3)
+    ev_m[0].record(stream)
+    row_ptr, col, val = ctx.interp_matrix(dW, ovs.OVS_F64 if fdt == torch.float64 else ovs.OVS_F32)
+    ev_m[1].record(stream)
+    xs = [torch.cat([f[c] for f in fields]) for c in range(4)]
+    reps = 20
+    for r in range(reps):
+        for c in range(4):
+            ctx.spmv(row_ptr, col, val, xs[c])
+    ev_m[2].record(stream)
+    torch.cuda.synchronize()
+    matrix = {"points": nW, "nnz": int(row_ptr[-1].item()), "build_ms": ev_m[0].elapsed_time(ev_m[1]),
+              "spmv_ms_per_component": ev_m[1].elapsed_time(ev_m[2]) / (4 * reps),
+              "note": "rows = fringe points, 8 weights per found point; x = every grid's node values"}
     learned = None if args.no_learned else learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush,
                                                             K, W, ovs, torch)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
@@ -352,6 +370,7 @@ def run_ovs(args, rank, world, local):
         "clocks": ck,
         "walk_stats": stats,
         "learned_vs_plain": learned,
+        "interp_matrix": matrix,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, inputs[W], args.cpu_sample)

@@ -250,6 +250,25 @@ int ovs_sync(ovs_ctx* ctx);
 /* Read (synchronously) and optionally reset the statistics counters. */
 int ovs_get_stats(ovs_ctx* ctx, ovs_stats* out, int reset);
 
+/* The interpolation as a sparse matrix (Sec. 2.2.6: the boundary interpolation assembled as a matrix whose rows
+ * are the receiver points and whose columns are donor nodes, applied inside an implicit solve).  From the donors
+ * `in` of a call (as ovs_assemble wrote them): one row per point; a point FOUND in a donor grid has 8 entries,
+ * every other row none.  Entry a of a row (a = 0..7; bits 0 / 1 / 2 of a: the corner at +1 along i / j / k of
+ * the donor cell): column = node_offset(donor grid) + that corner's node id, value = its trilinear weight from
+ * the stored xi (the weights ovs_interpolate uses).  node_offset(g) = the sum of the node counts of grids
+ * 0 .. g-1 in creation order, so the x of ovs_spmv holds every grid's node values back to back.
+ * row_ptr: device int32 [in->n + 1] (row_ptr[in->n] = the number of entries); col: device int64 and val: device
+ * FP32 or FP64 (val_dtype, OVS_F32 / OVS_F64), each with room for 8 * in->n entries.  Uses the context
+ * workspace as scratch (in->n <= its max_points, else OVS_ERR_WORKSPACE).  Enqueued on the context stream; a
+ * donor record that names no cell of its grid is reported by ovs_sync (its entries: columns -1, values 0). */
+int ovs_interp_matrix(ovs_ctx* ctx, const ovs_donors* in, int32_t* row_ptr, int64_t* col, void* val,
+                      int32_t val_dtype);
+/* y = A x for a matrix of ovs_interp_matrix (nrows = its number of rows): y[r] = the sum of the row's entries'
+ * val * x[col] in entry order (entries with column -1 skipped).  val, x and y share dtype (OVS_F32 / OVS_F64);
+ * device pointers; x in the global node numbering above.  Enqueued on the context stream. */
+int ovs_spmv(ovs_ctx* ctx, int64_t nrows, const int32_t* row_ptr, const int64_t* col, const void* val, const void* x,
+             void* y, int32_t dtype);
+
 /* Forget all per-node donor hints (next assemble starts cold). */
 int ovs_reset_hints(ovs_ctx* ctx);
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ovs_guess.cuh"
+#include "ovs_matrix.cuh"
 #include "ovs_internal.cuh"
 
 using namespace ovs;
@@ -974,6 +975,59 @@ int ovs_reset_hints(ovs_ctx* c) {
     OVS_CUDA(c, cudaSetDevice(c->device));
     for (int g = 0; g < c->ngrids; ++g)
         OVS_CUDA(c, cudaMemsetAsync(c->grids[g].hint, 0xFF, (size_t)c->grids[g].nnodes * 4, c->stream));
+    return OVS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------------
+// the interpolation matrix
+extern "C" {
+
+int ovs_interp_matrix(ovs_ctx* c, const ovs_donors* in, int32_t* row_ptr, int64_t* col, void* val,
+                      int32_t val_dtype) {
+    if (!c) return OVS_ERR_ARG;
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "no workspace attached");
+    if (!in || !row_ptr) return fail(c, OVS_ERR_ARG, "donors or row_ptr is NULL");
+    if (val_dtype != OVS_F32 && val_dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "val_dtype %d", val_dtype);
+    if (in->n < 0) return fail(c, OVS_ERR_ARG, "donors.n = %lld", (long long)in->n);
+    if (in->n > c->max_points)
+        return fail(c, OVS_ERR_WORKSPACE, "%lld points exceed the workspace's max_points %lld", (long long)in->n,
+                    (long long)c->max_points);
+    if (8 * in->n >= ((int64_t)1 << 31)) return fail(c, OVS_ERR_ARG, "more than 2^31 matrix entries");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    if (in->n == 0) {
+        OVS_CUDA(c, cudaMemsetAsync(row_ptr, 0, sizeof(int32_t), c->stream));
+        return OVS_OK;
+    }
+    if (!in->grid || !in->cell || !in->xi || !in->status || !col || !val)
+        return fail(c, OVS_ERR_ARG, "a donors array, col or val is NULL");
+    if (in->xi_dtype != OVS_F32 && in->xi_dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "xi_dtype");
+    if (interp_matrix_scratch_bytes(in->n) > (size_t)std::max<int64_t>(1, c->max_points) * sizeof(SlowEntry))
+        return fail(c, OVS_ERR_WORKSPACE, "workspace scratch too small");
+    NodeOffsets off;
+    int64_t o = 0;
+    for (int g = 0; g < OVS_MAX_GRIDS; ++g) {
+        off.off[g] = o;
+        if (g < c->ngrids) o += c->grids[g].nnodes;
+    }
+    cudaError_t e = launch_interp_matrix(c->d_grids, c->ngrids, off, in->status, in->grid, in->cell, in->xi,
+                                         in->xi_dtype == OVS_F64, in->n, (uint32_t*)c->d_queue, row_ptr, col, val,
+                                         val_dtype == OVS_F64, c->d_err, c->nsm, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "interp_matrix launch");
+    return OVS_OK;
+}
+
+int ovs_spmv(ovs_ctx* c, int64_t nrows, const int32_t* row_ptr, const int64_t* col, const void* val, const void* x,
+             void* y, int32_t dtype) {
+    if (!c) return OVS_ERR_ARG;
+    if (nrows < 0) return fail(c, OVS_ERR_ARG, "nrows = %lld", (long long)nrows);
+    if (dtype != OVS_F32 && dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "dtype %d", dtype);
+    if (nrows == 0) return OVS_OK;
+    if (!row_ptr || !col || !val || !x || !y) return fail(c, OVS_ERR_ARG, "a matrix or vector pointer is NULL");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_spmv(nrows, row_ptr, col, val, x, y, dtype == OVS_F64, c->nsm, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spmv launch");
     return OVS_OK;
 }
 

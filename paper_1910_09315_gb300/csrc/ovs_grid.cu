@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_bin_fill(GridDev g, const int
 constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
+static_assert(kScanTile == kScanTileElems, "scan tile size");
 
 __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
     __shared__ uint32_t sh[kScanThreads / 32];

@@ -621,6 +621,9 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 cudaError_t launch_build_records(const GridDev& g, CellRec* rec, float* xff, double* partials, int nblocks,
                                  double* out9, cudaStream_t st);
 cudaError_t launch_bin_count(const GridDev& g, uint32_t* counts, cudaStream_t st);
+// exclusive scan of n counts into start[0..n] (start[n] = total); block_sums: one entry per tile of
+// kScanTileElems counts
+constexpr int kScanTileElems = 2048;
 cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint32_t* block_sums, cudaStream_t st);
 cudaError_t launch_bin_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, int32_t* rep,
                             cudaStream_t st);

@@ -53,6 +53,7 @@ EXPORTS = [
     "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate", "ovs_guess_param_count",
     "ovs_train_workspace_size", "ovs_train_guess", "ovs_guess_get_params", "ovs_guess_set_params",
     "ovs_guess_eval", "ovs_mlp_loss_grad", "ovs_set_tuning", "ovs_get_tuning", "ovs_autotune",
+    "ovs_interp_matrix", "ovs_spmv",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -154,6 +155,8 @@ def load(path: Optional[str] = None):
         "ovs_guess_set_params": [V, I32, I32, V],
         "ovs_guess_eval": [V, I32, I64, V, V],
         "ovs_mlp_loss_grad": [V, I32, I64, V, V, V, V, V],
+        "ovs_interp_matrix": [V, ctypes.POINTER(ovs_donors), V, V, V, I32],
+        "ovs_spmv": [V, I64, V, V, V, V, V, I32],
         "ovs_set_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_autotune": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors), ctypes.POINTER(ovs_fields),
@@ -242,6 +245,14 @@ def ovs_assemble(ctx, sets, nsets: int, donors: ovs_donors):
 def ovs_assemble_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
     _check(ctx, load().ovs_assemble_interpolate(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
                                                 ctypes.byref(out)))
+
+
+def ovs_interp_matrix(ctx, donors: ovs_donors, row_ptr: int, col: int, val: int, val_dtype: int):
+    _check(ctx, load().ovs_interp_matrix(ctx, ctypes.byref(donors), row_ptr, col, val, int(val_dtype)))
+
+
+def ovs_spmv(ctx, nrows: int, row_ptr: int, col: int, val: int, x: int, y: int, dtype: int):
+    _check(ctx, load().ovs_spmv(ctx, int(nrows), row_ptr, col, val, x, y, int(dtype)))
 
 
 def ovs_set_tuning(ctx, t):
@@ -498,6 +509,26 @@ class Context:
         else:
             best = ovs_autotune(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), None, 0, None, reps)
         return {k: getattr(best, k) for k, _ in ovs_tuning._fields_}
+
+    def interp_matrix(self, donors, val_dtype: int = OVS_F32):
+        """ovs_interp_matrix of a donors dict -> (row_ptr int32 [n+1], col int64 [8n], val [8n]) on the device."""
+        t = self.torch
+        n = donors["n"]
+        row_ptr = t.empty(n + 1, dtype=t.int32, device=self.device)
+        col = t.empty(max(1, 8 * n), dtype=t.int64, device=self.device)
+        val = t.empty(max(1, 8 * n), dtype=t.float64 if val_dtype == OVS_F64 else t.float32, device=self.device)
+        ovs_interp_matrix(self.ctx, self.donors_struct(donors), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr(),
+                          val_dtype)
+        return row_ptr, col, val
+
+    def spmv(self, row_ptr, col, val, x):
+        """y = A x (ovs_spmv); x: device vector of all grids' node values in the global numbering."""
+        t = self.torch
+        nrows = int(row_ptr.numel()) - 1
+        y = t.empty(max(1, nrows), dtype=val.dtype, device=self.device)
+        ovs_spmv(self.ctx, nrows, row_ptr.data_ptr(), col.data_ptr(), val.data_ptr(), x.data_ptr(), y.data_ptr(),
+                 OVS_F64 if val.dtype == t.float64 else OVS_F32)
+        return y[:nrows]
 
     def set_tuning(self, **kw):
         t = ovs_get_tuning(self.ctx)
