@@ -285,6 +285,40 @@ def run_ovs(args, rank, world, local):
     for s in range(W):
         one_step(s, dev_sets[s], fused=False)
     _, sep_ms, _, _, _ = timed(False, trace=False)
+    # plain, unbatched: one ovs_assemble_interpolate per fringe set (direct launches, default launch shapes), the
+    # same steps and start (previous donor, else control cell), for the batching comparison
+    def unbatched_step(s):
+        m, fs = inputs[s]
+        for gid, mo in zip(gids, m):
+            ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
+        b = 0
+        for st_ in dev_sets[s]:
+            n = int(st_[1].numel())
+            d = {"grid": donors["grid"][b:b + n], "cell": donors["cell"][b:b + n], "xi": donors["xi"][3 * b:3 * (b + n)],
+                 "status": donors["status"][b:b + n], "xi_dtype": xi_dtype, "n": n}
+            ctx.assemble_interpolate([st_], fields, donors=d, out=[o[b:b + n] for o in outs])
+            b += n
+        return b
+
+    saved_tuning = ovs.ovs_get_tuning(ctx.ctx)
+    ctx.set_options(launch=ovs.OVS_LAUNCH_DIRECT)
+    ctx.set_tuning(assemble_blocks_per_sm=0, interp_blocks_per_sm=0, slow_blocks_per_sm=0, guess_blocks_per_sm=0)
+    for s in range(W):
+        unbatched_step(s)
+    e0u, e1u = events(K), events(K)
+    torch.cuda.synchronize()
+    for k, s in enumerate(range(W, W + K)):
+        flush.zero_()
+        e0u[k].record(stream)
+        unbatched_step(s)
+        e1u[k].record(stream)
+    torch.cuda.synchronize()
+    unbatched_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0u, e1u)]))
+    ovs.ovs_set_tuning(ctx.ctx, saved_tuning)
+    ctx.set_options(launch=ovs.OVS_LAUNCH_GRAPH)
+    for s in range(W):
+        one_step(s, dev_sets[s])
+
     # the interpolation as a sparse matrix (paper Sec. 2.2.6): build it from the donors of one step and time
     # one matrix-vector product per field component (as an implicit solve would apply it)
     nW = one_step(W, dev_sets[W])
@@ -369,6 +403,8 @@ def run_ovs(args, rank, world, local):
         "gpu_launches": 3 * K,  # per step (one graph): k_assemble, k_slow, k_interp
         "clocks": ck,
         "walk_stats": stats,
+        "plain_unbatched_ms_per_step": unbatched_ms,
+        "batched_over_unbatched": unbatched_ms / (total_ms / K),
         "learned_vs_plain": learned,
         "interp_matrix": matrix,
     }

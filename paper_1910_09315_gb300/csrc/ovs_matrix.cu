@@ -75,9 +75,30 @@ __global__ void __launch_bounds__(kMatThreads) k_spmv(int64_t nrows, const int32
          r += (int64_t)gridDim.x * kMatThreads) {
         const int32_t e0 = __ldg(row_ptr + r), e1 = __ldg(row_ptr + r + 1);
         T s = (T)0;
-        for (int32_t e = e0; e < e1; ++e) {
-            const int64_t cidx = __ldg(col + e);
-            if (cidx >= 0) s += __ldg(val + e) * __ldg(x + cidx);
+        if (e1 - e0 == 8 && (e0 & 7) == 0) {
+            // a full row (every row of ovs_interp_matrix): its 8 columns and values in 16-byte loads, then the 8
+            // gathers together; summed in entry order as below
+            const longlong2* cp = reinterpret_cast<const longlong2*>(col + e0);
+            long long c[8];
+            T v[8], xv[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const longlong2 cc = __ldg(cp + q);
+                c[2 * q] = cc.x;
+                c[2 * q + 1] = cc.y;
+            }
+#pragma unroll
+            for (int a = 0; a < 8; ++a) v[a] = __ldg(val + e0 + a);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) xv[a] = c[a] >= 0 ? __ldg(x + c[a]) : (T)0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if (c[a] >= 0) s += v[a] * xv[a];
+        } else {
+            for (int32_t e = e0; e < e1; ++e) {
+                const int64_t cidx = __ldg(col + e);
+                if (cidx >= 0) s += __ldg(val + e) * __ldg(x + cidx);
+            }
         }
         y[r] = s;
     }
