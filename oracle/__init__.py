@@ -55,7 +55,8 @@ def build(force: bool = False) -> str:
 
 class _OGrid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("per", ctypes.c_int32 * 3),
-                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p)]
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("iblank", ctypes.c_void_p)]
 
 
 _lib = None
@@ -114,6 +115,18 @@ class OracleGrid:
     @classmethod
     def from_gen(cls, g, bins=None) -> "OracleGrid":
         return cls(g.dims, g.periodic, g.x, g.y, g.z, bins=bins)
+
+    def set_iblank(self, iblank=None):
+        """Per-node mask (0 = blanked: a hole point, never a donor node), or None for every node active.  A cell
+        with a blanked corner is never a donor (Sec. 2.4); the search moves on to the next cell, then the next
+        grid of the priority list."""
+        if iblank is None:
+            self.iblank = None
+            self._s.iblank = None
+        else:
+            self.iblank = np.ascontiguousarray(np.asarray(iblank) != 0, dtype=np.uint8)
+            assert self.iblank.size == int(np.prod(self.dims))
+            self._s.iblank = self.iblank.ctypes.data
 
     def __del__(self):
         if getattr(self, "_bins", None) and _lib is not None:

@@ -51,6 +51,7 @@ typedef struct {
     const double* x;
     const double* y;
     const double* z;
+    const uint8_t* iblank; /* per node, 0 = blanked (a hole point, never a donor node); NULL: every node active */
 } og_grid;
 
 typedef struct {
@@ -306,14 +307,24 @@ void og_bins_free(og_bins* b) {
 
 int64_t og_bins_nreg(const og_bins* b) { return b->nreg; }
 
-/* Donor cell of p by the control-cell bins: lowest-id containing cell, or -1. */
+/* A cell may donate only if none of its corner nodes is blanked (Sec. 2.4: blanked donors are rejected). */
+static int og_cell_usable(const og_grid* g, int64_t c) {
+    if (!g->iblank) return 1;
+    int64_t nd[8];
+    og_cell_nodes(g, c, nd);
+    for (int a = 0; a < 8; ++a)
+        if (!g->iblank[nd[a]]) return 0;
+    return 1;
+}
+
+/* Donor cell of p by the control-cell bins: lowest-id usable containing cell, or -1. */
 int64_t og_find_donor(const og_grid* g, const og_bins* b, const double p[3], double xi[3]) {
     for (int d = 0; d < 3; ++d)
         if (!(p[d] >= b->lo[d] && p[d] <= b->hi[d])) return -1;
     int64_t q = og_bin_index(b, 0, p[0]) +
                 (int64_t)b->nb[0] * (og_bin_index(b, 1, p[1]) + (int64_t)b->nb[1] * og_bin_index(b, 2, p[2]));
     for (int64_t r = b->start[q]; r < b->start[q + 1]; ++r) {
-        if (og_cell_contains(g, b->cells[r], p, xi)) return b->cells[r];
+        if (og_cell_usable(g, b->cells[r]) && og_cell_contains(g, b->cells[r], p, xi)) return b->cells[r];
     }
     return -1;
 }
@@ -322,7 +333,7 @@ int64_t og_find_donor(const og_grid* g, const og_bins* b, const double p[3], dou
 int64_t og_find_donor_brute(const og_grid* g, const double p[3], double xi[3]) {
     int64_t ncell = og_num_cells(g);
     for (int64_t c = 0; c < ncell; ++c)
-        if (og_cell_contains(g, c, p, xi)) return c;
+        if (og_cell_usable(g, c) && og_cell_contains(g, c, p, xi)) return c;
     return -1;
 }
 

@@ -357,3 +357,70 @@ def test_adam_first_step_is_signed_lr():
     v = {"a": np.zeros(3)}
     oracle.adam_step(P, g, m, v, 1, lr=0.1)
     assert np.allclose(P["a"], [0.9, -1.9, 2.9], atol=1e-6)
+
+
+# ----------------------------------------------------------------------------- blanked donors (iblank)
+def _window(xi):
+    return bool(np.all(xi >= -1e-10) and np.all(xi <= 1 + 1e-10))
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_iblank_lowest_usable_cell_by_definition(periodic):
+    """With a random iblank, the donor is the lowest-id cell that contains the point (Newton on that cell's own
+    corners, ascending ids, written out here cell by cell) and has no blanked corner; bins = brute force."""
+    rng = np.random.default_rng(31 + periodic)
+    n = (5, 5, 4) if periodic else (6, 6, 5)
+    g = random_curvilinear(n, 0.8, rng, periodic_i=periodic)
+    iblank = (rng.uniform(size=int(np.prod(n))) > 0.15).astype(np.uint8)
+    g.set_iblank(iblank)
+    xyz = np.stack([g.x, g.y, g.z], axis=1)
+    lo, hi = xyz.min(0), xyz.max(0)
+    a = rng.integers(0, len(xyz), 60)
+    pts = np.concatenate([rng.uniform(lo, hi, size=(300, 3)), xyz[a],
+                          0.5 * (xyz[a] + xyz[np.minimum(a + 1, len(xyz) - 1)])])
+    c1, x1, _, _ = g.search(pts, brute=False)
+    c2, x2, _, _ = g.search(pts, brute=True)
+    assert np.array_equal(c1, c2)
+    expect = np.full(len(pts), -1)
+    for q, p in enumerate(pts):
+        for c in range(g.n_cells):
+            nodes = g.cell_nodes(c)
+            if not np.all(iblank[nodes]):
+                continue
+            ok, xi, _ = oracle.newton_hex(xyz[nodes], p)
+            if ok and _window(xi):
+                expect[q] = c
+                break
+    assert np.array_equal(c1, expect)
+    assert 0 < (c1 >= 0).sum() < len(pts)
+    # the blanked cells did change answers: without the mask more points find a donor
+    g.set_iblank(None)
+    c0, _, _, _ = g.search(pts)
+    assert (c0 >= 0).sum() > (c1 >= 0).sum()
+    assert np.all((c1 < 0) | (c1 >= c0))  # a usable donor is never below the unmasked lowest id
+
+
+def test_iblank_all_active_changes_nothing():
+    rng = np.random.default_rng(5)
+    g = random_curvilinear((7, 6, 5), 0.8, rng)
+    xyz = np.stack([g.x, g.y, g.z], axis=1)
+    pts = rng.uniform(xyz.min(0), xyz.max(0), size=(500, 3))
+    c0, x0, _, _ = g.search(pts)
+    g.set_iblank(np.ones(len(xyz), np.uint8))
+    c1, x1, _, _ = g.search(pts)
+    assert np.array_equal(c0, c1) and np.array_equal(np.isnan(x0), np.isnan(x1))
+
+
+def test_iblank_falls_through_the_priority_list():
+    """A point in a cell of the first grid that touches a blanked node takes its donor from the next grid."""
+    g1 = cart_grid((5, 5, 5), (0, 0, 0), (1, 1, 1))
+    g2 = cart_grid((4, 4, 4), (0, 0, 0), (1, 1, 1))
+    ib = np.ones(125, np.uint8)
+    ib[2 + 5 * (2 + 5 * 2)] = 0  # node (2,2,2) at (0.5, 0.5, 0.5): the 8 cells around it cannot donate
+    g1.set_iblank(ib)
+    I = oracle.Frame(np.eye(3), np.zeros(3), np.zeros(3), np.zeros(3))
+    pts = np.array([[0.45, 0.4, 0.6], [0.1, 0.1, 0.1], [0.6, 0.55, 0.3]])
+    d = oracle.assemble([None, g1, g2], [I, I, I], pts, 0, np.arange(3), [1, 2])
+    assert list(d.grid) == [2, 1, 2] and list(d.status) == [0, 0, 0]
+    d1 = oracle.assemble([None, g1], [I, I], pts, 0, np.arange(3), [1])
+    assert list(d1.status) == [1, 0, 1]  # with no other grid: orphans
