@@ -579,9 +579,20 @@ def fish_school(config_index: int, nfish: int, bg_dims: Sequence[int], size_lo: 
             sets.append(FringeSet(0, sel.astype(np.int32), don, "bg->body"))
         return sets
 
+    def iblank_fn(motions: List[Motion]) -> List[np.ndarray]:
+        """Hole cut of the step: background nodes inside any fish body are blanked (0); body nodes all active."""
+        ms = motions[1:]
+        bgmask = np.ones(bg.n_nodes, dtype=np.uint8)
+        for q in range(nfish):
+            cand = box_candidates(bg, ms[q].c - half, ms[q].c + half)
+            pb = to_body(ms[q], np.stack([bg.x[cand], bg.y[cand], bg.z[cand]], axis=1))
+            bgmask[cand[inside_fish_layer(pb, phase, 0.0)]] = 0
+        return [bgmask] + [np.ones(b.n_nodes, dtype=np.uint8) for b in bodies]
+
     return Scenario(f"cfg{config_index}: school of {nfish} fish O-grids in a stretched bg "
                     "%dx%dx%d" % tuple(bg_dims), grids, fields, np.float32, dt=dt, nsteps=nsteps,
-                    motion_fn=motion_fn, sets_fn=sets_fn, meta=dict(phase=phase, positions=pos, sizes=sizes))
+                    motion_fn=motion_fn, sets_fn=sets_fn,
+                    meta=dict(phase=phase, positions=pos, sizes=sizes, iblank_fn=iblank_fn))
 
 
 def config1() -> Scenario:

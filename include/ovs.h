@@ -185,6 +185,14 @@ int ovs_create_grid(ovs_ctx* ctx, const ovs_grid_desc* desc, void* dworkspace, s
 int ovs_set_motion(ovs_ctx* ctx, int32_t grid_id, const double R[9], const double c[3], const double V[3],
                    const double omega[3]);
 
+/* Blanked nodes of a grid (Sec. 2.4: blanked donors are rejected).  iblank: device uint8 [its node count], 0 =
+ * blanked (a hole point: never a donor node), nonzero = active; NULL: every node active (the state after
+ * ovs_create_grid).  From then on a cell with a blanked corner node never donates: a point is given the
+ * lowest-id cell holding it that has no blanked corner, else the next grid of its priority list, else it is
+ * an orphan.  The mask is read on the context stream by this call (it marks the grid's cell records); a later
+ * change to it needs another call.  Errors: OVS_ERR_ARG (unknown grid). */
+int ovs_set_iblank(ovs_ctx* ctx, int32_t grid_id, const uint8_t* iblank);
+
 int ovs_set_options(ovs_ctx* ctx, const ovs_options* opts);
 int ovs_get_options(const ovs_ctx* ctx, ovs_options* opts);
 

@@ -511,6 +511,15 @@ int ovs_set_motion(ovs_ctx* c, int32_t gid, const double R[9], const double cc[3
     return OVS_OK;
 }
 
+int ovs_set_iblank(ovs_ctx* c, int32_t grid_id, const uint8_t* iblank) {
+    if (!c) return OVS_ERR_ARG;
+    if (grid_id < 0 || grid_id >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", grid_id);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_mark_blocked(c->grids[grid_id], iblank, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_iblank launch");
+    return OVS_OK;
+}
+
 int ovs_set_options(ovs_ctx* c, const ovs_options* o) {
     if (!c) return OVS_ERR_ARG;
     if (!o) return fail(c, OVS_ERR_ARG, "options is NULL");

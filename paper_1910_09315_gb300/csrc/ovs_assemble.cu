@@ -26,7 +26,7 @@ enum WalkResult { kWalkFound = 0, kWalkStuck = 1 };
 // FP32 walk from `cell` toward the donor-frame point xd (FP32 pairs).  On kWalkFound, cell/u/v/w hold a cell
 // whose FP32 local coordinates lie within kAccept32 of [0,1]^3.
 __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t& cell, float& u, float& v, float& w,
-                                      float& tau, int max_walk, int& steps) {
+                                      float& tau, int max_walk, int& steps, bool& blocked) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
     u = v = w = 0.5f;
@@ -45,6 +45,7 @@ __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t&
                   w >= -kAccept32 && w <= 1.f + kAccept32;
         if (in && conv) {
             tau = near_tau(r, u, v, w);
+            blocked = rec_blocked(r);
             return kWalkFound;
         }
         // step toward the point by the sign (and size, up to kMaxJump) of the local coordinates: the sign
@@ -215,18 +216,22 @@ __device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev
                 if (cell < 0) continue;
             }
             float u, v, w, tau = 0.25f;
-            int r = walk32(g, xd, cell, u, v, w, tau, from_hint ? min(P.max_walk, kHintWalk) : P.max_walk, steps);
+            bool blocked = false;
+            int r = walk32(g, xd, cell, u, v, w, tau, from_hint ? min(P.max_walk, kHintWalk) : P.max_walk, steps,
+                           blocked);
             if (r != kWalkFound && from_hint) {
                 // a walk from the previous donor or the learned guess that got stuck (on the grid's boundary, or
                 // after kHintWalk steps) starts again from the control cell before the exhaustive search
                 cell = control_cell();
                 if (cell < 0) continue;
-                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps);
+                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps, blocked);
             }
             e.t = (int32_t)t;
             e.di = di;
             if (r == kWalkFound) {
                 const int mask = near_mask(u, v, w, tau);
+                // clear of every face: the only cell of this grid holding the point; blanked -> next donor grid
+                if (mask == 0 && !P.xi_f64 && blocked) continue;
                 if (mask == 0 && !P.xi_f64) {
                     write_donor32(P, t, gd, cell, u, v, w, OVS_STATUS_FOUND);
                     gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
@@ -362,8 +367,9 @@ __device__ bool neighbourhood_warp(const GridDev& g, const ff pf[3], const P64& 
                 o1 = off[q][1];
                 o2 = off[q][2];
             }
-        hit = contains_exact(g, mine, pf, p64, xi32[0] - (float)o0, xi32[1] - (float)o1, xi32[2] - (float)o2, a, b,
-                             c);
+        if (!cell_blocked(g.rec, mine))  // a blanked cell never donates
+            hit = contains_exact(g, mine, pf, p64, xi32[0] - (float)o0, xi32[1] - (float)o1, xi32[2] - (float)o2, a,
+                                 b, c);
     }
     unsigned m = __ballot_sync(0xffffffffu, hit);
     if (!m) return false;
@@ -388,6 +394,7 @@ constexpr int kSlowWarps = kSlowThreads / 32;
 __device__ __forceinline__ bool exhaustive_filter(const GridDev& g, const ff pf[3], uint32_t c, float xi[3]) {
     CellRec rec;
     load_rec(g.rec, c, rec);
+    if (rec_blocked(rec)) return false;  // a blanked cell never donates
     float d[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = __fadd_rn(__fsub_rn(pf[k].hi, rec.x0h[k]), __fsub_rn(pf[k].lo, rec.x0l[k]));

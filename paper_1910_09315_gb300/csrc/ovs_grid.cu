@@ -241,6 +241,27 @@ cudaError_t launch_bin_count(const GridDev& g, uint32_t* counts, cudaStream_t st
 
 size_t scan_scratch_elems(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
 
+__global__ void k_mark_blocked(GridDev g, const uint8_t* __restrict__ iblank, CellRec* __restrict__ rec) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t blocked = 0u;
+        if (iblank) {
+            int i, j, k;
+            cell_ijk(g, c, i, j, k);
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if (!__ldg(iblank + corner_node(g, i, j, k, a))) blocked = 1u;
+        }
+        rec[c].pad[0] = __uint_as_float(blocked);
+    }
+}
+
+cudaError_t launch_mark_blocked(const GridDev& g, const uint8_t* iblank, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((g.ncells + 255) / 256, 152 * 32);
+    k_mark_blocked<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(g, iblank, (CellRec*)g.rec);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint32_t* block_sums, cudaStream_t st) {
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, start, n, block_sums);

@@ -354,6 +354,13 @@ __device__ __forceinline__ int64_t point_bin(const GridDev& g, double3 p) {
     return (int64_t)bx + (int64_t)g.nb[0] * ((int64_t)by + (int64_t)g.nb[1] * bz);
 }
 
+// A cell with a blanked corner node never donates (Sec. 2.4); the flag sits in the record's first pad word
+// (nonzero bits: blocked), written by ovs_set_iblank and zero from the record build.
+__device__ __forceinline__ bool rec_blocked(const CellRec& r) { return __float_as_uint(r.pad[0]) != 0u; }
+__device__ __forceinline__ bool cell_blocked(const CellRec* rec, int64_t cell) {
+    return __float_as_uint(__ldg(&rec[cell].pad[0])) != 0u;
+}
+
 __device__ __forceinline__ void load_rec(const CellRec* rec, int64_t cell, CellRec& r) {
     const uint4* src = reinterpret_cast<const uint4*>(rec + cell);
     uint4 v[8];
@@ -625,6 +632,8 @@ cudaError_t launch_bin_count(const GridDev& g, uint32_t* counts, cudaStream_t st
 // kScanTileElems counts
 constexpr int kScanTileElems = 2048;
 cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint32_t* block_sums, cudaStream_t st);
+// marks each cell of g blocked (a corner with iblank 0) or not (iblank NULL: none blocked)
+cudaError_t launch_mark_blocked(const GridDev& g, const uint8_t* iblank, cudaStream_t st);
 cudaError_t launch_bin_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, int32_t* rep,
                             cudaStream_t st);
 size_t scan_scratch_elems(int64_t n);

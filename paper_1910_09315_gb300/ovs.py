@@ -53,7 +53,7 @@ EXPORTS = [
     "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate", "ovs_guess_param_count",
     "ovs_train_workspace_size", "ovs_train_guess", "ovs_guess_get_params", "ovs_guess_set_params",
     "ovs_guess_eval", "ovs_mlp_loss_grad", "ovs_set_tuning", "ovs_get_tuning", "ovs_autotune",
-    "ovs_interp_matrix", "ovs_spmv",
+    "ovs_interp_matrix", "ovs_spmv", "ovs_set_iblank",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -156,6 +156,7 @@ def load(path: Optional[str] = None):
         "ovs_guess_eval": [V, I32, I64, V, V],
         "ovs_mlp_loss_grad": [V, I32, I64, V, V, V, V, V],
         "ovs_interp_matrix": [V, ctypes.POINTER(ovs_donors), V, V, V, I32],
+        "ovs_set_iblank": [V, I32, V],
         "ovs_spmv": [V, I64, V, V, V, V, V, I32],
         "ovs_set_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
@@ -245,6 +246,11 @@ def ovs_assemble(ctx, sets, nsets: int, donors: ovs_donors):
 def ovs_assemble_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out: ovs_fields_out):
     _check(ctx, load().ovs_assemble_interpolate(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
                                                 ctypes.byref(out)))
+
+
+def ovs_set_iblank(ctx, grid_id: int, iblank: int):
+    """iblank: device pointer to uint8 [nodes] (0 = blanked), or 0 / None for every node active."""
+    _check(ctx, load().ovs_set_iblank(ctx, int(grid_id), iblank or None))
 
 
 def ovs_interp_matrix(ctx, donors: ovs_donors, row_ptr: int, col: int, val: int, val_dtype: int):

@@ -45,6 +45,18 @@ class GpuScene:
         self.fields = [tuple(torch.as_tensor(f[k]).to(self.ctx.device, fdt) for k in ("u", "v", "w", "p"))
                        for f in sc.fields]
 
+    def set_iblank(self, gid, mask):
+        """Blanked nodes of grid gid (uint8 host array, 0 = blanked) or None (every node active)."""
+        if not hasattr(self, "_iblank"):
+            self._iblank = {}
+        if mask is None:
+            self._iblank.pop(gid, None)
+            ovs.ovs_set_iblank(self.ctx.ctx, self.ids[gid], None)
+        else:
+            m = self.torch.as_tensor(np.ascontiguousarray(mask, dtype=np.uint8)).to(self.ctx.device)
+            self._iblank[gid] = m  # the library reads it on the stream: keep it alive
+            ovs.ovs_set_iblank(self.ctx.ctx, self.ids[gid], m.data_ptr())
+
     def set_motion(self, motions):
         for gid, m in zip(self.ids, motions):
             self.ctx.set_motion(gid, m.R, m.c, m.V, m.omega)
