@@ -256,6 +256,35 @@ def ellipsoid_ogrid(na: int, npol: int, nr: int, semi: Sequence[float], r_out: f
     return Grid("ogrid", (na, npol, nr), (True, False, False), flat(r * dx), flat(r * dy), flat(r * dz), 1, meta)
 
 
+def body_surface(g: Grid):
+    """The closed triangulated surface of an O-grid's body (its wall layer k = 0 closed by fans to the two pole
+    points), in the grid's own frame: vertices (nv, 3) float64 and triangles (nt, 3) int32 vertex ids."""
+    na, npol, _ = g.dims
+    ring = np.stack([g.x, g.y, g.z], axis=1)[: na * npol]  # k = 0 layer, node i + na j
+    kind = g.meta.get("kind")
+    if kind == "ogrid":
+        a = g.meta["semi"][0]
+        poles = np.array([[a, 0.0, 0.0], [-a, 0.0, 0.0]])  # j = 0 lies at +x, j = npol - 1 at -x
+    elif kind == "fish":
+        ph = g.meta["phase"]
+        poles = np.array([[-0.5, float(fish_midline(np.array([0.0]), ph)[0]), 0.0],
+                          [0.5, float(fish_midline(np.array([1.0]), ph)[0]), 0.0]])
+    else:
+        raise ValueError("body_surface: not an O-grid")
+    V = np.concatenate([ring, poles])
+    i = np.arange(na)
+    ip = (i + 1) % na
+    tris = []
+    for j in range(npol - 1):
+        a0, a1, b0, b1 = i + na * j, ip + na * j, i + na * (j + 1), ip + na * (j + 1)
+        tris.append(np.stack([a0, a1, b1], axis=1))
+        tris.append(np.stack([a0, b1, b0], axis=1))
+    A, B = na * npol, na * npol + 1
+    tris.append(np.stack([np.full(na, A), ip, i], axis=1))
+    tris.append(np.stack([np.full(na, B), i + na * (npol - 1), ip + na * (npol - 1)], axis=1))
+    return V, np.concatenate(tris).astype(np.int32)
+
+
 # ----------------------------------------------------------------------------
 # fringe-set construction (input selection)
 # ----------------------------------------------------------------------------

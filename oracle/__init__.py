@@ -78,6 +78,7 @@ def lib():
         L.og_search.argtypes = [P, P, ctypes.c_int, ctypes.c_int64, P, P, P, P, P]
         L.og_newton_hex.restype = ctypes.c_int
         L.og_newton_hex.argtypes = [P, P, P, P]
+        L.og_surface_inside.argtypes = [ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64, P, P]
         L.og_cell_nodes.argtypes = [P, ctypes.c_int64, P]
         L.og_shape.argtypes = [P, P]
         _lib = L
@@ -165,6 +166,18 @@ def newton_hex(X: np.ndarray, p: np.ndarray):
     it = ctypes.c_int(0)
     ok = lib().og_newton_hex(_ptr(X), _ptr(p), _ptr(xi), ctypes.byref(it))
     return bool(ok), xi, it.value
+
+
+def surface_inside(V: np.ndarray, T: np.ndarray, P: np.ndarray) -> np.ndarray:
+    """Hole cutting (Sec. 2.2.1): 1 where a point (n, 3) is inside the closed triangulated surface (vertices
+    V (nv, 3), triangles T (nt, 3) of vertex ids), by the parity of the crossings of a ray along +x (every
+    triangle tested; the tie rules are in ovs_oracle.c)."""
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1, 3)
+    T = np.ascontiguousarray(T, dtype=np.int32).reshape(-1, 3)
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(len(P), dtype=np.uint8)
+    lib().og_surface_inside(len(V), _ptr(V), len(T), _ptr(T), len(P), _ptr(P), _ptr(out))
+    return out
 
 
 def shape(xi: np.ndarray) -> np.ndarray:

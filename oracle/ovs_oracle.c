@@ -379,3 +379,50 @@ int og_newton_hex(const double* X, const double* p, double* xi, int* iters) {
         for (int c = 0; c < 3; ++c) Xa[a][c] = X[3 * a + c];
     return og_newton(Xa, p, xi, iters);
 }
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Hole cutting (Sec. 2.2.1): a point is inside a closed triangulated body surface iff a ray from it crosses the
+ * surface an odd number of times.  The ray runs along +x; a triangle is crossed when the point's (y, z) lies
+ * in the triangle's projection on the y-z plane and the crossing lies strictly ahead in x.  A point on a
+ * projected edge belongs to the one triangle whose counter-clockwise edge runs downward (or, level, toward -y),
+ * so a ray through a shared edge or vertex is counted once.  Every operation is one FP64 rounding (no fused
+ * multiply-add), so the decision is reproducible.
+ * ------------------------------------------------------------------------------------------------------- */
+__attribute__((optimize("fp-contract=off"))) static double og_edge2(double ay, double az, double by, double bz,
+                                                                   double py, double pz) {
+    return (by - ay) * (pz - az) - (bz - az) * (py - ay);
+}
+
+static int og_edge_owns(double ay, double az, double by, double bz) { return (bz < az) || (bz == az && by < ay); }
+
+__attribute__((optimize("fp-contract=off"))) static int og_ray_crosses(const double* A, const double* B,
+                                                                      const double* C, const double* p) {
+    const double area = og_edge2(A[1], A[2], B[1], B[2], C[1], C[2]);
+    if (area == 0.0) return 0; /* edge-on: never crossed */
+    const double* a = A;
+    const double* b = area > 0 ? B : C; /* counter-clockwise order in the y-z plane */
+    const double* c = area > 0 ? C : B;
+    const double w0 = og_edge2(b[1], b[2], c[1], c[2], p[1], p[2]);
+    const double w1 = og_edge2(c[1], c[2], a[1], a[2], p[1], p[2]);
+    const double w2 = og_edge2(a[1], a[2], b[1], b[2], p[1], p[2]);
+    if (w0 < 0 || w1 < 0 || w2 < 0) return 0;
+    if (w0 == 0 && !og_edge_owns(b[1], b[2], c[1], c[2])) return 0;
+    if (w1 == 0 && !og_edge_owns(c[1], c[2], a[1], a[2])) return 0;
+    if (w2 == 0 && !og_edge_owns(a[1], a[2], b[1], b[2])) return 0;
+    const double s = w0 + w1 + w2;
+    const double xs = w0 * a[0] + w1 * b[0] + w2 * c[0]; /* s times the crossing's x */
+    return xs > p[0] * s;
+}
+
+/* inside[q] = 1 iff point q (n x 3, row-major) is inside the surface (nv vertices, nt triangles of vertex ids). */
+void og_surface_inside(int64_t nv, const double* V, int64_t nt, const int32_t* T, int64_t n, const double* P,
+                       uint8_t* inside) {
+    (void)nv;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < n; ++q) {
+        int odd = 0;
+        for (int64_t t = 0; t < nt; ++t)
+            odd ^= og_ray_crosses(V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], P + 3 * q);
+        inside[q] = (uint8_t)odd;
+    }
+}

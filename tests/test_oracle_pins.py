@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+import gen
 import oracle
 from gen import axis_angle, euler_zyx
 
@@ -424,3 +425,61 @@ def test_iblank_falls_through_the_priority_list():
     assert list(d.grid) == [2, 1, 2] and list(d.status) == [0, 0, 0]
     d1 = oracle.assemble([None, g1], [I, I], pts, 0, np.arange(3), [1])
     assert list(d1.status) == [1, 0, 1]  # with no other grid: orphans
+
+
+# ----------------------------------------------------------------------------- hole cutting (ray parity)
+def _cube_surface():
+    V = np.array([[x, y, z] for z in (0.0, 1.0) for y in (0.0, 1.0) for x in (0.0, 1.0)])
+    vid = lambda x, y, z: x + 2 * y + 4 * z
+    quads = [(vid(0, 0, 0), vid(0, 1, 0), vid(0, 1, 1), vid(0, 0, 1)), (vid(1, 0, 0), vid(1, 1, 0), vid(1, 1, 1), vid(1, 0, 1)),
+             (vid(0, 0, 0), vid(1, 0, 0), vid(1, 0, 1), vid(0, 0, 1)), (vid(0, 1, 0), vid(1, 1, 0), vid(1, 1, 1), vid(0, 1, 1)),
+             (vid(0, 0, 0), vid(1, 0, 0), vid(1, 1, 0), vid(0, 1, 0)), (vid(0, 0, 1), vid(1, 0, 1), vid(1, 1, 1), vid(0, 1, 1))]
+    T = []
+    for a, b, c, d in quads:  # each face split along its a-c diagonal
+        T += [(a, b, c), (a, c, d)]
+    return V, np.array(T, np.int32)
+
+
+def test_ray_parity_cube_with_ties():
+    """Lattice points of spacing 1/4 around the unit cube: strictly inside -> inside, strictly outside -> outside,
+    including rays through the faces' shared diagonals, edges and vertices (each crossing counted once)."""
+    V, T = _cube_surface()
+    g = np.arange(-2, 7) / 4.0
+    P = np.array(np.meshgrid(g, g, g, indexing="ij")).reshape(3, -1).T
+    inside = oracle.surface_inside(V, T, P)
+    strict_in = np.all((P > 0) & (P < 1), axis=1)
+    strict_out = np.any((P < 0) | (P > 1), axis=1)
+    assert np.all(inside[strict_in] == 1) and np.all(inside[strict_out] == 0)
+    assert strict_in.sum() == 27 and np.sum(strict_in & (P[:, 1] == P[:, 2])) == 9  # rays along a diagonal
+
+
+def test_ray_parity_ellipsoid_surface():
+    """The triangulated wall of the ellipsoid O-grid: inside iff inside the analytic ellipsoid, away from a band
+    around the surface that covers the chords' deviation; invariant under a rigid motion of points and surface."""
+    g = gen.ellipsoid_ogrid(48, 32, 8, (0.2, 0.1, 0.1), 0.4, beta_r=2.0)
+    V, T = gen.body_surface(g)
+    rng = np.random.default_rng(2)
+    P = rng.uniform(-0.25, 0.25, size=(20000, 3)) * np.array([1.0, 0.6, 0.6])
+    f = (P[:, 0] / 0.2) ** 2 + (P[:, 1] / 0.1) ** 2 + (P[:, 2] / 0.1) ** 2
+    clear = np.abs(f - 1) > 0.05
+    inside = oracle.surface_inside(V, T, P)
+    assert np.array_equal(inside[clear], (f[clear] < 1).astype(np.uint8))
+    assert 2000 < inside.sum() < 18000
+    R = gen.euler_zyx(0.3, 1.1, -0.7)
+    c = np.array([0.5, -0.2, 0.1])
+    inside2 = oracle.surface_inside(V @ R.T + c, T, P @ R.T + c)
+    assert np.array_equal(inside2[clear], inside[clear])
+
+
+def test_ray_parity_fish_surface_matches_its_shape():
+    g = gen.fish_ogrid("fish", 64, 48, 8, phase=1.1)
+    V, T = gen.body_surface(g)
+    rng = np.random.default_rng(4)
+    P = np.stack([rng.uniform(-0.55, 0.55, 30000), rng.uniform(-0.2, 0.2, 30000), rng.uniform(-0.12, 0.12, 30000)], 1)
+    inside = oracle.surface_inside(V, T, P)
+    # compare only points well inside or well outside the analytic body (the facets are chords of it): inside
+    # the body shrunk vertically by 1/1.25, or outside it stretched vertically by 1/0.8
+    inner = gen.inside_fish_layer(np.stack([P[:, 0], P[:, 1], P[:, 2] * 1.25], 1), 1.1, 0.0)
+    outer = ~gen.inside_fish_layer(np.stack([P[:, 0], P[:, 1], P[:, 2] * 0.8], 1), 1.1, 0.0)
+    assert inner.sum() > 500 and outer.sum() > 10000
+    assert np.all(inside[inner] == 1) and np.all(inside[outer & (np.abs(P[:, 0]) < 0.45)] == 0)
