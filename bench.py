@@ -337,6 +337,37 @@ def run_ovs(args, rank, world, local):
     matrix = {"points": nW, "nnz": int(row_ptr[-1].item()), "build_ms": ev_m[0].elapsed_time(ev_m[1]),
               "spmv_ms_per_component": ev_m[1].elapsed_time(ev_m[2]) / (4 * reps),
               "note": "rows = fringe points, 8 weights per found point; x = every grid's node values"}
+    # hole cutting (paper Sec. 2.2.1): every body's closed wall surface blanks the background nodes in a box
+    # around it (the box's nodes are listed once, outside the timing); time per step for all bodies
+    import gen as _gen
+
+    holes = None
+    bodies = [q for q, g in enumerate(sc.grids) if g.role == 1 and g.meta.get("kind") in ("ogrid", "fish")]
+    if bodies and sc.grids[0].meta.get("axes") is not None:
+        mW = inputs[W][0]
+        bg0 = sc.grids[0]
+        cuts = []
+        for q in bodies:
+            V, T = _gen.body_surface(sc.grids[q])
+            sid = ctx.add_surface(gids[q], V, T)
+            ext = np.abs(V).max(axis=0).max() + 0.02
+            cand = _gen.box_candidates(bg0, mW[q].c - ext, mW[q].c + ext).astype(np.int32)
+            cuts.append((sid, torch.as_tensor(cand).to(dev)))
+        iblank = torch.ones(bg0.n_nodes, dtype=torch.uint8, device=dev)
+        for gid, mo in zip(gids, mW):
+            ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
+        ev_h = events(2)
+        reps = 10
+        ev_h[0].record(stream)
+        for r in range(reps):
+            iblank.fill_(1)
+            for sid, cand in cuts:
+                ctx.hole_cut(sid, gids[0], iblank, nodes=cand)
+        ev_h[1].record(stream)
+        torch.cuda.synchronize()
+        holes = {"bodies": len(bodies), "candidate_nodes": int(sum(int(c.numel()) for _, c in cuts)),
+                 "blanked": int((iblank == 0).sum().item()), "ms_per_step": ev_h[0].elapsed_time(ev_h[1]) / reps}
+        ovs.ovs_set_iblank(ctx.ctx, gids[0], None)
     learned = None if args.no_learned else learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush,
                                                             K, W, ovs, torch)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
@@ -407,6 +438,7 @@ def run_ovs(args, rank, world, local):
         "batched_over_unbatched": unbatched_ms / (total_ms / K),
         "learned_vs_plain": learned,
         "interp_matrix": matrix,
+        "hole_cut": holes,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, inputs[W], args.cpu_sample)

@@ -185,6 +185,28 @@ int ovs_create_grid(ovs_ctx* ctx, const ovs_grid_desc* desc, void* dworkspace, s
 int ovs_set_motion(ovs_ctx* ctx, int32_t grid_id, const double R[9], const double c[3], const double V[3],
                    const double omega[3]);
 
+/* Hole cutting (Sec. 2.2.1): a closed triangulated body surface, fixed in the frame of body_grid (it moves with
+ * that grid's motion), and the blanking of another grid's nodes inside it.
+ * v: host FP64 [nv x 3] vertex coordinates (row-major, body frame); tri: host int32 [nt x 3] vertex ids; the
+ * surface must be closed (every edge shared by two triangles) for "inside" to be meaningful.
+ * ovs_surface_workspace_size: bytes of the device workspace the surface needs (its vertices, triangles and a
+ * grid of bins over its projection on the body frame's y-z plane). */
+int ovs_surface_workspace_size(int64_t nv, const double* v, int64_t nt, const int32_t* tri, size_t* bytes);
+/* Copies the surface into the caller's workspace dws (256-byte aligned, at least the size above; borrowed until
+ * ovs_ctx_destroy) and returns its id (0, 1, ... in creation order, at most OVS_MAX_GRIDS).  Synchronises the
+ * stream.  Errors: OVS_ERR_ARG (bad grid id, vertex id out of range, empty surface), OVS_ERR_WORKSPACE. */
+int ovs_create_surface(ovs_ctx* ctx, int32_t body_grid, int64_t nv, const double* v, int64_t nt, const int32_t* tri,
+                       void* dws, size_t bytes, int32_t* surface_id);
+/* For each node in nodes (device int32 [n], ids of target_grid's nodes; NULL: nodes 0 .. n-1), sets
+ * iblank[node] = 0 (device uint8 [target_grid's node count]) if the node lies inside the surface at the
+ * frames' current motions; other entries are left as they are (start from all ones; several surfaces can cut
+ * the same mask in turn).  Inside = an odd number of crossings of a ray along the body frame's +x: the point's
+ * (y, z) in a triangle's projection, with a point on a projected edge owned by the one triangle whose
+ * counter-clockwise edge runs downward (or level toward -y), and the crossing strictly ahead in x; FP64, one
+ * rounding per operation.  Enqueued on the context stream; bad node ids are reported by ovs_sync. */
+int ovs_hole_cut(ovs_ctx* ctx, int32_t surface_id, int32_t target_grid, int64_t n, const int32_t* nodes,
+                 uint8_t* iblank);
+
 /* Blanked nodes of a grid (Sec. 2.4: blanked donors are rejected).  iblank: device uint8 [its node count], 0 =
  * blanked (a hole point: never a donor node), nonzero = active; NULL: every node active (the state after
  * ovs_create_grid).  From then on a cell with a blanked corner node never donates: a point is given the

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ovs_guess.cuh"
+#include "ovs_hole.cuh"
 #include "ovs_matrix.cuh"
 #include "ovs_internal.cuh"
 
@@ -72,6 +73,10 @@ struct ovs_ctx {
     };
     std::vector<GraphEntry> graphs;
     ovs_tuning tune = {0, 0, 0, 0};  // launch shapes (0: defaults)
+    // body surfaces for hole cutting
+    int nsurf = 0;
+    SurfaceDev surf[OVS_MAX_GRIDS];
+    int32_t surf_body[OVS_MAX_GRIDS];
 };
 
 namespace {
@@ -508,6 +513,96 @@ int ovs_set_motion(ovs_ctx* c, int32_t gid, const double R[9], const double cc[3
               R[7] == 0;
     for (int q = 0; q < 3; ++q) id = id && cc[q] == 0 && V[q] == 0 && w[q] == 0;
     m.identity = id ? 1 : 0;
+    return OVS_OK;
+}
+
+namespace {
+struct SurfaceLayout {
+    size_t v, tri, start, tris, total;
+};
+// sections of a surface workspace, each 256-byte aligned
+SurfaceLayout surface_layout(int64_t nv, int64_t nt, int64_t nbins, int64_t nreg) {
+    SurfaceLayout L;
+    size_t off = 0;
+    L.v = off;
+    off = align_up(off + sizeof(double) * 3 * (size_t)nv);
+    L.tri = off;
+    off = align_up(off + sizeof(int32_t) * 3 * (size_t)nt);
+    L.start = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)(nbins + 1));
+    L.tris = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)std::max<int64_t>(1, nreg));
+    L.total = off;
+    return L;
+}
+bool surface_ok(int64_t nv, const double* v, int64_t nt, const int32_t* tri) {
+    if (nv < 3 || nt < 1 || !v || !tri) return false;
+    for (int64_t q = 0; q < 3 * nt; ++q)
+        if (tri[q] < 0 || tri[q] >= nv) return false;
+    for (int64_t q = 0; q < 3 * nv; ++q)
+        if (!std::isfinite(v[q])) return false;
+    return nt < ((int64_t)1 << 31) / 3;
+}
+}  // namespace
+
+int ovs_surface_workspace_size(int64_t nv, const double* v, int64_t nt, const int32_t* tri, size_t* bytes) {
+    if (!bytes || !surface_ok(nv, v, nt, tri)) return OVS_ERR_ARG;
+    SurfaceDev S;
+    std::vector<int32_t> start, tris;
+    const int64_t nreg = surface_bins(v, nv, tri, nt, S, start, tris);
+    *bytes = surface_layout(nv, nt, (int64_t)S.nb[0] * S.nb[1], nreg).total;
+    return OVS_OK;
+}
+
+int ovs_create_surface(ovs_ctx* c, int32_t body_grid, int64_t nv, const double* v, int64_t nt, const int32_t* tri,
+                       void* dws, size_t bytes, int32_t* surface_id) {
+    if (!c) return OVS_ERR_ARG;
+    if (body_grid < 0 || body_grid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", body_grid);
+    if (!surface_ok(nv, v, nt, tri)) return fail(c, OVS_ERR_ARG, "bad surface (empty, non-finite or vertex id out of range)");
+    if (c->nsurf >= OVS_MAX_GRIDS) return fail(c, OVS_ERR_ARG, "more than %d surfaces", OVS_MAX_GRIDS);
+    if (!dws || (uintptr_t)dws % kAlign) return fail(c, OVS_ERR_ARG, "surface workspace NULL or not 256-byte aligned");
+    SurfaceDev S;
+    std::vector<int32_t> start, tris;
+    const int64_t nreg = surface_bins(v, nv, tri, nt, S, start, tris);
+    const SurfaceLayout L = surface_layout(nv, nt, (int64_t)S.nb[0] * S.nb[1], nreg);
+    if (bytes < L.total)
+        return fail(c, OVS_ERR_WORKSPACE, "surface workspace has %zu bytes, needs %zu", bytes, L.total);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    char* base = (char*)dws;
+    OVS_CUDA(c, cudaMemcpyAsync(base + L.v, v, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, c->stream));
+    OVS_CUDA(c, cudaMemcpyAsync(base + L.tri, tri, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, c->stream));
+    OVS_CUDA(c, cudaMemcpyAsync(base + L.start, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    if (!tris.empty())
+        OVS_CUDA(c, cudaMemcpyAsync(base + L.tris, tris.data(), sizeof(int32_t) * tris.size(), cudaMemcpyHostToDevice,
+                                    c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+    S.v = (const double*)(base + L.v);
+    S.tri = (const int32_t*)(base + L.tri);
+    S.bin_start = (const int32_t*)(base + L.start);
+    S.bin_tris = (const int32_t*)(base + L.tris);
+    S.nv = nv;
+    S.nt = nt;
+    c->surf[c->nsurf] = S;
+    c->surf_body[c->nsurf] = body_grid;
+    if (surface_id) *surface_id = c->nsurf;
+    ++c->nsurf;
+    return OVS_OK;
+}
+
+int ovs_hole_cut(ovs_ctx* c, int32_t surface_id, int32_t target_grid, int64_t n, const int32_t* nodes,
+                 uint8_t* iblank) {
+    if (!c) return OVS_ERR_ARG;
+    if (surface_id < 0 || surface_id >= c->nsurf) return fail(c, OVS_ERR_ARG, "surface %d does not exist", surface_id);
+    if (target_grid < 0 || target_grid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", target_grid);
+    if (n < 0) return fail(c, OVS_ERR_ARG, "n = %lld", (long long)n);
+    if (n == 0) return OVS_OK;
+    if (!iblank) return fail(c, OVS_ERR_ARG, "iblank is NULL");
+    if (!nodes && n > c->grids[target_grid].nnodes) return fail(c, OVS_ERR_ARG, "n exceeds the grid's node count");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_hole_cut(c->surf[surface_id], c->grids[target_grid], c->motion[target_grid],
+                                    c->motion[c->surf_body[surface_id]], nodes, n, iblank, c->d_err, c->nsm, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hole_cut launch");
     return OVS_OK;
 }
 

@@ -53,7 +53,8 @@ EXPORTS = [
     "ovs_set_trace_events", "ovs_assemble_noalloc", "ovs_assemble_interpolate", "ovs_guess_param_count",
     "ovs_train_workspace_size", "ovs_train_guess", "ovs_guess_get_params", "ovs_guess_set_params",
     "ovs_guess_eval", "ovs_mlp_loss_grad", "ovs_set_tuning", "ovs_get_tuning", "ovs_autotune",
-    "ovs_interp_matrix", "ovs_spmv", "ovs_set_iblank",
+    "ovs_interp_matrix", "ovs_spmv", "ovs_set_iblank", "ovs_surface_workspace_size", "ovs_create_surface",
+    "ovs_hole_cut",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -157,6 +158,9 @@ def load(path: Optional[str] = None):
         "ovs_mlp_loss_grad": [V, I32, I64, V, V, V, V, V],
         "ovs_interp_matrix": [V, ctypes.POINTER(ovs_donors), V, V, V, I32],
         "ovs_set_iblank": [V, I32, V],
+        "ovs_surface_workspace_size": [I64, V, I64, V, ctypes.POINTER(SZ)],
+        "ovs_create_surface": [V, I32, I64, V, I64, V, V, SZ, ctypes.POINTER(I32)],
+        "ovs_hole_cut": [V, I32, I32, I64, V, V],
         "ovs_spmv": [V, I64, V, V, V, V, V, I32],
         "ovs_set_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
@@ -251,6 +255,34 @@ def ovs_assemble_interpolate(ctx, sets, nsets: int, donors: ovs_donors, fields, 
 def ovs_set_iblank(ctx, grid_id: int, iblank: int):
     """iblank: device pointer to uint8 [nodes] (0 = blanked), or 0 / None for every node active."""
     _check(ctx, load().ovs_set_iblank(ctx, int(grid_id), iblank or None))
+
+
+def ovs_surface_workspace_size(V, T) -> int:
+    """V: float64 (nv, 3) host vertices, T: int32 (nt, 3) host triangles."""
+    import numpy as np
+
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    out = ctypes.c_size_t(0)
+    rc = load().ovs_surface_workspace_size(len(V), V.ctypes.data, len(T), T.ctypes.data, ctypes.byref(out))
+    if rc != OVS_OK:
+        raise OvsError(rc, "ovs_surface_workspace_size: bad surface")
+    return out.value
+
+
+def ovs_create_surface(ctx, body_grid: int, V, T, dws: int, nbytes: int) -> int:
+    import numpy as np
+
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    sid = ctypes.c_int32(0)
+    _check(ctx, load().ovs_create_surface(ctx, int(body_grid), len(V), V.ctypes.data, len(T), T.ctypes.data, dws,
+                                          int(nbytes), ctypes.byref(sid)))
+    return sid.value
+
+
+def ovs_hole_cut(ctx, surface_id: int, target_grid: int, n: int, nodes: int, iblank: int):
+    _check(ctx, load().ovs_hole_cut(ctx, int(surface_id), int(target_grid), int(n), nodes or None, iblank))
 
 
 def ovs_interp_matrix(ctx, donors: ovs_donors, row_ptr: int, col: int, val: int, val_dtype: int):
@@ -515,6 +547,23 @@ class Context:
         else:
             best = ovs_autotune(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), None, 0, None, reps)
         return {k: getattr(best, k) for k, _ in ovs_tuning._fields_}
+
+    def add_surface(self, body_gid: int, V, T) -> int:
+        """ovs_create_surface of a closed triangulated body surface (host V (nv, 3), T (nt, 3)) fixed in grid
+        body_gid's frame; the workspace is a torch tensor kept alive by this context."""
+        nbytes = ovs_surface_workspace_size(V, T)
+        ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
+        ptr = _aligned(ws)
+        sid = ovs_create_surface(self.ctx, body_gid, V, T, ptr, nbytes)
+        self._surface_ws = getattr(self, "_surface_ws", []) + [ws]
+        return sid
+
+    def hole_cut(self, sid: int, target_gid: int, iblank, nodes=None):
+        """ovs_hole_cut: zero iblank (device uint8 tensor over target_gid's nodes) at the given nodes (device
+        int32 tensor, or None for all nodes) that lie inside surface sid."""
+        n = int(nodes.numel()) if nodes is not None else int(iblank.numel())
+        ovs_hole_cut(self.ctx, sid, target_gid, n, nodes.data_ptr() if nodes is not None else None,
+                     iblank.data_ptr())
 
     def interp_matrix(self, donors, val_dtype: int = OVS_F32):
         """ovs_interp_matrix of a donors dict -> (row_ptr int32 [n+1], col int64 [8n], val [8n]) on the device."""

@@ -1,0 +1,115 @@
+"""Hole cutting on the GPU (paper Sec. 2.2.1: background nodes inside a moving body's closed surface are blanked)
+against the oracle's ray parity:
+
+* every fish surface of the 8-fish school cuts the background nodes near it; on a seeded sample the GPU's mask
+  equals the oracle's, except at points whose answer the oracle itself changes under a 1e-12 displacement
+  (on the surface to within rounding: either answer is right there);
+* the mask then drives the donor search (blanked donors rejected), which equals the oracle's with that mask.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from harness import GpuScene, OracleScene, compare, split
+from paper_1910_09315_gb300 import ovs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+def near_body_nodes(bg, m):
+    """Background nodes in a box around a fish body (length 1, half-width < 0.2, half-height < 0.12), any yaw."""
+    return gen.box_candidates(bg, m.c - np.array([0.56, 0.56, 0.14]), m.c + np.array([0.56, 0.56, 0.14]))
+
+
+def test_hole_cut_matches_oracle(torch_cuda):
+    t = torch_cuda
+    sc = gen.config(3)
+    m = sc.motion(0)
+    scene = GpuScene(sc, max_points=1024)
+    scene.set_motion(m)
+    bg = sc.grids[0]
+    dev = scene.ctx.device
+    iblank = t.ones(bg.n_nodes, dtype=t.uint8, device=dev)
+    rng = np.random.default_rng(11)
+    checked, ambiguous, cut = 0, 0, 0
+    surfaces = []
+    for q in range(1, len(sc.grids)):
+        V, T = gen.body_surface(sc.grids[q])
+        sid = scene.ctx.add_surface(scene.ids[q], V, T)
+        surfaces.append((q, V, T))
+        cand = near_body_nodes(bg, m[q])
+        scene.ctx.hole_cut(sid, scene.ids[0], iblank, nodes=t.as_tensor(cand.astype(np.int32)).to(dev))
+    scene.ctx.sync()
+    mask = iblank.cpu().numpy()
+    # one seeded sample of background nodes, each tested against every surface whose box holds it
+    keep = rng.random(bg.n_nodes) < 0.15
+    inside_any = np.zeros(bg.n_nodes, dtype=bool)
+    sampled = np.zeros(bg.n_nodes, dtype=bool)
+    for q, V, T in surfaces:
+        cand = near_body_nodes(bg, m[q])
+        cand = cand[keep[cand]]
+        pb = gen.to_body(m[q], bg.xyz()[cand])
+        ins = oracle.surface_inside(V, T, pb).astype(bool)
+        inside_any[cand[ins]] = True
+        sampled[cand] = True
+        cut += int(ins.sum())
+    s = np.nonzero(sampled)[0]
+    got = mask[s] == 0
+    want = inside_any[s]
+    bad = s[got != want]
+    # a disagreement must be a point on a surface to within rounding: the oracle's own answer changes when it moves
+    for node in bad:
+        x = bg.xyz()[node]
+        flips = False
+        for q, V, T in surfaces:
+            pb = gen.to_body(m[q], x[None])[0]
+            d = 1e-12 * np.vstack([np.zeros(3), np.eye(3), -np.eye(3)])
+            r = oracle.surface_inside(V, T, pb + d)
+            flips = flips or (r.min() != r.max())
+        assert flips, f"node {node}: GPU {mask[node]} oracle inside {inside_any[node]}"
+        ambiguous += 1
+    checked = len(s)
+    assert checked > 100_000 and cut > 5_000 and ambiguous <= checked * 1e-4
+
+
+def test_hole_cut_drives_the_donor_search(torch_cuda):
+    t = torch_cuda
+    sc = gen.config(3)
+    m = sc.motion(0)
+    fsets = sc.fringe_sets(0, m)
+    n = sum(len(s.node_ids) for s in fsets)
+    scene = GpuScene(sc, max_points=n + 1024)
+    scene.set_motion(m)
+    bg = sc.grids[0]
+    dev = scene.ctx.device
+    iblank = t.ones(bg.n_nodes, dtype=t.uint8, device=dev)
+    for q in range(1, len(sc.grids)):
+        V, T = gen.body_surface(sc.grids[q])
+        sid = scene.ctx.add_surface(scene.ids[q], V, T)
+        scene.ctx.hole_cut(sid, scene.ids[0], iblank, nodes=t.as_tensor(near_body_nodes(bg, m[q]).astype(np.int32)).to(dev))
+    ovs.ovs_set_iblank(scene.ctx.ctx, scene.ids[0], iblank.data_ptr())
+    mask = iblank.cpu().numpy()
+    assert (mask == 0).sum() > 10_000
+    ref = OracleScene(sc)
+    ref.grids[0].set_iblank(mask)
+    _, d, out = scene.step(m, fsets)
+    res = GpuScene.to_numpy(d, out)
+    parts = split(res, [len(s.node_ids) for s in fsets])
+    rng = np.random.default_rng(5)
+    sample = [np.sort(rng.choice(len(s.node_ids), size=max(1, len(s.node_ids) // 10), replace=False)) for s in fsets]
+    oref, frames = ref.step(m, fsets, sample=sample)
+    total = 0
+    for k, (s, part, (od, oq)) in enumerate(zip(fsets, parts, oref)):
+        part = {kk: (v[..., sample[k]] if kk == "q" else v[sample[k]]) for kk, v in part.items()}
+        total += compare(part, od, oq, sc, frames, s.receiver, ovs.OVS_F32, label=f"hole-cut set {k}")
+    assert total > 50_000
