@@ -612,6 +612,10 @@ int ovs_set_iblank(ovs_ctx* c, int32_t grid_id, const uint8_t* iblank) {
     OVS_CUDA(c, cudaSetDevice(c->device));
     cudaError_t e = launch_mark_blocked(c->grids[grid_id], iblank, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_iblank launch");
+    c->grids[grid_id].blanked = iblank ? 1 : 0;
+    OVS_CUDA(c, cudaMemcpyAsync(c->d_grids + grid_id, &c->grids[grid_id], sizeof(GridDev), cudaMemcpyHostToDevice,
+                                c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));  // the host copy is the source of the transfer
     return OVS_OK;
 }
 

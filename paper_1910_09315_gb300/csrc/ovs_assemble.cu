@@ -367,9 +367,9 @@ __device__ bool neighbourhood_warp(const GridDev& g, const ff pf[3], const P64& 
                 o1 = off[q][1];
                 o2 = off[q][2];
             }
-        if (!cell_blocked(g.rec, mine))  // a blanked cell never donates
-            hit = contains_exact(g, mine, pf, p64, xi32[0] - (float)o0, xi32[1] - (float)o1, xi32[2] - (float)o2, a,
-                                 b, c);
+        hit = contains_exact(g, mine, pf, p64, xi32[0] - (float)o0, xi32[1] - (float)o1, xi32[2] - (float)o2, a, b,
+                             c);
+        if (hit && g.blanked && cell_blocked(g.rec, mine)) hit = false;  // a blanked cell never donates
     }
     unsigned m = __ballot_sync(0xffffffffu, hit);
     if (!m) return false;
@@ -394,7 +394,6 @@ constexpr int kSlowWarps = kSlowThreads / 32;
 __device__ __forceinline__ bool exhaustive_filter(const GridDev& g, const ff pf[3], uint32_t c, float xi[3]) {
     CellRec rec;
     load_rec(g.rec, c, rec);
-    if (rec_blocked(rec)) return false;  // a blanked cell never donates
     float d[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = __fadd_rn(__fsub_rn(pf[k].hi, rec.x0h[k]), __fsub_rn(pf[k].lo, rec.x0l[k]));
@@ -455,7 +454,7 @@ __device__ __forceinline__ bool exhaustive_filter(const GridDev& g, const ff pf[
     xi[0] = fu;
     xi[1] = fv;
     xi[2] = fw;
-    return true;
+    return !(g.blanked && rec_blocked(rec));  // a blanked cell never donates
 }
 
 // Warp-level exhaustive search of a control cell (lanes stride its list); lowest id wins.  All lanes call.

@@ -64,6 +64,8 @@ struct GridDev {
     double inv_w[3];           // bins per unit length
     int32_t nb[3];
     int32_t mlp_hidden;
+    int32_t blanked;  // 1 once ovs_set_iblank gave the grid a mask (cell records then carry blocked flags)
+    int32_t pad;
 };
 
 struct MotionDev {
