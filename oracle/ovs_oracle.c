@@ -382,11 +382,13 @@ int og_newton_hex(const double* X, const double* p, double* xi, int* iters) {
 
 /* ---------------------------------------------------------------------------------------------------------
  * Hole cutting (Sec. 2.2.1): a point is inside a closed triangulated body surface iff a ray from it crosses the
- * surface an odd number of times.  The ray runs along +x; a triangle is crossed when the point's (y, z) lies
- * in the triangle's projection on the y-z plane and the crossing lies strictly ahead in x.  A point on a
- * projected edge belongs to the one triangle whose counter-clockwise edge runs downward (or, level, toward -y),
- * so a ray through a shared edge or vertex is counted once.  Every operation is one FP64 rounding (no fused
- * multiply-add), so the decision is reproducible.
+ * surface an odd number of times.  The ray runs along the surface's shortest bounding-box axis r (the first
+ * such axis on a tie), with (u, w) the two axes that follow it cyclically; a triangle is crossed when the point's
+ * (u, w) lies in the triangle's projection on the u-w plane and the crossing lies strictly ahead along r.  A
+ * point on a projected edge belongs to the one triangle whose counter-clockwise edge runs toward -w (or, level,
+ * toward -u), so a ray through a shared edge or vertex is counted once.  Every operation is one FP64 rounding
+ * (no fused multiply-add), so the decision is reproducible.  (For a closed surface the parity does not depend
+ * on the ray's direction away from those ties; the shortest axis keeps the projected triangles apart.)
  * ------------------------------------------------------------------------------------------------------- */
 __attribute__((optimize("fp-contract=off"))) static double og_edge2(double ay, double az, double by, double bz,
                                                                    double py, double pz) {
@@ -395,34 +397,46 @@ __attribute__((optimize("fp-contract=off"))) static double og_edge2(double ay, d
 
 static int og_edge_owns(double ay, double az, double by, double bz) { return (bz < az) || (bz == az && by < ay); }
 
+/* ax = {r, u, w}: the ray's axis and the projection plane's two axes */
 __attribute__((optimize("fp-contract=off"))) static int og_ray_crosses(const double* A, const double* B,
-                                                                      const double* C, const double* p) {
-    const double area = og_edge2(A[1], A[2], B[1], B[2], C[1], C[2]);
+                                                                      const double* C, const double* p,
+                                                                      const int ax[3]) {
+    const int r = ax[0], u = ax[1], w = ax[2];
+    const double area = og_edge2(A[u], A[w], B[u], B[w], C[u], C[w]);
     if (area == 0.0) return 0; /* edge-on: never crossed */
     const double* a = A;
-    const double* b = area > 0 ? B : C; /* counter-clockwise order in the y-z plane */
+    const double* b = area > 0 ? B : C; /* counter-clockwise order in the u-w plane */
     const double* c = area > 0 ? C : B;
-    const double w0 = og_edge2(b[1], b[2], c[1], c[2], p[1], p[2]);
-    const double w1 = og_edge2(c[1], c[2], a[1], a[2], p[1], p[2]);
-    const double w2 = og_edge2(a[1], a[2], b[1], b[2], p[1], p[2]);
+    const double w0 = og_edge2(b[u], b[w], c[u], c[w], p[u], p[w]);
+    const double w1 = og_edge2(c[u], c[w], a[u], a[w], p[u], p[w]);
+    const double w2 = og_edge2(a[u], a[w], b[u], b[w], p[u], p[w]);
     if (w0 < 0 || w1 < 0 || w2 < 0) return 0;
-    if (w0 == 0 && !og_edge_owns(b[1], b[2], c[1], c[2])) return 0;
-    if (w1 == 0 && !og_edge_owns(c[1], c[2], a[1], a[2])) return 0;
-    if (w2 == 0 && !og_edge_owns(a[1], a[2], b[1], b[2])) return 0;
+    if (w0 == 0 && !og_edge_owns(b[u], b[w], c[u], c[w])) return 0;
+    if (w1 == 0 && !og_edge_owns(c[u], c[w], a[u], a[w])) return 0;
+    if (w2 == 0 && !og_edge_owns(a[u], a[w], b[u], b[w])) return 0;
     const double s = w0 + w1 + w2;
-    const double xs = w0 * a[0] + w1 * b[0] + w2 * c[0]; /* s times the crossing's x */
-    return xs > p[0] * s;
+    const double xs = w0 * a[r] + w1 * b[r] + w2 * c[r]; /* s times the crossing's coordinate along r */
+    return xs > p[r] * s;
 }
 
 /* inside[q] = 1 iff point q (n x 3, row-major) is inside the surface (nv vertices, nt triangles of vertex ids). */
 void og_surface_inside(int64_t nv, const double* V, int64_t nt, const int32_t* T, int64_t n, const double* P,
                        uint8_t* inside) {
-    (void)nv;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nv; ++i)
+        for (int c = 0; c < 3; ++c) {
+            if (V[3 * i + c] < lo[c]) lo[c] = V[3 * i + c];
+            if (V[3 * i + c] > hi[c]) hi[c] = V[3 * i + c];
+        }
+    int r = 0;
+    for (int c = 1; c < 3; ++c)
+        if (hi[c] - lo[c] < hi[r] - lo[r]) r = c;
+    const int ax[3] = {r, (r + 1) % 3, (r + 2) % 3};
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t q = 0; q < n; ++q) {
         int odd = 0;
         for (int64_t t = 0; t < nt; ++t)
-            odd ^= og_ray_crosses(V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], P + 3 * q);
+            odd ^= og_ray_crosses(V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], P + 3 * q, ax);
         inside[q] = (uint8_t)odd;
     }
 }
