@@ -350,7 +350,7 @@ def run_ovs(args, rank, world, local):
         for q in bodies:
             V, T = _gen.body_surface(sc.grids[q])
             sid = ctx.add_surface(gids[q], V, T)
-            ext = np.abs(V).max(axis=0).max() + 0.02
+            ext = np.linalg.norm(V, axis=1).max() + 0.02  # the body's bounding sphere: any rotation
             cand = _gen.box_candidates(bg0, mW[q].c - ext, mW[q].c + ext).astype(np.int32)
             cuts.append((sid, torch.as_tensor(cand).to(dev)))
         iblank = torch.ones(bg0.n_nodes, dtype=torch.uint8, device=dev)
@@ -449,8 +449,8 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
     """Train every body grid's guess network (3-H-H-3 SiLU, 2M samples of the grid itself, by the library's
     kernels) for H = 32, 64, 128; time the same steps with the plain start (previous donor, else the control
     cell) and the learned one, cold (no previous donors: the first step of a run) and warm (a time loop); the
-    width with the fastest cold step is kept (the MLP-width part of the autotuning).  ms_per_step: graph
-    launches; phases: a second, traced pass (direct launches)."""
+    width with the fastest cold step is kept (the MLP-width part of the autotuning).  ms_per_step: the median
+    step, graph launches (the mean beside it); phases: a second, traced pass (direct launches)."""
     import gen
 
     out = {"network": "3-H-H-3 SiLU, FP16 tensor-core inference (FP32 accumulation in layers 1 and 3), trained by "
@@ -486,7 +486,9 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
             one_step(s, dev_sets[s])
             e1[k].record(stream)
         torch.cuda.synchronize()
-        ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
+        per_step = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+        ms = float(np.median(per_step))  # the median step: a one-off stall of the host does not decide it
+        ms_mean = float(np.mean(per_step))
         # traced pass: per-phase times and walk statistics (direct launches)
         if not cold:
             for s in range(W):
@@ -509,7 +511,7 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
         st = ctx.stats(reset=True)
         ctx.set_options(collect_stats=0)
         learned_mode = mode in (ovs.OVS_GUESS_MLP, ovs.OVS_GUESS_MLP_ONLY)
-        return {"ms_per_step": ms, "walk_steps_per_step": st["walk_steps"] / len(steps),
+        return {"ms_per_step": ms, "ms_per_step_mean": ms_mean, "walk_steps_per_step": st["walk_steps"] / len(steps),
                 "guess_kernels_ms": float(np.mean([r[5].elapsed_time(r[6]) for r in tr])) if learned_mode else 0.0,
                 "k_assemble_ms": float(np.mean([r[0].elapsed_time(r[1]) for r in tr])),
                 "slow_kernels_ms": float(np.mean([r[1].elapsed_time(r[2]) for r in tr])),

@@ -200,10 +200,10 @@ int ovs_create_surface(ovs_ctx* ctx, int32_t body_grid, int64_t nv, const double
 /* For each node in nodes (device int32 [n], ids of target_grid's nodes; NULL: nodes 0 .. n-1), sets
  * iblank[node] = 0 (device uint8 [target_grid's node count]) if the node lies inside the surface at the
  * frames' current motions; other entries are left as they are (start from all ones; several surfaces can cut
- * the same mask in turn).  Inside = an odd number of crossings of a ray along the body frame's +x: the point's
- * (y, z) in a triangle's projection, with a point on a projected edge owned by the one triangle whose
- * counter-clockwise edge runs downward (or level toward -y), and the crossing strictly ahead in x; FP64, one
- * rounding per operation.  Enqueued on the context stream; bad node ids are reported by ovs_sync. */
+ * the same mask in turn).  Inside = an odd number of crossings of a ray along the surface's shortest box axis r
+ * of the body frame (the first on a tie; u, w = the next axes cyclically): the point's (u, w) in a triangle's
+ * projection, with a point on a projected edge owned by the one triangle whose counter-clockwise edge runs
+ * toward -w (or level toward -u), and the crossing strictly ahead along r; FP64, one rounding per operation.  Enqueued on the context stream; bad node ids are reported by ovs_sync. */
 int ovs_hole_cut(ovs_ctx* ctx, int32_t surface_id, int32_t target_grid, int64_t n, const int32_t* nodes,
                  uint8_t* iblank);
 
