@@ -518,7 +518,7 @@ int ovs_set_motion(ovs_ctx* c, int32_t gid, const double R[9], const double cc[3
 
 namespace {
 struct SurfaceLayout {
-    size_t v, tri, start, tris, uv, total;
+    size_t v, tri, start, rec, tr, total;
 };
 // sections of a surface workspace, each 256-byte aligned
 SurfaceLayout surface_layout(int64_t nv, int64_t nt, int64_t nbins, int64_t nreg) {
@@ -530,10 +530,10 @@ SurfaceLayout surface_layout(int64_t nv, int64_t nt, int64_t nbins, int64_t nreg
     off = align_up(off + sizeof(int32_t) * 3 * (size_t)nt);
     L.start = off;
     off = align_up(off + sizeof(int32_t) * (size_t)(nbins + 1));
-    L.tris = off;
-    off = align_up(off + sizeof(int32_t) * (size_t)std::max<int64_t>(1, nreg));
-    L.uv = off;
-    off = align_up(off + sizeof(float) * 6 * (size_t)std::max<int64_t>(1, nreg));
+    L.rec = off;
+    off = align_up(off + sizeof(float) * 8 * (size_t)std::max<int64_t>(1, nreg));
+    L.tr = off;
+    off = align_up(off + sizeof(float) * 4 * (size_t)nt);
     L.total = off;
     return L;
 }
@@ -565,8 +565,8 @@ int ovs_create_surface(ovs_ctx* c, int32_t body_grid, int64_t nv, const double* 
     if (!dws || (uintptr_t)dws % kAlign) return fail(c, OVS_ERR_ARG, "surface workspace NULL or not 256-byte aligned");
     SurfaceDev S;
     std::vector<int32_t> start, tris;
-    std::vector<float> uv;
-    const int64_t nreg = surface_bins(v, nv, tri, nt, S, start, tris, &uv);
+    std::vector<float> rec, tr;
+    const int64_t nreg = surface_bins(v, nv, tri, nt, S, start, tris, &rec, &tr);
     const SurfaceLayout L = surface_layout(nv, nt, (int64_t)S.nb[0] * S.nb[1], nreg);
     if (bytes < L.total)
         return fail(c, OVS_ERR_WORKSPACE, "surface workspace has %zu bytes, needs %zu", bytes, L.total);
@@ -576,18 +576,16 @@ int ovs_create_surface(ovs_ctx* c, int32_t body_grid, int64_t nv, const double* 
     OVS_CUDA(c, cudaMemcpyAsync(base + L.tri, tri, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, c->stream));
     OVS_CUDA(c, cudaMemcpyAsync(base + L.start, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice,
                                 c->stream));
-    if (!tris.empty()) {
-        OVS_CUDA(c, cudaMemcpyAsync(base + L.tris, tris.data(), sizeof(int32_t) * tris.size(), cudaMemcpyHostToDevice,
+    if (!rec.empty())
+        OVS_CUDA(c, cudaMemcpyAsync(base + L.rec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice,
                                     c->stream));
-        OVS_CUDA(c, cudaMemcpyAsync(base + L.uv, uv.data(), sizeof(float) * uv.size(), cudaMemcpyHostToDevice,
-                                    c->stream));
-    }
+    OVS_CUDA(c, cudaMemcpyAsync(base + L.tr, tr.data(), sizeof(float) * tr.size(), cudaMemcpyHostToDevice, c->stream));
     OVS_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
     S.v = (const double*)(base + L.v);
     S.tri = (const int32_t*)(base + L.tri);
     S.bin_start = (const int32_t*)(base + L.start);
-    S.bin_tris = (const int32_t*)(base + L.tris);
-    S.bin_uv = (const float2*)(base + L.uv);
+    S.bin_rec = (const float4*)(base + L.rec);
+    S.tri_r = (const float4*)(base + L.tr);
     S.nv = nv;
     S.nt = nt;
     c->surf[c->nsurf] = S;

@@ -5,8 +5,11 @@
 // a projected edge belonging to the one triangle whose counter-clockwise edge runs downward, or level toward -y)
 // and the crossing lies strictly ahead in x.  Every FP64 operation is one rounding (no fused
 // multiply-add: the _rn intrinsics), so the decision is reproducible.  The triangles are registered in a uniform
-// grid of bins over the surface's projected box; a point tests only its bin's triangles.
+// grid of bins over the surface's projected box; a point tests only its bin's triangles, first with an FP32
+// screen whose error bound is proven below, and in FP64 only where that screen is unsure.
 #include "ovs_hole.cuh"
+
+#include <cstring>
 
 namespace ovs {
 
@@ -39,8 +42,10 @@ __device__ __forceinline__ int ray_crosses(const double* A, const double* B, con
     return xs > __dmul_rn(px, s) ? 1 : 0;
 }
 
-// target-grid position -> body frame in FP32 (x_b = M x + t), and the surface box widened by the FP32 error bound
-struct HoleF32 {
+// target-grid position -> body frame, x_b = M x + t: in FP32 from the coordinates' high parts for a first
+// rejection against the surface box widened by the FP32 error bound (lo, hi), and as FP32 pairs (X) for the rest
+struct HoleXf {
+    XfFF X;
     float M[9], t[3], lo[3], hi[3];
     __device__ __forceinline__ float3 apply(float x, float y, float z) const {
         return make_float3(fmaf(M[0], x, fmaf(M[1], y, fmaf(M[2], z, t[0]))),
@@ -49,77 +54,161 @@ struct HoleF32 {
     }
 };
 
-// FP32 screen of one triangle (plane coordinates (y, z) of A, B, C and of the point): true when the FP64 test
-// can only say "not crossed" -- the projected triangle's orientation is certain and the point lies outside one
-// of its edges by more than the FP32 error bound.  With every coordinate of magnitude <= mag, the inputs' FP32
-// rounding moves a difference by <= 1.2e-7 mag and the products round by <= 6e-8 of their size; the bound
-// 1e-5 ((|dy| + mag)(|ez| + mag) + (|dz| + mag)(|ey| + mag)) exceeds both by a factor of about 80.
-__device__ __forceinline__ bool surely_missed(const float* A, const float* B, const float* C, float qy, float qz,
-                                              float mag) {
-    const float ay = A[1], az = A[2], by = B[1], bz = B[2], cy = C[1], cz = C[2];
-    auto e = [mag](float y0, float z0, float y1, float z1, float y2, float z2, float& err) {
-        const float dy = y1 - y0, dz = z1 - z0, ey = y2 - y0, ez = z2 - z0;
-        err = 1e-5f * ((fabsf(dy) + mag) * (fabsf(ez) + mag) + (fabsf(dz) + mag) * (fabsf(ey) + mag));
-        return dy * ez - dz * ey;
-    };
-    float ea, e0, e1, e2;
-    const float area = e(ay, az, by, bz, cy, cz, ea);
-    if (!(fabsf(area) > ea)) return false;  // orientation unsure: decide in FP64
-    const float s = area > 0 ? 1.f : -1.f;   // counter-clockwise order: the point inside has every s * w >= 0
-    const float w0 = e(by, bz, cy, cz, qy, qz, e0), w1 = e(cy, cz, ay, az, qy, qz, e1), w2 = e(ay, az, by, bz, qy, qz, e2);
-    return s * w0 < -e0 || s * w1 < -e1 || s * w2 < -e2;
+// The FP32 edge function dy ez - dz ey of (y0, z0) -> (y1, z1) at (y2, z2), and a bound on its distance from the
+// exact value of the same function at the FP64 inputs (returned in err).  The FP32 inputs are the FP64 values
+// rounded (each within u |c| <= u mag, u = 2^-24, every coordinate and the point being <= mag in size), so a
+// computed difference d' of two of them is within D = 4 u mag of the exact difference d, a product d1' d2' within
+// D (|d1| + |d2|) + D^2 + u |d1 d2|, and the edge function (with or without a fused multiply-add) within
+// D (|dy| + |ez| + |dz| + |ey|) + 2 D^2 + 2 u (|dy ez| + |dz ey|); the FP64 test's own rounding adds a few 1e-16
+// (|dy ez| + |dz ey|).  The bound 4e-6 (mag (|dy| + |dz| + |ey| + |ez|) + |dy ez| + |dz ey|) + 1e-12 mag^2
+// exceeds all of it by a factor of at least 8.
+__device__ __forceinline__ float edge_f32(float y0, float z0, float y1, float z1, float y2, float z2, float mag,
+                                          float& err) {
+    const float dy = y1 - y0, dz = z1 - z0, ey = y2 - y0, ez = z2 - z0;
+    const float p0 = dy * ez, p1 = dz * ey;
+    err = 4e-6f * (mag * (fabsf(dy) + fabsf(dz) + fabsf(ey) + fabsf(ez)) + fabsf(p0) + fabsf(p1)) + 1e-12f * mag * mag;
+    return p0 - p1;
 }
 
-__global__ void __launch_bounds__(256) k_hole_cut(SurfaceDev S, HoleF32 F, GridDev tg, MotionDev mt, MotionDev mb,
-                                                  const int32_t* __restrict__ nodes, int64_t n,
-                                                  uint8_t* __restrict__ iblank, int32_t* __restrict__ err) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t node = nodes ? (int64_t)__ldg(nodes + q) : q;
-        if (node < 0 || node >= tg.nnodes) {
-            atomicOr(err, kErrBadNode);
-            continue;
-        }
-        {
-            // FP32 pre-rejection from the grid's FP32 coordinates (FP64 is slow on this GPU): a point further than
-            // 1e-4 (relative to its size and the box's) outside the surface's box in FP32 lies outside it in FP64
-            const int64_t nn = tg.nnodes;
-            const float3 pf = F.apply(__ldg(tg.xff + node), __ldg(tg.xff + 2 * nn + node), __ldg(tg.xff + 4 * nn + node));
-            bool out = false;
+enum Screen { kMissed = 0, kCrossed = 1, kUnsure = 2 };
+
+// FP32 decision of the FP64 test for one triangle (plane coordinates A, B, C; ray-axis coordinates r of A, B, C
+// loaded on demand), or kUnsure.  With w0, w1, w2 the edge functions of B->C, C->A, A->B at the point q and s the
+// sign of the projected area:
+//  * area certain (|area| > its bound): the FP64 test has the same orientation; it misses if some s w_i is below
+//    minus its bound, and if every s w_i is above its bound the point is strictly inside (no edge ownership), and
+//    crossed iff s (w0 (A.r - q.r) + w1 (B.r - q.r) + w2 (C.r - q.r)) > 0 -- the FP64 comparison of the crossing
+//    with the point along r, up to a positive factor -- when that sum exceeds its bound: each w_i is within e_i
+//    / 8, each FP32 difference within 4 u mag, and the FP32 and FP64 sums' rounding within 3 u of the sum of the
+//    terms' sizes, so e_i (|d_i| + 4e-6 mag) + 4e-6 |w_i| (mag + |d_i|) per term bounds the distance;
+//  * area unsure: some w_i below minus its bound and some w_j above its bound means outside for either
+//    orientation (and an FP64 area of 0 is never crossed).
+__device__ __forceinline__ int screen(float4 g0, float4 g1, const float4* __restrict__ tri_r, float qy, float qz,
+                                      float qr, float mag) {
+    float ea, e0, e1, e2;
+    const float area = edge_f32(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, mag, ea);
+    const float w0 = edge_f32(g0.z, g0.w, g1.x, g1.y, qy, qz, mag, e0);
+    const float w1 = edge_f32(g1.x, g1.y, g0.x, g0.y, qy, qz, mag, e1);
+    const float w2 = edge_f32(g0.x, g0.y, g0.z, g0.w, qy, qz, mag, e2);
+    if (!(fabsf(area) > ea)) {
+        const bool neg = w0 < -e0 || w1 < -e1 || w2 < -e2, pos = w0 > e0 || w1 > e1 || w2 > e2;
+        return neg && pos ? kMissed : kUnsure;
+    }
+    const float s = area > 0 ? 1.f : -1.f;
+    const float s0 = s * w0, s1 = s * w1, s2 = s * w2;
+    if (s0 < -e0 || s1 < -e1 || s2 < -e2) return kMissed;
+    if (!(s0 > e0 && s1 > e1 && s2 > e2)) return kUnsure;
+    const float4 r = __ldg(tri_r + __float_as_int(g1.z));
+    const float d0 = r.x - qr, d1 = r.y - qr, d2 = r.z - qr;
+    const float D = s * (w0 * d0 + w1 * d1 + w2 * d2);
+    const float eD = e0 * (fabsf(d0) + 4e-6f * mag) + e1 * (fabsf(d1) + 4e-6f * mag) + e2 * (fabsf(d2) + 4e-6f * mag) +
+                     4e-6f * (fabsf(w0) * (mag + fabsf(d0)) + fabsf(w1) * (mag + fabsf(d1)) + fabsf(w2) * (mag + fabsf(d2)));
+    if (D > eD) return kCrossed;
+    if (D < -eD) return kMissed;
+    return kUnsure;
+}
+
+// A point's bin in FP32.  The FP32 point is within u mag of the pair-precision one and the map's own rounding
+// moves it by a few u mag more, far inside the margin (1e-5 mag) by which each triangle's projected box was
+// widened when it was registered: every triangle whose box holds the point is in the point's bin.
+__device__ __forceinline__ int64_t bin_of_point(const SurfaceDev& S, float qy, float qz) {
+    int by = (int)floorf((qy - S.lo_f[0]) * S.inv_w_f[0]);
+    int bz = (int)floorf((qz - S.lo_f[1]) * S.inv_w_f[1]);
+    by = min(max(by, 0), S.nb[0] - 1);
+    bz = min(max(bz, 0), S.nb[1] - 1);
+    return by + (int64_t)S.nb[0] * bz;
+}
+
+// The point (pr along the ray; pu, pw in the plane; FP32 pairs) against registration e: the FP32 decision, else
+// the FP64 test at the point hi + lo.
+__device__ __forceinline__ int crosses(const SurfaceDev& S, int32_t e, ff pr, ff pu, ff pw) {
+    const float4 g0 = __ldg(S.bin_rec + 2 * (int64_t)e), g1 = __ldg(S.bin_rec + 2 * (int64_t)e + 1);
+    const int sc = screen(g0, g1, S.tri_r, pu.hi, pw.hi, pr.hi, S.mag);
+    if (sc != kUnsure) return sc;
+    const int ar = S.ax[0], au = S.ax[1], aw = S.ax[2];
+    const int32_t t = __float_as_int(g1.z);
+    const int32_t i0 = __ldg(S.tri + 3 * t), i1 = __ldg(S.tri + 3 * t + 1), i2 = __ldg(S.tri + 3 * t + 2);
+    const double A[3] = {__ldg(S.v + 3 * i0 + ar), __ldg(S.v + 3 * i0 + au), __ldg(S.v + 3 * i0 + aw)};
+    const double B[3] = {__ldg(S.v + 3 * i1 + ar), __ldg(S.v + 3 * i1 + au), __ldg(S.v + 3 * i1 + aw)};
+    const double C[3] = {__ldg(S.v + 3 * i2 + ar), __ldg(S.v + 3 * i2 + au), __ldg(S.v + 3 * i2 + aw)};
+    return ray_crosses(A, B, C, (double)pr.hi + (double)pr.lo, (double)pu.hi + (double)pu.lo,
+                       (double)pw.hi + (double)pw.lo);
+}
+
+constexpr int kHoleThreads = 256;
+constexpr int kHeavyBin = 32;  // a point whose bin holds more registrations is tested by its whole warp
+
+// One lane per candidate node: the node's position in the body frame as FP32 pairs p (about 1e-14 relative),
+// then its bin's registrations, each decided in FP32 and, where that is unsure, tested in FP64 at the point
+// hi + lo of p.  The parity is that of every triangle the FP64 test crosses at that point: a triangle outside
+// the bin has its box further than the margin from the point, and a point further than the margin outside the
+// surface's box is outside the body.  FP64 (slow on this GPU) runs only in those unsure tests.  A point in a bin
+// with more than kHeavyBin registrations (near a pole, where many triangles meet) is tested by all 32 lanes of its
+// warp, a registration per lane, the parity a ballot's popcount: such bins would otherwise set the kernel's tail.
+// The candidate loop is warp-uniform (the stride is a multiple of 32) so that every lane reaches the ballots.
+__global__ void __launch_bounds__(kHoleThreads) k_hole_cut(SurfaceDev S, HoleXf F, GridDev tg,
+                                                           const int32_t* __restrict__ nodes, int64_t n,
+                                                           uint8_t* __restrict__ iblank, int32_t* __restrict__ err) {
+    const int ar = S.ax[0], au = S.ax[1], aw = S.ax[2];
+    const float m = (float)kBinMargin * S.mag;
+    const int lane = threadIdx.x & 31;
+    const int64_t nn = tg.nnodes;
+    for (int64_t base = blockIdx.x * (int64_t)kHoleThreads + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * kHoleThreads) {
+        const int64_t q = base + lane;
+        int64_t node = -1;
+        bool work = false;
+        ff pr = {0.f, 0.f}, pu = {0.f, 0.f}, pw = {0.f, 0.f};
+        int32_t e0 = 0, e1 = 0;
+        if (q < n) {
+            node = nodes ? (int64_t)__ldg(nodes + q) : q;
+            if (node < 0 || node >= nn) {
+                atomicOr(err, kErrBadNode);
+            } else {
+                const ff x[3] = {{__ldg(tg.xff + node), __ldg(tg.xff + nn + node)},
+                                 {__ldg(tg.xff + 2 * nn + node), __ldg(tg.xff + 3 * nn + node)},
+                                 {__ldg(tg.xff + 4 * nn + node), __ldg(tg.xff + 5 * nn + node)}};
+                // first rejection: further than the FP32 error bound outside the surface's box
+                const float3 pf = F.apply(x[0].hi, x[1].hi, x[2].hi);
+                work = !(pf.x < F.lo[0] || pf.x > F.hi[0] || pf.y < F.lo[1] || pf.y > F.hi[1] || pf.z < F.lo[2] ||
+                         pf.z > F.hi[2]);
+                if (work) {
+                    ff pb[3];
+                    xf_apply(F.X, x, pb);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float v = c == 0 ? pf.x : (c == 1 ? pf.y : pf.z);
-                out = out || v < F.lo[c] || v > F.hi[c];
+                    for (int c = 0; c < 3; ++c)
+                        work = work && !(pb[c].hi < (float)S.bmin[c] - m || pb[c].hi > (float)S.bmax[c] + m);
+                    auto pick = [&pb](int c) { return c == 0 ? pb[0] : (c == 1 ? pb[1] : pb[2]); };  // registers
+                    pr = pick(ar);
+                    pu = pick(au);
+                    pw = pick(aw);
+                }
+                if (work) {
+                    const int64_t b = bin_of_point(S, pu.hi, pw.hi);
+                    e0 = __ldg(S.bin_start + b);
+                    e1 = __ldg(S.bin_start + b + 1);
+                }
             }
-            if (out) continue;
         }
-        const double3 x = make_double3(__ldg(tg.x + node), __ldg(tg.y + node), __ldg(tg.z + node));
-        const double3 p3 = to_body(mb, to_inertial(mt, x));
-        if (!(p3.x >= S.bmin[0] && p3.x <= S.bmax[0] && p3.y >= S.bmin[1] && p3.y <= S.bmax[1] && p3.z >= S.bmin[2] &&
-              p3.z <= S.bmax[2]))
-            continue;  // outside the surface's box: outside the body
-        const double pa[3] = {p3.x, p3.y, p3.z};
-        const int ar = S.ax[0], au = S.ax[1], aw = S.ax[2];
-        const double3 p = make_double3(pa[ar], pa[au], pa[aw]);  // (ray axis, plane axes)
-        int by = (int)floor((p.y - S.lo[0]) * S.inv_w[0]);
-        int bz = (int)floor((p.z - S.lo[1]) * S.inv_w[1]);
-        by = min(max(by, 0), S.nb[0] - 1);
-        bz = min(max(bz, 0), S.nb[1] - 1);
-        const int64_t b = by + (int64_t)S.nb[0] * bz;
+        const bool heavy = work && e1 - e0 > kHeavyBin;
         int odd = 0;
-        const float qy = (float)p.y, qz = (float)p.z;
-        for (int32_t e = __ldg(S.bin_start + b); e < __ldg(S.bin_start + b + 1); ++e) {
-            const float2 ua = __ldg(S.bin_uv + 3 * (int64_t)e), ub = __ldg(S.bin_uv + 3 * (int64_t)e + 1),
-                         uc = __ldg(S.bin_uv + 3 * (int64_t)e + 2);
-            const float A32[3] = {0.f, ua.x, ua.y}, B32[3] = {0.f, ub.x, ub.y}, C32[3] = {0.f, uc.x, uc.y};
-            if (surely_missed(A32, B32, C32, qy, qz, S.mag)) continue;
-            const int32_t t = __ldg(S.bin_tris + e);
-            const int32_t i0 = __ldg(S.tri + 3 * t), i1 = __ldg(S.tri + 3 * t + 1), i2 = __ldg(S.tri + 3 * t + 2);
-            const double A[3] = {__ldg(S.v + 3 * i0 + ar), __ldg(S.v + 3 * i0 + au), __ldg(S.v + 3 * i0 + aw)};
-            const double B[3] = {__ldg(S.v + 3 * i1 + ar), __ldg(S.v + 3 * i1 + au), __ldg(S.v + 3 * i1 + aw)};
-            const double C[3] = {__ldg(S.v + 3 * i2 + ar), __ldg(S.v + 3 * i2 + au), __ldg(S.v + 3 * i2 + aw)};
-            odd ^= ray_crosses(A, B, C, p.x, p.y, p.z);
+        if (work && !heavy) {
+#pragma unroll 4
+            for (int32_t e = e0; e < e1; ++e) odd ^= crosses(S, e, pr, pu, pw);
         }
-        if (odd) iblank[node] = 0;
+        // the heavy points of this warp, one after another, each over all lanes
+        for (unsigned hm = __ballot_sync(0xffffffffu, heavy); hm; hm &= hm - 1) {
+            const int l = __ffs(hm) - 1;
+            const int32_t h0 = __shfl_sync(0xffffffffu, e0, l), h1 = __shfl_sync(0xffffffffu, e1, l);
+            const ff hr = {__shfl_sync(0xffffffffu, pr.hi, l), __shfl_sync(0xffffffffu, pr.lo, l)};
+            const ff hu = {__shfl_sync(0xffffffffu, pu.hi, l), __shfl_sync(0xffffffffu, pu.lo, l)};
+            const ff hw = {__shfl_sync(0xffffffffu, pw.hi, l), __shfl_sync(0xffffffffu, pw.lo, l)};
+            int par = 0;
+            for (int32_t e = h0 + lane; e < h1; e += 32) par ^= crosses(S, e, hr, hu, hw);
+            const unsigned bits = __ballot_sync(0xffffffffu, par != 0);
+            if (lane == l) odd = __popc(bits) & 1;
+        }
+        if (work && odd) iblank[node] = 0;
     }
 }
 
@@ -128,20 +217,28 @@ __global__ void __launch_bounds__(256) k_hole_cut(SurfaceDev S, HoleF32 F, GridD
 cudaError_t launch_hole_cut(const SurfaceDev& S, const GridDev& target, const MotionDev& mt, const MotionDev& mb,
                             const int32_t* nodes, int64_t n, uint8_t* iblank, int32_t* err, int nsm, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    // the FP32 map composed in FP64 on the host: M = R_b^T R_t, t = R_b^T (c_t - c_b); margin: 1e-4 of the
-    // largest of the box's extent and the transformed magnitudes (far above the FP32 rounding of 3 products)
-    HoleF32 F;
+    // the map composed in FP64 on the host: M = R_b^T R_t, t = R_b^T (c_t - c_b); first-rejection margin: 1e-4 of
+    // the largest of the box's extent and the transformed magnitudes (far above the FP32 rounding of 3 products)
+    HoleXf F;
+    memset(&F, 0, sizeof F);
+    F.X.identity = mt.identity && mb.identity;
     double tmag = 0, ext = 0;
+    auto split2 = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
     for (int i = 0; i < 3; ++i) {
         double tv = 0;
         for (int k = 0; k < 3; ++k) {
             double m = 0;
             for (int j = 0; j < 3; ++j) m += (mb.identity ? (i == j) : mb.R[3 * j + i]) * (mt.identity ? (j == k) : mt.R[3 * j + k]);
             F.M[3 * i + k] = (float)m;
+            split2(m, F.X.Mh[3 * i + k], F.X.Ml[3 * i + k]);
         }
         for (int j = 0; j < 3; ++j)
             tv += (mb.identity ? (i == j) : mb.R[3 * j + i]) * ((mt.identity ? 0.0 : mt.c[j]) - (mb.identity ? 0.0 : mb.c[j]));
         F.t[i] = (float)tv;
+        split2(tv, F.X.th[i], F.X.tl[i]);
         tmag = std::max(tmag, std::fabs(tv));
         ext = std::max(ext, S.bmax[i] - S.bmin[i]);
     }
@@ -154,17 +251,18 @@ cudaError_t launch_hole_cut(const SurfaceDev& S, const GridDev& target, const Mo
         F.lo[c] = (float)(S.bmin[c] - margin);
         F.hi[c] = (float)(S.bmax[c] + margin);
     }
-    const int64_t want = (n + 255) / 256;
+    const int64_t want = (n + kHoleThreads - 1) / kHoleThreads;
     const unsigned blocks = (unsigned)std::min<int64_t>(want, (int64_t)nsm * 8);
-    k_hole_cut<<<blocks, 256, 0, st>>>(S, F, target, mt, mb, nodes, n, iblank, err);
+    k_hole_cut<<<blocks, kHoleThreads, 0, st>>>(S, F, target, nodes, n, iblank, err);
     return cudaGetLastError();
 }
 
 // Host: the bin grid of a surface (about one bin per triangle, shaped like the projected box), each triangle
-// registered in every bin its projected box overlaps, with its plane coordinates in FP32 beside it (uv).  The device maps a point to its bin by the same IEEE operations (subtract, multiply, floor), and
-// that map is monotone, so a point inside a triangle's box always falls in one of the triangle's bins.
+// registered in every bin that its projected box, widened by the margin, overlaps, with its plane coordinates in
+// FP32 and its id in the registration's record.
 int64_t surface_bins(const double* v, int64_t nv, const int32_t* tri, int64_t nt, SurfaceDev& S,
-                     std::vector<int32_t>& start, std::vector<int32_t>& tris, std::vector<float>* uv) {
+                     std::vector<int32_t>& start, std::vector<int32_t>& tris, std::vector<float>* rec,
+                     std::vector<float>* tr) {
     for (int c = 0; c < 3; ++c) {
         S.bmin[c] = 1e300;
         S.bmax[c] = -1e300;
@@ -192,7 +290,10 @@ int64_t surface_bins(const double* v, int64_t nv, const int32_t* tri, int64_t nt
         S.lo[d] = S.bmin[S.ax[1 + d]];
         const double ext = S.bmax[S.ax[1 + d]] - S.bmin[S.ax[1 + d]];
         S.inv_w[d] = ext > 0 ? S.nb[d] / ext : 0.0;
+        S.lo_f[d] = (float)S.lo[d];
+        S.inv_w_f[d] = (float)S.inv_w[d];
     }
+    const double reg_margin = kBinMargin * mag;
     const int nb0 = S.nb[0], nb1 = S.nb[1];
     auto bin_of = [&](int d, double x) {
         int b = (int)std::floor((x - S.lo[d]) * S.inv_w[d]);
@@ -207,10 +308,10 @@ int64_t surface_bins(const double* v, int64_t nv, const int32_t* tri, int64_t nt
                 mn[d] = std::min(mn[d], v[3 * tri[3 * t + k] + S.ax[1 + d]]);
                 mx[d] = std::max(mx[d], v[3 * tri[3 * t + k] + S.ax[1 + d]]);
             }
-        lo0[t] = bin_of(0, mn[0]);
-        hi0[t] = bin_of(0, mx[0]);
-        lo1[t] = bin_of(1, mn[1]);
-        hi1[t] = bin_of(1, mx[1]);
+        lo0[t] = bin_of(0, mn[0] - reg_margin);
+        hi0[t] = bin_of(0, mx[0] + reg_margin);
+        lo1[t] = bin_of(1, mn[1] - reg_margin);
+        hi1[t] = bin_of(1, mx[1] + reg_margin);
         for (int b1 = lo1[t]; b1 <= hi1[t]; ++b1)
             for (int b0 = lo0[t]; b0 <= hi0[t]; ++b0) ++count[b0 + (int64_t)nb0 * b1];
     }
@@ -222,18 +323,27 @@ int64_t surface_bins(const double* v, int64_t nv, const int32_t* tri, int64_t nt
     }
     start[(size_t)nb0 * nb1] = (int32_t)acc;
     tris.assign((size_t)acc, 0);
-    if (uv) uv->assign((size_t)acc * 6, 0.f);
+    if (rec) rec->assign((size_t)acc * 8, 0.f);
+    if (tr) {
+        tr->assign((size_t)nt * 4, 0.f);
+        for (int64_t t = 0; t < nt; ++t)
+            for (int k = 0; k < 3; ++k) (*tr)[4 * (size_t)t + k] = (float)v[3 * tri[3 * t + k] + S.ax[0]];
+    }
     std::vector<int32_t> cursor(start.begin(), start.end() - 1);
     for (int64_t t = 0; t < nt; ++t)
         for (int b1 = lo1[t]; b1 <= hi1[t]; ++b1)
             for (int b0 = lo0[t]; b0 <= hi0[t]; ++b0) {
                 const int32_t slot = cursor[b0 + (size_t)nb0 * b1]++;
                 tris[slot] = (int32_t)t;
-                if (uv)
+                if (rec) {
+                    float* o = rec->data() + 8 * (size_t)slot;
                     for (int k = 0; k < 3; ++k) {
-                        (*uv)[6 * (size_t)slot + 2 * k] = (float)v[3 * tri[3 * t + k] + S.ax[1]];
-                        (*uv)[6 * (size_t)slot + 2 * k + 1] = (float)v[3 * tri[3 * t + k] + S.ax[2]];
+                        o[2 * k] = (float)v[3 * tri[3 * t + k] + S.ax[1]];
+                        o[2 * k + 1] = (float)v[3 * tri[3 * t + k] + S.ax[2]];
                     }
+                    const int32_t id = (int32_t)t;
+                    std::memcpy(o + 6, &id, sizeof id);  // the triangle id, as its int bits
+                }
             }
     return acc;
 }
