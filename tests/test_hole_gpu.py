@@ -113,3 +113,59 @@ def test_hole_cut_drives_the_donor_search(torch_cuda):
         part = {kk: (v[..., sample[k]] if kk == "q" else v[sample[k]]) for kk, v in part.items()}
         total += compare(part, od, oq, sc, frames, s.receiver, ovs.OVS_F32, label=f"hole-cut set {k}")
     assert total > 50_000
+
+
+def cube_surface(k):
+    """The unit cube's surface, each face split into k x k squares and each square into two triangles along a
+    diagonal (vertex coordinates multiples of 1/k: shared edges have identical coordinates)."""
+    V, T = [], []
+    for a in range(3):
+        u, w = (a + 1) % 3, (a + 2) % 3
+        for side in (0.0, 1.0):
+            base = len(V)
+            for j in range(k + 1):
+                for i in range(k + 1):
+                    p = [0.0, 0.0, 0.0]
+                    p[a], p[u], p[w] = side, i / k, j / k
+                    V.append(p)
+            vid = lambda i, j: base + i + (k + 1) * j
+            for j in range(k):
+                for i in range(k):
+                    T += [(vid(i, j), vid(i + 1, j), vid(i + 1, j + 1)), (vid(i, j), vid(i + 1, j + 1), vid(i, j + 1))]
+    return np.array(V), np.array(T, np.int32)
+
+
+def test_hole_cut_cube_ties_bit_exact(torch_cuda):
+    """Points exactly on the cube's faces, edges, vertices and face diagonals (a lattice of spacing 1/16), and
+    points at dyadic distances 2^-40 .. 2^-10 off the faces or exactly on them: every coordinate is exact in FP32
+    pairs and the motion is the identity, so the GPU's FP64 tie rules see the oracle's points and its mask must
+    equal the oracle's everywhere; most of these points sit where the FP32 decisions must defer to FP64."""
+    t = torch_cuda
+    V, T = cube_surface(4)
+    lat = gen.cartesian_grid("lattice", (25, 25, 25), (-0.25, -0.25, -0.25), (1.25, 1.25, 1.25), role=0)
+    rng = np.random.default_rng(8)
+    m = 4 * 6000
+    P = np.empty((m, 3))
+    a = rng.integers(0, 3, m)
+    side = rng.integers(0, 2, m).astype(np.float64)
+    off = np.ldexp(rng.choice([-1.0, 1.0], m), -rng.integers(10, 41, m))
+    off[rng.random(m) < 0.1] = 0.0
+    for r in range(m):
+        q = rng.integers(-(1 << 18), (1 << 20) + (1 << 18), 3) / float(1 << 20)
+        q[a[r]] = side[r] + off[r]
+        P[r] = q
+    near = gen.Grid("near", (m // 4, 2, 2), (False, False, False), P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy(), 0)
+    body = gen.cartesian_grid("body", (3, 3, 3), (0.2, 0.2, 0.2), (0.8, 0.8, 0.8), role=1)
+    ctx = ovs.Context(max_points=1024)
+    ids = [ctx.add_grid(g.x, g.y, g.z, g.dims, g.periodic, g.role) for g in (lat, near, body)]
+    for gid in ids:
+        ctx.set_motion(gid, np.eye(3), np.zeros(3), np.zeros(3), np.zeros(3))
+    sid = ctx.add_surface(ids[2], V, T)
+    for g, gid in zip((lat, near), ids):
+        iblank = t.ones(g.n_nodes, dtype=t.uint8, device=ctx.device)
+        ctx.hole_cut(sid, gid, iblank)
+        ctx.sync()
+        want = 1 - oracle.surface_inside(V, T, g.xyz())
+        got = iblank.cpu().numpy()
+        assert np.array_equal(got, want), (g.name, np.nonzero(got != want)[0][:10])
+    assert (1 - want).sum() > m // 10 and want.sum() > m // 2
