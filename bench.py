@@ -356,17 +356,35 @@ def run_ovs(args, rank, world, local):
         iblank = torch.ones(bg0.n_nodes, dtype=torch.uint8, device=dev)
         for gid, mo in zip(gids, mW):
             ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
-        ev_h = events(2)
+        sids, cand_list = [c[0] for c in cuts], [c[1] for c in cuts]
+
+        def cut_all(batched):
+            iblank.fill_(1)
+            if batched:
+                ctx.hole_cut_many(sids, gids[0], iblank, cand_list)
+            else:
+                for sid, cand in cuts:
+                    ctx.hole_cut(sid, gids[0], iblank, nodes=cand)
+
+        ev_h = events(4)
         reps = 10
+        for batched in (True, False):
+            cut_all(batched)  # warm-up
         ev_h[0].record(stream)
         for r in range(reps):
-            iblank.fill_(1)
-            for sid, cand in cuts:
-                ctx.hole_cut(sid, gids[0], iblank, nodes=cand)
+            cut_all(True)
         ev_h[1].record(stream)
+        blanked = int((iblank == 0).sum().item())
+        ev_h[2].record(stream)
+        for r in range(reps):
+            cut_all(False)
+        ev_h[3].record(stream)
         torch.cuda.synchronize()
+        assert int((iblank == 0).sum().item()) == blanked
         holes = {"bodies": len(bodies), "candidate_nodes": int(sum(int(c.numel()) for _, c in cuts)),
-                 "blanked": int((iblank == 0).sum().item()), "ms_per_step": ev_h[0].elapsed_time(ev_h[1]) / reps}
+                 "blanked": blanked, "ms_per_step": ev_h[0].elapsed_time(ev_h[1]) / reps,
+                 "ms_per_step_one_call_per_body": ev_h[2].elapsed_time(ev_h[3]) / reps,
+                 "note": "one ovs_hole_cut_many launch for all bodies (mask fill included)"}
         ovs.ovs_set_iblank(ctx.ctx, gids[0], None)
     learned = None if args.no_learned else learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush,
                                                             K, W, ovs, torch)

@@ -190,7 +190,7 @@ int ovs_set_motion(ovs_ctx* ctx, int32_t grid_id, const double R[9], const doubl
  * v: host FP64 [nv x 3] vertex coordinates (row-major, body frame); tri: host int32 [nt x 3] vertex ids; the
  * surface must be closed (every edge shared by two triangles) for "inside" to be meaningful.
  * ovs_surface_workspace_size: bytes of the device workspace the surface needs (its vertices, triangles and a
- * grid of bins over its projection on the body frame's y-z plane). */
+ * grid of bins over its projection along its shortest box axis). */
 int ovs_surface_workspace_size(int64_t nv, const double* v, int64_t nt, const int32_t* tri, size_t* bytes);
 /* Copies the surface into the caller's workspace dws (256-byte aligned, at least the size above; borrowed until
  * ovs_ctx_destroy) and returns its id (0, 1, ... in creation order, at most OVS_MAX_GRIDS).  Synchronises the
@@ -203,9 +203,18 @@ int ovs_create_surface(ovs_ctx* ctx, int32_t body_grid, int64_t nv, const double
  * the same mask in turn).  Inside = an odd number of crossings of a ray along the surface's shortest box axis r
  * of the body frame (the first on a tie; u, w = the next axes cyclically): the point's (u, w) in a triangle's
  * projection, with a point on a projected edge owned by the one triangle whose counter-clockwise edge runs
- * toward -w (or level toward -u), and the crossing strictly ahead along r; FP64, one rounding per operation.  Enqueued on the context stream; bad node ids are reported by ovs_sync. */
+ * toward -w (or level toward -u), and the crossing strictly ahead along r; FP64, one rounding per operation
+ * (the node carried to the body frame in FP32 pairs, about 1e-14 relative; FP32 decides wherever its error
+ * bound proves the FP64 answer).  Enqueued on the context stream; bad node ids are reported by ovs_sync.
+ * Errors: OVS_ERR_ARG (unknown surface or grid, n < 0, n above the node count with nodes NULL, iblank NULL). */
 int ovs_hole_cut(ovs_ctx* ctx, int32_t surface_id, int32_t target_grid, int64_t n, const int32_t* nodes,
                  uint8_t* iblank);
+/* Several surfaces cutting one target grid in one launch, the same result as ovs_hole_cut for each in turn:
+ * surface_ids, n: host arrays [nsurf] (0 <= nsurf <= OVS_MAX_GRIDS); nodes: host array [nsurf] of device int32
+ * node-id arrays (an entry NULL, or nodes NULL: nodes 0 .. n[s]-1).  The candidates of all surfaces are spread
+ * over the whole GPU together, which balances surfaces whose inside points cluster.  Errors as ovs_hole_cut. */
+int ovs_hole_cut_many(ovs_ctx* ctx, int32_t nsurf, const int32_t* surface_ids, int32_t target_grid,
+                      const int64_t* n, const int32_t* const* nodes, uint8_t* iblank);
 
 /* Blanked nodes of a grid (Sec. 2.4: blanked donors are rejected).  iblank: device uint8 [its node count], 0 =
  * blanked (a hole point: never a donor node), nonzero = active; NULL: every node active (the state after

@@ -595,20 +595,38 @@ int ovs_create_surface(ovs_ctx* c, int32_t body_grid, int64_t nv, const double* 
     return OVS_OK;
 }
 
-int ovs_hole_cut(ovs_ctx* c, int32_t surface_id, int32_t target_grid, int64_t n, const int32_t* nodes,
-                 uint8_t* iblank) {
+int ovs_hole_cut_many(ovs_ctx* c, int32_t nsurf, const int32_t* surface_ids, int32_t target_grid, const int64_t* n,
+                      const int32_t* const* nodes, uint8_t* iblank) {
     if (!c) return OVS_ERR_ARG;
-    if (surface_id < 0 || surface_id >= c->nsurf) return fail(c, OVS_ERR_ARG, "surface %d does not exist", surface_id);
+    if (nsurf < 0 || nsurf > OVS_MAX_GRIDS) return fail(c, OVS_ERR_ARG, "nsurf = %d (0 .. %d)", nsurf, OVS_MAX_GRIDS);
+    if (nsurf == 0) return OVS_OK;
+    if (!surface_ids || !n) return fail(c, OVS_ERR_ARG, "surface_ids or n is NULL");
     if (target_grid < 0 || target_grid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", target_grid);
-    if (n < 0) return fail(c, OVS_ERR_ARG, "n = %lld", (long long)n);
-    if (n == 0) return OVS_OK;
+    HoleJob jobs[OVS_MAX_GRIDS];
+    int64_t total = 0;
+    for (int32_t s = 0; s < nsurf; ++s) {
+        const int32_t id = surface_ids[s];
+        if (id < 0 || id >= c->nsurf) return fail(c, OVS_ERR_ARG, "surface %d does not exist", id);
+        if (n[s] < 0) return fail(c, OVS_ERR_ARG, "n[%d] = %lld", s, (long long)n[s]);
+        const int32_t* nd = nodes ? nodes[s] : nullptr;
+        if (!nd && n[s] > c->grids[target_grid].nnodes)
+            return fail(c, OVS_ERR_ARG, "n[%d] exceeds the grid's node count", s);
+        jobs[s] = {&c->surf[id], &c->motion[c->surf_body[id]], nd, n[s]};
+        total += n[s];
+    }
+    if (total == 0) return OVS_OK;
     if (!iblank) return fail(c, OVS_ERR_ARG, "iblank is NULL");
-    if (!nodes && n > c->grids[target_grid].nnodes) return fail(c, OVS_ERR_ARG, "n exceeds the grid's node count");
     OVS_CUDA(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_hole_cut(c->surf[surface_id], c->grids[target_grid], c->motion[target_grid],
-                                    c->motion[c->surf_body[surface_id]], nodes, n, iblank, c->d_err, c->nsm, c->stream);
+    cudaError_t e = launch_hole_cut(jobs, nsurf, c->grids[target_grid], c->motion[target_grid], iblank, c->d_err,
+                                    c->nsm, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "hole_cut launch");
     return OVS_OK;
+}
+
+int ovs_hole_cut(ovs_ctx* c, int32_t surface_id, int32_t target_grid, int64_t n, const int32_t* nodes,
+                 uint8_t* iblank) {
+    const int32_t* nl[1] = {nodes};
+    return ovs_hole_cut_many(c, 1, &surface_id, target_grid, &n, nl, iblank);
 }
 
 int ovs_set_iblank(ovs_ctx* c, int32_t grid_id, const uint8_t* iblank) {

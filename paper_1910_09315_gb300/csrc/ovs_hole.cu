@@ -47,6 +47,7 @@ __device__ __forceinline__ int ray_crosses(const double* A, const double* B, con
 struct HoleXf {
     XfFF X;
     float M[9], t[3], lo[3], hi[3];
+    float blo[3], bhi[3];  // the surface's box widened by kBinMargin * mag, in FP32 (the pair-precision test)
     __device__ __forceinline__ float3 apply(float x, float y, float z) const {
         return make_float3(fmaf(M[0], x, fmaf(M[1], y, fmaf(M[2], z, t[0]))),
                            fmaf(M[3], x, fmaf(M[4], y, fmaf(M[5], z, t[1]))),
@@ -119,24 +120,48 @@ __device__ __forceinline__ int64_t bin_of_point(const SurfaceDev& S, float qy, f
     return by + (int64_t)S.nb[0] * bz;
 }
 
+// What the registration loop reads of a surface, held in registers for the loop (the surface itself sits in the
+// kernel's parameters, picked by a runtime index).
+struct SurfHot {
+    const float4* __restrict__ rec;
+    const float4* __restrict__ tri_r;
+    const int32_t* __restrict__ tri;
+    const double* __restrict__ v;
+    float mag;
+    int ar, au, aw;
+};
+
 // The point (pr along the ray; pu, pw in the plane; FP32 pairs) against registration e: the FP32 decision, else
 // the FP64 test at the point hi + lo.
-__device__ __forceinline__ int crosses(const SurfaceDev& S, int32_t e, ff pr, ff pu, ff pw) {
-    const float4 g0 = __ldg(S.bin_rec + 2 * (int64_t)e), g1 = __ldg(S.bin_rec + 2 * (int64_t)e + 1);
-    const int sc = screen(g0, g1, S.tri_r, pu.hi, pw.hi, pr.hi, S.mag);
+__device__ __forceinline__ int crosses(const SurfHot& H, int32_t e, ff pr, ff pu, ff pw) {
+    const float4 g0 = __ldg(H.rec + 2 * (int64_t)e), g1 = __ldg(H.rec + 2 * (int64_t)e + 1);
+    const int sc = screen(g0, g1, H.tri_r, pu.hi, pw.hi, pr.hi, H.mag);
     if (sc != kUnsure) return sc;
-    const int ar = S.ax[0], au = S.ax[1], aw = S.ax[2];
     const int32_t t = __float_as_int(g1.z);
-    const int32_t i0 = __ldg(S.tri + 3 * t), i1 = __ldg(S.tri + 3 * t + 1), i2 = __ldg(S.tri + 3 * t + 2);
-    const double A[3] = {__ldg(S.v + 3 * i0 + ar), __ldg(S.v + 3 * i0 + au), __ldg(S.v + 3 * i0 + aw)};
-    const double B[3] = {__ldg(S.v + 3 * i1 + ar), __ldg(S.v + 3 * i1 + au), __ldg(S.v + 3 * i1 + aw)};
-    const double C[3] = {__ldg(S.v + 3 * i2 + ar), __ldg(S.v + 3 * i2 + au), __ldg(S.v + 3 * i2 + aw)};
+    const int32_t i0 = __ldg(H.tri + 3 * t), i1 = __ldg(H.tri + 3 * t + 1), i2 = __ldg(H.tri + 3 * t + 2);
+    const double A[3] = {__ldg(H.v + 3 * i0 + H.ar), __ldg(H.v + 3 * i0 + H.au), __ldg(H.v + 3 * i0 + H.aw)};
+    const double B[3] = {__ldg(H.v + 3 * i1 + H.ar), __ldg(H.v + 3 * i1 + H.au), __ldg(H.v + 3 * i1 + H.aw)};
+    const double C[3] = {__ldg(H.v + 3 * i2 + H.ar), __ldg(H.v + 3 * i2 + H.au), __ldg(H.v + 3 * i2 + H.aw)};
     return ray_crosses(A, B, C, (double)pr.hi + (double)pr.lo, (double)pu.hi + (double)pu.lo,
                        (double)pw.hi + (double)pw.lo);
 }
 
 constexpr int kHoleThreads = 256;
 constexpr int kHeavyBin = 32;  // a point whose bin holds more registrations is tested by its whole warp
+
+// Several surfaces cutting one target grid in one launch: surface s's candidates fill groups of 32 lanes
+// group_begin[s] .. group_begin[s + 1] (its last group ragged), and the groups are dealt to the warps round-robin,
+// so that every warp gets a share of every surface's (spatially clustered) heavy points.
+struct HoleBatch {
+    int32_t nsurf;
+    int32_t pad;
+    int64_t group_begin[OVS_MAX_GRIDS + 1];
+    int64_t n[OVS_MAX_GRIDS];
+    const int32_t* nodes[OVS_MAX_GRIDS];
+    SurfaceDev S[OVS_MAX_GRIDS];
+    HoleXf F[OVS_MAX_GRIDS];
+};
+static_assert(sizeof(HoleBatch) + sizeof(GridDev) + 16 <= 32764, "kernel parameters exceed the 32764-byte limit");
 
 // One lane per candidate node: the node's position in the body frame as FP32 pairs p (about 1e-14 relative),
 // then its bin's registrations, each decided in FP32 and, where that is unsure, tested in FP64 at the point
@@ -145,39 +170,45 @@ constexpr int kHeavyBin = 32;  // a point whose bin holds more registrations is 
 // surface's box is outside the body.  FP64 (slow on this GPU) runs only in those unsure tests.  A point in a bin
 // with more than kHeavyBin registrations (near a pole, where many triangles meet) is tested by all 32 lanes of its
 // warp, a registration per lane, the parity a ballot's popcount: such bins would otherwise set the kernel's tail.
-// The candidate loop is warp-uniform (the stride is a multiple of 32) so that every lane reaches the ballots.
-__global__ void __launch_bounds__(kHoleThreads) k_hole_cut(SurfaceDev S, HoleXf F, GridDev tg,
-                                                           const int32_t* __restrict__ nodes, int64_t n,
+// Every lane of a warp works on the same group, so that all of them reach the ballots.
+__global__ void __launch_bounds__(kHoleThreads) k_hole_cut(const __grid_constant__ HoleBatch P, GridDev tg,
                                                            uint8_t* __restrict__ iblank, int32_t* __restrict__ err) {
-    const int ar = S.ax[0], au = S.ax[1], aw = S.ax[2];
-    const float m = (float)kBinMargin * S.mag;
     const int lane = threadIdx.x & 31;
     const int64_t nn = tg.nnodes;
-    for (int64_t base = blockIdx.x * (int64_t)kHoleThreads + (threadIdx.x & ~31); base < n;
-         base += (int64_t)gridDim.x * kHoleThreads) {
-        const int64_t q = base + lane;
+    const int64_t groups = P.group_begin[P.nsurf];
+    const int64_t warps = (int64_t)gridDim.x * (kHoleThreads / 32);
+    int si = 0;  // the surface of group gi (gi only grows: the search moves forward)
+    for (int64_t gi = (blockIdx.x * (int64_t)kHoleThreads + threadIdx.x) >> 5; gi < groups; gi += warps) {
+        while (si + 1 < P.nsurf && P.group_begin[si + 1] <= gi) ++si;  // warp-uniform
+        const SurfaceDev& S = P.S[si];
+        const HoleXf& F = P.F[si];
+        const int ar = S.ax[0], au = S.ax[1], aw = S.ax[2];
+        const int64_t q = (gi - P.group_begin[si]) * 32 + lane;
+        const int32_t* __restrict__ nodes = P.nodes[si];
         int64_t node = -1;
         bool work = false;
         ff pr = {0.f, 0.f}, pu = {0.f, 0.f}, pw = {0.f, 0.f};
         int32_t e0 = 0, e1 = 0;
-        if (q < n) {
+        if (q < P.n[si]) {
             node = nodes ? (int64_t)__ldg(nodes + q) : q;
             if (node < 0 || node >= nn) {
                 atomicOr(err, kErrBadNode);
             } else {
-                const ff x[3] = {{__ldg(tg.xff + node), __ldg(tg.xff + nn + node)},
-                                 {__ldg(tg.xff + 2 * nn + node), __ldg(tg.xff + 3 * nn + node)},
-                                 {__ldg(tg.xff + 4 * nn + node), __ldg(tg.xff + 5 * nn + node)}};
-                // first rejection: further than the FP32 error bound outside the surface's box
-                const float3 pf = F.apply(x[0].hi, x[1].hi, x[2].hi);
+                // first rejection from the coordinates' high parts alone (most candidates end here): further
+                // than the FP32 error bound outside the surface's box
+                const float xh = __ldg(tg.xff + node), yh = __ldg(tg.xff + 2 * nn + node),
+                            zh = __ldg(tg.xff + 4 * nn + node);
+                const float3 pf = F.apply(xh, yh, zh);
                 work = !(pf.x < F.lo[0] || pf.x > F.hi[0] || pf.y < F.lo[1] || pf.y > F.hi[1] || pf.z < F.lo[2] ||
                          pf.z > F.hi[2]);
                 if (work) {
+                    const ff x[3] = {{xh, __ldg(tg.xff + nn + node)},
+                                     {yh, __ldg(tg.xff + 3 * nn + node)},
+                                     {zh, __ldg(tg.xff + 5 * nn + node)}};
                     ff pb[3];
                     xf_apply(F.X, x, pb);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        work = work && !(pb[c].hi < (float)S.bmin[c] - m || pb[c].hi > (float)S.bmax[c] + m);
+                    for (int c = 0; c < 3; ++c) work = work && !(pb[c].hi < F.blo[c] || pb[c].hi > F.bhi[c]);
                     auto pick = [&pb](int c) { return c == 0 ? pb[0] : (c == 1 ? pb[1] : pb[2]); };  // registers
                     pr = pick(ar);
                     pu = pick(au);
@@ -192,9 +223,11 @@ __global__ void __launch_bounds__(kHoleThreads) k_hole_cut(SurfaceDev S, HoleXf 
         }
         const bool heavy = work && e1 - e0 > kHeavyBin;
         int odd = 0;
+        if (!__any_sync(0xffffffffu, work)) continue;  // (warp-uniform)
+        const SurfHot H = {S.bin_rec, S.tri_r, S.tri, S.v, S.mag, ar, au, aw};
         if (work && !heavy) {
 #pragma unroll 4
-            for (int32_t e = e0; e < e1; ++e) odd ^= crosses(S, e, pr, pu, pw);
+            for (int32_t e = e0; e < e1; ++e) odd ^= crosses(H, e, pr, pu, pw);
         }
         // the heavy points of this warp, one after another, each over all lanes
         for (unsigned hm = __ballot_sync(0xffffffffu, heavy); hm; hm &= hm - 1) {
@@ -204,7 +237,7 @@ __global__ void __launch_bounds__(kHoleThreads) k_hole_cut(SurfaceDev S, HoleXf 
             const ff hu = {__shfl_sync(0xffffffffu, pu.hi, l), __shfl_sync(0xffffffffu, pu.lo, l)};
             const ff hw = {__shfl_sync(0xffffffffu, pw.hi, l), __shfl_sync(0xffffffffu, pw.lo, l)};
             int par = 0;
-            for (int32_t e = h0 + lane; e < h1; e += 32) par ^= crosses(S, e, hr, hu, hw);
+            for (int32_t e = h0 + lane; e < h1; e += 32) par ^= crosses(H, e, hr, hu, hw);
             const unsigned bits = __ballot_sync(0xffffffffu, par != 0);
             if (lane == l) odd = __popc(bits) & 1;
         }
@@ -214,11 +247,12 @@ __global__ void __launch_bounds__(kHoleThreads) k_hole_cut(SurfaceDev S, HoleXf 
 
 }  // namespace
 
-cudaError_t launch_hole_cut(const SurfaceDev& S, const GridDev& target, const MotionDev& mt, const MotionDev& mb,
-                            const int32_t* nodes, int64_t n, uint8_t* iblank, int32_t* err, int nsm, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    // the map composed in FP64 on the host: M = R_b^T R_t, t = R_b^T (c_t - c_b); first-rejection margin: 1e-4 of
-    // the largest of the box's extent and the transformed magnitudes (far above the FP32 rounding of 3 products)
+namespace {
+
+// the body-frame map of one surface at the current motions: M = R_b^T R_t, t = R_b^T (c_t - c_b) composed in FP64;
+// first-rejection box: the surface box widened by 1e-4 of the largest of its extent and the transformed
+// magnitudes (far above the FP32 rounding of 3 products)
+HoleXf hole_map(const SurfaceDev& S, const GridDev& target, const MotionDev& mt, const MotionDev& mb) {
     HoleXf F;
     memset(&F, 0, sizeof F);
     F.X.identity = mt.identity && mb.identity;
@@ -250,10 +284,41 @@ cudaError_t launch_hole_cut(const SurfaceDev& S, const GridDev& target, const Mo
     for (int c = 0; c < 3; ++c) {
         F.lo[c] = (float)(S.bmin[c] - margin);
         F.hi[c] = (float)(S.bmax[c] + margin);
+        F.blo[c] = (float)(S.bmin[c] - kBinMargin * S.mag);
+        F.bhi[c] = (float)(S.bmax[c] + kBinMargin * S.mag);
     }
-    const int64_t want = (n + kHoleThreads - 1) / kHoleThreads;
-    const unsigned blocks = (unsigned)std::min<int64_t>(want, (int64_t)nsm * 8);
-    k_hole_cut<<<blocks, kHoleThreads, 0, st>>>(S, F, target, nodes, n, iblank, err);
+    return F;
+}
+
+}  // namespace
+
+cudaError_t launch_hole_cut(const HoleJob* jobs, int njobs, const GridDev& target, const MotionDev& mt,
+                            uint8_t* iblank, int32_t* err, int nsm, cudaStream_t st) {
+    if (njobs > OVS_MAX_GRIDS) return cudaErrorInvalidValue;
+    HoleBatch P;
+    memset(&P, 0, sizeof P);
+    int64_t g = 0;
+    for (int j = 0; j < njobs; ++j) {
+        if (jobs[j].n <= 0) continue;
+        const int k = P.nsurf++;
+        P.group_begin[k] = g;
+        g += (jobs[j].n + 31) / 32;
+        P.n[k] = jobs[j].n;
+        P.nodes[k] = jobs[j].nodes;
+        P.S[k] = *jobs[j].S;
+        P.F[k] = hole_map(*jobs[j].S, target, mt, *jobs[j].mb);
+    }
+    P.group_begin[P.nsurf] = g;
+    if (g == 0) return cudaSuccess;
+    // one resident wave; the groups are dealt round-robin to its warps
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hole_cut, kHoleThreads, 0);
+        if (e != cudaSuccess || occ < 1) occ = 1;
+    }
+    const int64_t want = (g + kHoleThreads / 32 - 1) / (kHoleThreads / 32);
+    const unsigned blocks = (unsigned)std::min<int64_t>(want, (int64_t)nsm * occ);
+    k_hole_cut<<<blocks, kHoleThreads, 0, st>>>(P, target, iblank, err);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,16 @@ struct SurfaceDev {
 int64_t surface_bins(const double* v, int64_t nv, const int32_t* tri, int64_t nt, SurfaceDev& S,
                      std::vector<int32_t>& start, std::vector<int32_t>& tris, std::vector<float>* rec = nullptr,
                      std::vector<float>* tr = nullptr);
-cudaError_t launch_hole_cut(const SurfaceDev& S, const GridDev& target, const MotionDev& mt, const MotionDev& mb,
-                            const int32_t* nodes, int64_t n, uint8_t* iblank, int32_t* err, int nsm, cudaStream_t st);
+// one surface's share of a hole-cutting launch: the surface, its body grid's motion, its candidate nodes (device,
+// NULL: nodes 0 .. n-1 of the target grid)
+struct HoleJob {
+    const SurfaceDev* S;
+    const MotionDev* mb;
+    const int32_t* nodes;
+    int64_t n;
+};
+// at most OVS_MAX_GRIDS jobs, all cutting the target grid (motion mt) in one launch
+cudaError_t launch_hole_cut(const HoleJob* jobs, int njobs, const GridDev& target, const MotionDev& mt,
+                            uint8_t* iblank, int32_t* err, int nsm, cudaStream_t st);
 
 }  // namespace ovs

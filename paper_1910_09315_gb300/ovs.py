@@ -55,6 +55,7 @@ EXPORTS = [
     "ovs_guess_eval", "ovs_mlp_loss_grad", "ovs_set_tuning", "ovs_get_tuning", "ovs_autotune",
     "ovs_interp_matrix", "ovs_spmv", "ovs_set_iblank", "ovs_surface_workspace_size", "ovs_create_surface",
     "ovs_hole_cut",
+    "ovs_hole_cut_many",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -161,6 +162,7 @@ def load(path: Optional[str] = None):
         "ovs_surface_workspace_size": [I64, V, I64, V, ctypes.POINTER(SZ)],
         "ovs_create_surface": [V, I32, I64, V, I64, V, V, SZ, ctypes.POINTER(I32)],
         "ovs_hole_cut": [V, I32, I32, I64, V, V],
+        "ovs_hole_cut_many": [V, I32, V, I32, V, V, V],
         "ovs_spmv": [V, I64, V, V, V, V, V, I32],
         "ovs_set_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
@@ -283,6 +285,15 @@ def ovs_create_surface(ctx, body_grid: int, V, T, dws: int, nbytes: int) -> int:
 
 def ovs_hole_cut(ctx, surface_id: int, target_grid: int, n: int, nodes: int, iblank: int):
     _check(ctx, load().ovs_hole_cut(ctx, int(surface_id), int(target_grid), int(n), nodes or None, iblank))
+
+
+def ovs_hole_cut_many(ctx, surface_ids, target_grid: int, ns, nodes, iblank: int):
+    """surface_ids, ns: sequences of ints; nodes: sequence of device pointers (int, or None for 0 .. n-1)."""
+    k = len(surface_ids)
+    ids = (ctypes.c_int32 * max(1, k))(*[int(x) for x in surface_ids])
+    nn = (ctypes.c_int64 * max(1, k))(*[int(x) for x in ns])
+    nd = (ctypes.c_void_p * max(1, k))(*[(p or None) for p in nodes])
+    _check(ctx, load().ovs_hole_cut_many(ctx, k, ids, int(target_grid), nn, nd, iblank))
 
 
 def ovs_interp_matrix(ctx, donors: ovs_donors, row_ptr: int, col: int, val: int, val_dtype: int):
@@ -564,6 +575,13 @@ class Context:
         n = int(nodes.numel()) if nodes is not None else int(iblank.numel())
         ovs_hole_cut(self.ctx, sid, target_gid, n, nodes.data_ptr() if nodes is not None else None,
                      iblank.data_ptr())
+
+    def hole_cut_many(self, sids, target_gid: int, iblank, nodes):
+        """ovs_hole_cut_many: surfaces sids cut iblank in one launch; nodes: one device int32 tensor per surface
+        (or None for all of the target grid's nodes)."""
+        ns = [int(x.numel()) if x is not None else int(iblank.numel()) for x in nodes]
+        ptrs = [x.data_ptr() if x is not None else None for x in nodes]
+        ovs_hole_cut_many(self.ctx, list(sids), target_gid, ns, ptrs, iblank.data_ptr())
 
     def interp_matrix(self, donors, val_dtype: int = OVS_F32):
         """ovs_interp_matrix of a donors dict -> (row_ptr int32 [n+1], col int64 [8n], val [8n]) on the device."""

@@ -1,9 +1,10 @@
 """Hole cutting on the GPU (paper Sec. 2.2.1: background nodes inside a moving body's closed surface are blanked)
 against the oracle's ray parity:
 
-* every fish surface of the 8-fish school cuts the background nodes near it; on a seeded sample the GPU's mask
-  equals the oracle's, except at points whose answer the oracle itself changes under a 1e-12 displacement
-  (on the surface to within rounding: either answer is right there);
+* every fish surface of the 8-fish school cuts the background nodes near it (all in one launch, the same mask as
+  one call per fish); on a seeded sample the GPU's mask equals the oracle's, except at points whose answer the
+  oracle itself changes under a 1e-12 displacement (on the surface to within rounding: either answer is right
+  there);
 * the mask then drives the donor search (blanked donors rejected), which equals the oracle's with that mask.
 """
 import numpy as np
@@ -42,15 +43,20 @@ def test_hole_cut_matches_oracle(torch_cuda):
     iblank = t.ones(bg.n_nodes, dtype=t.uint8, device=dev)
     rng = np.random.default_rng(11)
     checked, ambiguous, cut = 0, 0, 0
-    surfaces = []
+    surfaces, sids, cands = [], [], []
     for q in range(1, len(sc.grids)):
         V, T = gen.body_surface(sc.grids[q])
-        sid = scene.ctx.add_surface(scene.ids[q], V, T)
+        sids.append(scene.ctx.add_surface(scene.ids[q], V, T))
         surfaces.append((q, V, T))
-        cand = near_body_nodes(bg, m[q])
-        scene.ctx.hole_cut(sid, scene.ids[0], iblank, nodes=t.as_tensor(cand.astype(np.int32)).to(dev))
+        cands.append(t.as_tensor(near_body_nodes(bg, m[q]).astype(np.int32)).to(dev))
+    # all bodies in one launch, and one call per body: the same mask
+    scene.ctx.hole_cut_many(sids, scene.ids[0], iblank, cands)
+    one_by_one = t.ones_like(iblank)
+    for sid, cand in zip(sids, cands):
+        scene.ctx.hole_cut(sid, scene.ids[0], one_by_one, nodes=cand)
     scene.ctx.sync()
     mask = iblank.cpu().numpy()
+    assert np.array_equal(mask, one_by_one.cpu().numpy())
     # one seeded sample of background nodes, each tested against every surface whose box holds it
     keep = rng.random(bg.n_nodes) < 0.15
     inside_any = np.zeros(bg.n_nodes, dtype=bool)
