@@ -214,6 +214,8 @@ def run_ovs(args, rank, world, local):
         return {"grid": donors["grid"][:n], "cell": donors["cell"][:n], "xi": donors["xi"][:3 * n],
                 "status": donors["status"][:n], "xi_dtype": xi_dtype, "n": n}
 
+    layout = [fields]  # the donor fields one_step passes: four arrays per grid (the headline), or records
+
     def one_step(s, sets, fused=True):
         m, fs = inputs[s]
         for gid, mo in zip(gids, m):
@@ -221,10 +223,10 @@ def run_ovs(args, rank, world, local):
         n = sum(int(x[1].numel()) for x in sets)
         d = donors_view(n)
         if fused:
-            ctx.assemble_interpolate(sets, fields, donors=d, out=[o[:n] for o in outs])
+            ctx.assemble_interpolate(sets, layout[0], donors=d, out=[o[:n] for o in outs])
         else:
             ctx.assemble(sets, donors=d)
-            ctx.interpolate(sets, d, fields, out=[o[:n] for o in outs])
+            ctx.interpolate(sets, d, layout[0], out=[o[:n] for o in outs])
         return n
 
     # warm-up (hints become warm exactly as in a time loop)
@@ -285,6 +287,16 @@ def run_ovs(args, rank, world, local):
     for s in range(W):
         one_step(s, dev_sets[s], fused=False)
     _, sep_ms, _, _, _ = timed(False, trace=False)
+    # the same steps with each grid's fields as one array of (u, v, w, p) records per node (ovs_fields.stride 4):
+    # one 16-byte load per donor corner instead of four
+    layout[0] = [torch.stack(f, 1).contiguous() for f in fields]
+    for s in range(W):
+        one_step(s, dev_sets[s])
+    _, rec_ms, _, _, _ = timed(True, trace=False)
+    _, _, _, _, rec_interp_ms = timed(True, trace=True)
+    layout[0] = fields
+    interleaved = {"ms_per_step": float(np.mean(rec_ms)), "k_interp_ms": float(np.mean(rec_interp_ms)),
+                   "note": "fields as (u, v, w, p) records per node; the headline passes four arrays per grid"}
     # plain, unbatched: one ovs_assemble_interpolate per fringe set (direct launches, default launch shapes), the
     # same steps and start (previous donor, else control cell), for the batching comparison
     def unbatched_step(s):
@@ -457,6 +469,7 @@ def run_ovs(args, rank, world, local):
         "learned_vs_plain": learned,
         "interp_matrix": matrix,
         "hole_cut": holes,
+        "interleaved_fields": interleaved,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, inputs[W], args.cpu_sample)

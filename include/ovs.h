@@ -128,6 +128,10 @@ typedef struct {
     const void* w;
     const void* p;
     int32_t dtype;   /* OVS_F32 or OVS_F64 */
+    int32_t stride;  /* elements from one node's value to the next node's, the same for u, v, w and p: 0 or 1 =
+                        four contiguous arrays; 4 with v = u + 1, w = u + 2, p = u + 3 and u 16-byte aligned =
+                        one array of (u, v, w, p) records per node (the layout of a 4-dof structured-grid vector),
+                        read one record per corner; any other value >= 1: strided arrays.  Negative: OVS_ERR_ARG */
 } ovs_fields;
 
 typedef struct {

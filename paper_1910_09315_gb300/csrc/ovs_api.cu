@@ -680,6 +680,7 @@ int check_fields(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
             if (f.dtype != out->dtype)
                 return fail(c, OVS_ERR_ARG, "donor grid %d fields dtype %d != output dtype %d", sets[s].donors[d],
                             f.dtype, out->dtype);
+            if (f.stride < 0) return fail(c, OVS_ERR_ARG, "donor grid %d fields stride %d", sets[s].donors[d], f.stride);
         }
     return OVS_OK;
 }
@@ -705,10 +706,17 @@ void fill_interp(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
     memcpy(P->m, c->motion, sizeof P->m);
     fill_motion_f32(c, P->mf);
     for (int g = 0; g < c->ngrids; ++g) {
-        P->fields[g].f[0] = fields[g].u;
-        P->fields[g].f[1] = fields[g].v;
-        P->fields[g].f[2] = fields[g].w;
-        P->fields[g].f[3] = fields[g].p;
+        FieldsDev& F = P->fields[g];
+        F.f[0] = fields[g].u;
+        F.f[1] = fields[g].v;
+        F.f[2] = fields[g].w;
+        F.f[3] = fields[g].p;
+        F.stride = fields[g].stride > 1 ? fields[g].stride : 1;
+        const size_t es = fields[g].dtype == OVS_F64 ? 8 : 4;
+        const char* u = (const char*)fields[g].u;
+        F.rec4 = F.stride == 4 && u && (uintptr_t)u % 16 == 0 && (const char*)fields[g].v == u + es &&
+                 (const char*)fields[g].w == u + 2 * es && (const char*)fields[g].p == u + 3 * es;
+        F.pad = 0;
     }
 }
 

@@ -34,15 +34,41 @@ template <typename T>
 __device__ __forceinline__ void gather8(const GridDev& g, const FieldsDev& F, int64_t cell, T u, T v, T w, T q[4]) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
-    const T* f[4] = {(const T*)F.f[0], (const T*)F.f[1], (const T*)F.f[2], (const T*)F.f[3]};
     q[0] = q[1] = q[2] = q[3] = (T)0;
+    if (F.rec4) {
+        // one (u, v, w, p) record per corner: one 16-byte load (FP32) or two (FP64); the sums as below
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        T wa = ((a & 1) ? u : (T)1 - u) * ((a & 2) ? v : (T)1 - v) * ((a & 4) ? w : (T)1 - w);
-        int64_t nd = corner_node(g, i, j, k, a);
+        for (int a = 0; a < 8; ++a) {
+            T wa = ((a & 1) ? u : (T)1 - u) * ((a & 2) ? v : (T)1 - v) * ((a & 4) ? w : (T)1 - w);
+            const int64_t nd = corner_node(g, i, j, k, a);
+            T r[4];
+            if constexpr (sizeof(T) == 4) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(F.f[0]) + nd);
+                r[0] = x.x, r[1] = x.y, r[2] = x.z, r[3] = x.w;
+            } else {
+                const double2 x0 = __ldg(reinterpret_cast<const double2*>(F.f[0]) + 2 * nd),
+                              x1 = __ldg(reinterpret_cast<const double2*>(F.f[0]) + 2 * nd + 1);
+                r[0] = x0.x, r[1] = x0.y, r[2] = x1.x, r[3] = x1.y;
+            }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) q[c] += wa * __ldg(f[c] + nd);
+            for (int c = 0; c < 4; ++c) q[c] += wa * r[c];
+        }
+        return;
     }
+    const T* f[4] = {(const T*)F.f[0], (const T*)F.f[1], (const T*)F.f[2], (const T*)F.f[3]};
+    auto sum = [&](int64_t st) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            T wa = ((a & 1) ? u : (T)1 - u) * ((a & 2) ? v : (T)1 - v) * ((a & 4) ? w : (T)1 - w);
+            const int64_t nd = corner_node(g, i, j, k, a) * st;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) q[c] += wa * __ldg(f[c] + nd);
+        }
+    };
+    if (F.stride == 1)
+        sum(1);  // four contiguous arrays (the multiply folds away)
+    else
+        sum(F.stride);
 }
 
 // FP32 velocity transform.  The receiver node's position is its FP32 pair (xh + xl) in the receiver frame;

@@ -105,8 +105,13 @@ struct SetDev {
     int64_t n;
 };
 
+// A donor grid's fields: component c of node n at f[c] + n * stride; rec4: one 16-byte-aligned array of
+// (u, v, w, p) records per node (stride 4, f[c] = f[0] + c), read as one record per corner.
 struct FieldsDev {
     const void* f[4];
+    int64_t stride;
+    int32_t rec4;
+    int32_t pad;
 };
 
 struct SlowEntry {

@@ -78,7 +78,7 @@ class ovs_donors(ctypes.Structure):
 
 class ovs_fields(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("p", ctypes.c_void_p),
-                ("dtype", ctypes.c_int32)]
+                ("dtype", ctypes.c_int32), ("stride", ctypes.c_int32)]
 
 
 class ovs_fields_out(ctypes.Structure):
@@ -520,15 +520,25 @@ class Context:
         return out
 
     def _fields_structs(self, fields, n, out):
+        """fields[g]: (u, v, w, p) tensors, or one (nodes, k >= 4) tensor whose rows hold (u, v, w, p, ...) (rows
+        evenly spaced, columns contiguous: the row spacing is the stride)."""
         t = self.torch
         dtype = None
         farr = (ovs_fields * len(self.grids))()
         for g, f in enumerate(fields):
             if f is None:
                 continue
-            farr[g].u, farr[g].v, farr[g].w, farr[g].p = (a.data_ptr() for a in f)
-            farr[g].dtype = OVS_F64 if f[0].dtype == t.float64 else OVS_F32
-            dtype = f[0].dtype
+            if isinstance(f, t.Tensor):
+                assert f.dim() == 2 and f.shape[1] >= 4 and f.stride(1) == 1
+                base, es = f.data_ptr(), f.element_size()
+                farr[g].u, farr[g].v, farr[g].w, farr[g].p = (base + c * es for c in range(4))
+                farr[g].stride = f.stride(0)
+                dt = f.dtype
+            else:
+                farr[g].u, farr[g].v, farr[g].w, farr[g].p = (a.data_ptr() for a in f)
+                dt = f[0].dtype
+            farr[g].dtype = OVS_F64 if dt == t.float64 else OVS_F32
+            dtype = dt
         if out is None:
             out = [t.empty(n, dtype=dtype, device=self.device) for _ in range(4)]
         o = ovs_fields_out()
