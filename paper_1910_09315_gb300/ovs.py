@@ -93,7 +93,8 @@ class ovs_options(ctypes.Structure):
 
 class ovs_tuning(ctypes.Structure):
     _fields_ = [("assemble_blocks_per_sm", ctypes.c_int32), ("interp_blocks_per_sm", ctypes.c_int32),
-                ("slow_blocks_per_sm", ctypes.c_int32), ("guess_blocks_per_sm", ctypes.c_int32)]
+                ("slow_blocks_per_sm", ctypes.c_int32), ("guess_blocks_per_sm", ctypes.c_int32),
+                ("launch", ctypes.c_int32)]
 
 
 class ovs_stats(ctypes.Structure):
