@@ -331,7 +331,8 @@ def run_ovs(args, rank, world, local):
             one_step(s, dev_sets[s])
             ec1[s].record(stream)
         torch.cuda.synchronize()
-        calib[mode] += float(np.sum([a.elapsed_time(b) for a, b in zip(ec0, ec1)]))
+        # (the first step after the reset starts cold in both modes: left out, it would dominate the sums)
+        calib[mode] += float(np.sum([a.elapsed_time(b) for a, b in list(zip(ec0, ec1))[1:]]))
     if world > 1:  # every rank the same mode: rank 0's choice
         pick = torch.tensor([calib[ovs.OVS_LAUNCH_GRAPH] <= calib[ovs.OVS_LAUNCH_DIRECT]], dtype=torch.int32,
                             device=dev)
