@@ -511,10 +511,13 @@ __device__ __forceinline__ bool newton64_contains(const GridDev& g, int64_t cell
 }
 
 // The donor predicate in FP32-pair arithmetic (~44 significant bits) on the node coordinates' FP32 pairs,
-// started at (u,v,w): the same Newton iteration as newton64_contains, with steps <= 1e-12 as convergence.
-// Returns 1 (the cell holds the point), 0 (it does not) or -1 (undecided: not converged, or a local coordinate
-// within 1e-12 of a window bound, where only the FP64 predicate may decide).  Away from that band the FP64
-// definition gives the same answer, because the two iterations agree to far better than 1e-12.
+// started at (u,v,w): the same Newton iteration as newton64_contains, converged when a step is <= 1e-12, or when
+// the steps stop shrinking quadratically below 1e-9 (they have reached the pair arithmetic's rounding noise,
+// which in thin or badly scaled cells lies above 1e-12: the iterate is then accurate to about that step).
+// Returns 1 (the cell holds the point), 0 (it does not) or -1 (undecided: not converged; the noise so large
+// (> 1e-11) that the FP64 definition, 2^8 times less noisy, might itself not reach its 1e-13 tolerance; or a
+// local coordinate within the band of a window bound, where only the FP64 predicate may decide).  Away from
+// that band the FP64 definition gives the same answer, because the two iterations agree to within the band.
 __device__ __forceinline__ int newton_ff(const GridDev& g, int64_t cell, const ff p[3], float u0, float v0, float w0,
                                          double& u, double& v, double& w) {
     int i, j, k;
@@ -545,6 +548,7 @@ __device__ __forceinline__ int newton_ff(const GridDev& g, int64_t cell, const f
     }
     ff U = {u0, 0.f}, V = {v0, 0.f}, W = {w0, 0.f};
     bool conv = false;
+    float m_prev = 3.4e38f, m_noise = 0.f;
 #pragma unroll 1
     for (int it = 0; it < kNewtonMaxIt64; ++it) {
         ff uv = ff_mul(U, V), vw = ff_mul(V, W), uw = ff_mul(U, W), uvw = ff_mul(uv, W);
@@ -585,10 +589,17 @@ __device__ __forceinline__ int newton_ff(const GridDev& g, int64_t cell, const f
             conv = true;
             break;
         }
+        if (m < 1e-9f && m > 0.5f * m_prev) {  // no longer quadratic: at the rounding noise
+            conv = true;
+            m_noise = m;
+            break;
+        }
+        m_prev = m;
     }
-    if (!conv) return -1;
+    if (!conv || m_noise > 1e-11f) return -1;
     // undecided band: 1e-12 plus the FP32-pair error of the point and corners (~4e-14 of the coordinates'
-    // magnitude) measured in local-coordinate units of the cell's shortest edge
+    // magnitude) measured in local-coordinate units of the cell's shortest edge; at least 8 times the last step
+    // when the iteration stopped at its rounding noise
     float pm = fmaxf(fabsf(p[0].hi), fmaxf(fabsf(p[1].hi), fabsf(p[2].hi))) +
                fmaxf(fabsf(X0[0].hi), fmaxf(fabsf(X0[1].hi), fabsf(X0[2].hi)));
     float hmin = 3.4e38f;
@@ -597,7 +608,7 @@ __device__ __forceinline__ int newton_ff(const GridDev& g, int64_t cell, const f
         float n2 = A[q][0].hi * A[q][0].hi + A[q][1].hi * A[q][1].hi + A[q][2].hi * A[q][2].hi;
         hmin = fminf(hmin, sqrtf(n2));
     }
-    const float band = 1e-12f + 4e-14f * pm / hmin;
+    const float band = fmaxf(1e-12f + 4e-14f * pm / hmin, 8.f * m_noise);
     ff q[3] = {U, V, W};
     bool in = true, amb = false;
 #pragma unroll
