@@ -5,8 +5,8 @@
 // a projected edge belonging to the one triangle whose counter-clockwise edge runs downward, or level toward -y)
 // and the crossing lies strictly ahead in x.  Every FP64 operation is one rounding (no fused
 // multiply-add: the _rn intrinsics), so the decision is reproducible.  The triangles are registered in a uniform
-// grid of bins over the surface's projected box; a point tests only its bin's triangles, first with an FP32
-// screen whose error bound is proven below, and in FP64 only where that screen is unsure.
+// grid of bins over the surface's projected box; a point tests only its bin's triangles, each decided in FP32
+// where an error bound (proven below) shows what the FP64 test would answer, and by the FP64 test otherwise.
 #include "ovs_hole.cuh"
 
 #include <cstring>
