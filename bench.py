@@ -701,10 +701,20 @@ def cpu_baseline(sc, step_input, sample_n: int):
     tot = sum(len(s.node_ids) for s in fsets)
     if sample_n <= 0:
         sample_n = min(tot, 400_000)
-    n, dt, _ = oracle_points_per_s(sc, motions, fsets, sample_n, rng)
-    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    n, dt, grids = oracle_points_per_s(sc, motions, fsets, sample_n, rng)
+    cores = oracle.num_threads()
+    # the same oracle on one core, on a smaller sample (about 3 s of work)
+    n1_want = int(max(2_000, min(25_000, 3.0 * n / dt / max(1, cores))))
+    oracle.set_num_threads(1)
+    try:
+        n1, dt1, _ = oracle_points_per_s(sc, motions, fsets, n1_want, rng, grids)
+    finally:
+        oracle.set_num_threads(0)
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} of the {tot} fringe points of one step (seeded random subset), bins built before timing",
-            "seconds": dt}
+            "seconds": dt,
+            "single_core": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} fringe points of the same step (seeded random subset)", "seconds": dt1}}
 
 
 def run_reference(args, rank, world):

@@ -70,6 +70,8 @@ def lib():
         L.og_num_cells.restype = ctypes.c_int64
         L.og_num_cells.argtypes = [P]
         L.og_num_threads.restype = ctypes.c_int
+        L.og_set_num_threads.argtypes = [ctypes.c_int]
+        L.og_set_num_threads.restype = None
         L.og_bins_build.restype = P
         L.og_bins_build.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.og_bins_free.argtypes = [P]
@@ -91,6 +93,11 @@ def _ptr(a: np.ndarray) -> int:
 
 def num_threads() -> int:
     return lib().og_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops (n <= 0: one per processor); for timing only."""
+    lib().og_set_num_threads(int(n))
 
 
 class OracleGrid:

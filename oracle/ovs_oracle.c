@@ -76,6 +76,15 @@ int og_num_threads(void) {
 #endif
 }
 
+/* threads of the calling thread's later parallel loops (n <= 0: one per processor); timing only */
+void og_set_num_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 /* Node ids of the 8 corners of a cell, corner a = di + 2dj + 4dk. */
 void og_cell_nodes(const og_grid* g, int64_t cell, int64_t nodes[8]) {
     int64_t ci = og_cells_axis(g, 0), cj = og_cells_axis(g, 1);
