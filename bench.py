@@ -74,6 +74,31 @@ def dist_env():
     return rank, world, local
 
 
+def combine_ranks(world: int, total_ms: float, e2e_ms: float, pts: float, device="cpu"):
+    """Whole-job figures of a replicas run: the slowest rank's timed-region and end-to-end times (max over ranks)
+    and the points of all ranks (sum).  One rank: the local figures."""
+    if world == 1:
+        return total_ms, e2e_ms, pts
+    import torch
+
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    p = torch.tensor([pts], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(p, op=torch.distributed.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(p[0])
+
+
+def rank0_choice(world: int, flag: bool, device="cpu") -> bool:
+    """Every rank takes rank 0's choice (e.g. the launch mode), so that all replicas run the same way."""
+    if world == 1:
+        return flag
+    import torch
+
+    t = torch.tensor([1 if flag else 0], dtype=torch.int32, device=device)
+    torch.distributed.broadcast(t, 0)
+    return bool(t.item())
+
+
 def config_index(name: str) -> int:
     return int(name[3:])
 
@@ -333,13 +358,7 @@ def run_ovs(args, rank, world, local):
         torch.cuda.synchronize()
         # (the first step after the reset starts cold in both modes: left out, it would dominate the sums)
         calib[mode] += float(np.sum([a.elapsed_time(b) for a, b in list(zip(ec0, ec1))[1:]]))
-    if world > 1:  # every rank the same mode: rank 0's choice
-        pick = torch.tensor([calib[ovs.OVS_LAUNCH_GRAPH] <= calib[ovs.OVS_LAUNCH_DIRECT]], dtype=torch.int32,
-                            device=dev)
-        torch.distributed.broadcast(pick, 0)
-        use_graph = bool(pick.item())
-    else:
-        use_graph = calib[ovs.OVS_LAUNCH_GRAPH] <= calib[ovs.OVS_LAUNCH_DIRECT]
+    use_graph = rank0_choice(world, calib[ovs.OVS_LAUNCH_GRAPH] <= calib[ovs.OVS_LAUNCH_DIRECT], dev)
     tuning["launch"] = ovs.OVS_LAUNCH_GRAPH if use_graph else ovs.OVS_LAUNCH_DIRECT
     ctx.set_options(launch=tuning["launch"])
     # the clock sampler starts before the timed region and has reported once before it begins (its start-up
@@ -508,12 +527,7 @@ def run_ovs(args, rank, world, local):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         h2d += 4 * n
         d2h += n * (4 * outs[0].element_size() + 1)
-    if world > 1:
-        t = torch.tensor([total_ms, float(np.sum(e2e_ms))], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_total = float(t[0]), float(t[1])
-    else:
-        e2e_total = float(np.sum(e2e_ms))
+    total_ms, e2e_total, pts_all = combine_ranks(world, total_ms, float(np.sum(e2e_ms)), float(pts), dev)
     stats = None
     if rank == 0:
         ctx.set_options(collect_stats=1)
@@ -522,7 +536,6 @@ def run_ovs(args, rank, world, local):
         stats = ctx.stats(reset=True)
         ctx.set_options(collect_stats=0)
     ctx.sync()
-    pts_all = pts * world
     value = pts_all / (total_ms / 1e3)
     peak, peak_kind = measured_peak()
     fast_avg_ms = float(np.mean(fast_ms))
