@@ -483,3 +483,22 @@ def test_ray_parity_fish_surface_matches_its_shape():
     outer = ~gen.inside_fish_layer(np.stack([P[:, 0], P[:, 1], P[:, 2] * 0.8], 1), 1.1, 0.0)
     assert inner.sum() > 500 and outer.sum() > 10000
     assert np.all(inside[inner] == 1) and np.all(inside[outer & (np.abs(P[:, 0]) < 0.45)] == 0)
+
+
+def test_ray_parity_same_along_every_axis():
+    """A positive scaling of the axes maps inside to inside, and shrinking one axis 10x makes it the shortest, so
+    the ray runs along x, y and z in turn: away from the surface the three answers equal the unscaled one (pins
+    the choice of the ray's axis and the order of the projection plane's axes)."""
+    g = gen.ellipsoid_ogrid(48, 32, 8, (0.2, 0.1, 0.1), 0.4, beta_r=2.0)
+    V, T = gen.body_surface(g)
+    rng = np.random.default_rng(9)
+    P = rng.uniform(-0.25, 0.25, size=(8000, 3)) * np.array([1.0, 0.6, 0.6])
+    f = (P[:, 0] / 0.2) ** 2 + (P[:, 1] / 0.1) ** 2 + (P[:, 2] / 0.1) ** 2
+    clear = np.abs(f - 1) > 0.05
+    ref = oracle.surface_inside(V, T, P)
+    for a in range(3):
+        s = np.ones(3)
+        s[a] = 0.1
+        got = oracle.surface_inside(V * s, T, P * s)
+        assert np.array_equal(got[clear], ref[clear]), a
+    assert 500 < ref[clear].sum() < clear.sum() - 500
