@@ -315,6 +315,17 @@ int ovs_spmv(ovs_ctx* ctx, int64_t nrows, const int32_t* row_ptr, const int64_t*
 /* Forget all per-node donor hints (next assemble starts cold). */
 int ovs_reset_hints(ovs_ctx* ctx);
 
+/* Checkpoint / resume of what a time loop carries from one step to the next (no counterpart in the paper):
+ * the previous donor of every node of a receiver grid, which the next assembly starts its walk from.
+ * dst / src: device uint32 [the grid's node count], one entry per node: (donor grid id << 27) | donor cell id,
+ * or 0xFFFFFFFF for none.  Copied on the context stream (the caller synchronises before reading dst or
+ * reusing src).  ovs_set_donors accepts any values: an entry that names no cell of its donor grid is ignored
+ * (that node's search starts cold), so a checkpoint can never change a result, only how fast it is found.
+ * With the guess networks (ovs_guess_get_params / ovs_guess_set_params) this is the whole state: a resumed
+ * run gives the donors of an uninterrupted one, bit for bit.  Errors: OVS_ERR_ARG (unknown grid, NULL). */
+int ovs_get_donors(ovs_ctx* ctx, int32_t grid_id, uint32_t* dst);
+int ovs_set_donors(ovs_ctx* ctx, int32_t grid_id, const uint32_t* src);
+
 /* Launch shapes of the persistent kernels: blocks per SM of each grid (a kernel's grid is this many blocks
  * times the SM count, whatever the call's size).  0 = the default: assembly 3 (its launch bound), interpolation
  * the occupancy calculator's figure, slow path 1, learned guess 8. */

@@ -1117,6 +1117,26 @@ int ovs_reset_hints(ovs_ctx* c) {
     return OVS_OK;
 }
 
+int ovs_get_donors(ovs_ctx* c, int32_t grid_id, uint32_t* dst) {
+    if (!c) return OVS_ERR_ARG;
+    if (grid_id < 0 || grid_id >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", grid_id);
+    if (!dst) return fail(c, OVS_ERR_ARG, "dst is NULL");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    OVS_CUDA(c, cudaMemcpyAsync(dst, c->grids[grid_id].hint, (size_t)c->grids[grid_id].nnodes * 4,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    return OVS_OK;
+}
+
+int ovs_set_donors(ovs_ctx* c, int32_t grid_id, const uint32_t* src) {
+    if (!c) return OVS_ERR_ARG;
+    if (grid_id < 0 || grid_id >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", grid_id);
+    if (!src) return fail(c, OVS_ERR_ARG, "src is NULL");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    OVS_CUDA(c, cudaMemcpyAsync(c->grids[grid_id].hint, src, (size_t)c->grids[grid_id].nnodes * 4,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    return OVS_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------------------

@@ -56,6 +56,8 @@ EXPORTS = [
     "ovs_interp_matrix", "ovs_spmv", "ovs_set_iblank", "ovs_surface_workspace_size", "ovs_create_surface",
     "ovs_hole_cut",
     "ovs_hole_cut_many",
+    "ovs_get_donors",
+    "ovs_set_donors",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -164,6 +166,8 @@ def load(path: Optional[str] = None):
         "ovs_create_surface": [V, I32, I64, V, I64, V, V, SZ, ctypes.POINTER(I32)],
         "ovs_hole_cut": [V, I32, I32, I64, V, V],
         "ovs_hole_cut_many": [V, I32, V, I32, V, V, V],
+        "ovs_get_donors": [V, I32, V],
+        "ovs_set_donors": [V, I32, V],
         "ovs_spmv": [V, I64, V, V, V, V, V, I32],
         "ovs_set_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
@@ -392,6 +396,16 @@ def ovs_reset_hints(ctx):
     _check(ctx, load().ovs_reset_hints(ctx))
 
 
+def ovs_get_donors(ctx, grid_id: int, dst: int):
+    """dst: device pointer to uint32 [the grid's node count]."""
+    _check(ctx, load().ovs_get_donors(ctx, int(grid_id), dst))
+
+
+def ovs_set_donors(ctx, grid_id: int, src: int):
+    """src: device pointer to uint32 [the grid's node count]."""
+    _check(ctx, load().ovs_set_donors(ctx, int(grid_id), src))
+
+
 def ovs_set_trace_events(ctx, events):
     """events: sequence of torch.cuda.Event (or None) -> recorded at the points include/ovs.h lists.  A torch
     event exists only after its first record(), so record each once before passing it."""
@@ -586,6 +600,19 @@ class Context:
         n = int(nodes.numel()) if nodes is not None else int(iblank.numel())
         ovs_hole_cut(self.ctx, sid, target_gid, n, nodes.data_ptr() if nodes is not None else None,
                      iblank.data_ptr())
+
+    def get_donors(self, gid: int):
+        """ovs_get_donors: grid gid's previous donors as a device int32 tensor (the uint32 bits), one per node."""
+        d = self.grids[gid][0]
+        out = self.torch.empty(int(d.n[0]) * int(d.n[1]) * int(d.n[2]), dtype=self.torch.int32, device=self.device)
+        ovs_get_donors(self.ctx, gid, out.data_ptr())
+        return out
+
+    def set_donors(self, gid: int, donors):
+        """ovs_set_donors from a device int32 tensor of get_donors' layout (kept alive by this context until the
+        copy has run: the caller synchronises or keeps the tensor)."""
+        assert donors.dtype == self.torch.int32 and donors.is_contiguous()
+        ovs_set_donors(self.ctx, gid, donors.data_ptr())
 
     def hole_cut_many(self, sids, target_gid: int, iblank, nodes):
         """ovs_hole_cut_many: surfaces sids cut iblank in one launch; nodes: one device int32 tensor per surface
