@@ -154,3 +154,32 @@ def test_school_motion(school):
         ang = np.arctan2(dR[1, 0], dR[0, 0])
         assert ang == pytest.approx(0.5 * (a.omega[2] + b.omega[2]) * dt, rel=1e-3, abs=1e-9)
         assert np.abs(a.R.T @ a.R - np.eye(3)).max() < 1e-14
+
+
+def naca12_half_width(s):
+    """NACA four-digit half-thickness at 12 % of the chord (closed trailing edge), written out from its definition."""
+    return 5 * 0.12 * (0.2969 * np.sqrt(s) - 0.1260 * s - 0.3516 * s ** 2 + 0.2843 * s ** 3 - 0.1036 * s ** 4)
+
+
+@pytest.mark.parametrize("which", ["ellipsoid", "fish"])
+def test_body_surface_closed_oriented_and_of_the_body_volume(which):
+    """The hole-cutting surfaces: every directed edge used once and its reverse once (closed, consistently
+    oriented), no zero-area triangle, and the enclosed volume (divergence theorem) just below the body's own --
+    the vertices lie on the body, so the facets are chords: the ellipsoid 4/3 pi abc, the fish the integral of
+    its elliptic cross-sections pi w (1.6 w) (the midline shear keeps volume)."""
+    from scipy.integrate import quad
+
+    if which == "ellipsoid":
+        g = gen.ellipsoid_ogrid(48, 32, 8, (0.2, 0.1, 0.1), 0.4, beta_r=2.0)
+        want = 4.0 / 3.0 * np.pi * 0.2 * 0.1 * 0.1
+    else:
+        g = gen.fish_ogrid("fish", 64, 48, 8, phase=1.1)
+        want = quad(lambda s: np.pi * naca12_half_width(s) * 1.6 * naca12_half_width(s), 0.0, 1.0)[0]
+    V, T = gen.body_surface(g)
+    e = np.concatenate([T[:, [0, 1]], T[:, [1, 2]], T[:, [2, 0]]]).tolist()
+    directed = set(map(tuple, e))
+    assert len(directed) == len(e) and all((b, a) in directed for a, b in directed)
+    P = V[T]
+    assert np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1).min() > 0
+    vol = abs(np.einsum("ij,ij->i", P[:, 0], np.cross(P[:, 1], P[:, 2])).sum() / 6.0)
+    assert 0.985 * want < vol <= want * (1 + 1e-9), (vol, want)
