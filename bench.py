@@ -409,17 +409,25 @@ def run_ovs(args, rank, world, local):
                    "note": "fields as (u, v, w, p) records per node; the headline passes four arrays per grid"}
     # plain, unbatched: one ovs_assemble_interpolate per fringe set (direct launches, default launch shapes), the
     # same steps and start (previous donor, else control cell), for the batching comparison
-    def unbatched_step(s):
-        m, fs = inputs[s]
-        for gid, mo in zip(gids, m):
-            ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
-        b = 0
-        for st_ in dev_sets[s]:
+    # (its call arguments, one call per set, marshalled before timing as for the batched calls)
+    unb_prep = []
+    for s_ in range(len(inputs)):
+        calls, b = [], 0
+        for st_ in dev_sets[s_]:
             n = int(st_[1].numel())
             d = {"grid": donors["grid"][b:b + n], "cell": donors["cell"][b:b + n], "xi": donors["xi"][3 * b:3 * (b + n)],
                  "status": donors["status"][b:b + n], "xi_dtype": xi_dtype, "n": n}
-            ctx.assemble_interpolate([st_], fields, donors=d, out=[o[b:b + n] for o in outs])
+            farr, o, _ = ctx._fields_structs(fields, n, [x[b:b + n] for x in outs])
+            calls.append((ovs.make_sets([st_]), ovs.Context.donors_struct(d), farr, o))
             b += n
+        unb_prep.append((calls, b))
+
+    def unbatched_step(s):
+        for gid, _, ptrs in prep[s][0]:
+            call(lib.ovs_set_motion(ctx.ctx, gid, *ptrs))
+        calls, b = unb_prep[s]
+        for sarr, dstruct, farr, o in calls:
+            call(lib.ovs_assemble_interpolate(ctx.ctx, sarr, 1, ctypes.byref(dstruct), farr, len(gids), ctypes.byref(o)))
         return b
 
     saved_tuning = ovs.ovs_get_tuning(ctx.ctx)
