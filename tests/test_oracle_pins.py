@@ -502,3 +502,36 @@ def test_ray_parity_same_along_every_axis():
         got = oracle.surface_inside(V * s, T, P * s)
         assert np.array_equal(got[clear], ref[clear]), a
     assert 500 < ref[clear].sum() < clear.sum() - 500
+
+
+def _torus_surface(R=0.3, r=0.1, nu=64, nv=32):
+    """A closed triangulated torus about the z axis (tube radius r, centre radius R)."""
+    u = 2 * np.pi * np.arange(nu) / nu
+    v = 2 * np.pi * np.arange(nv) / nv
+    U, Vv = np.meshgrid(u, v, indexing="ij")
+    P = np.stack([(R + r * np.cos(Vv)) * np.cos(U), (R + r * np.cos(Vv)) * np.sin(U), r * np.sin(Vv)], -1)
+    V = P.reshape(-1, 3)
+    vid = lambda i, j: (i % nu) * nv + (j % nv)
+    T = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            T += [(a, b, c), (a, c, d)]
+    return V, np.array(T, np.int32)
+
+
+def test_ray_parity_torus_many_crossings():
+    """Rays through a torus cross its surface up to four times: inside iff inside the tube, away from a band
+    that covers the facets' chords, with the ray along the torus axis (z is the shortest box axis) and, the z
+    axis stretched 5x, across it (x is then the shortest, and rays through the hole cross four times)."""
+    R, r = 0.3, 0.1
+    V, T = _torus_surface(R, r)
+    rng = np.random.default_rng(12)
+    P = rng.uniform(-0.45, 0.45, size=(20000, 3)) * np.array([1.0, 1.0, 0.3])
+    d = (np.hypot(P[:, 0], P[:, 1]) - R) ** 2 + P[:, 2] ** 2
+    clear = np.abs(np.sqrt(d) - r) > 0.01
+    want = (d < r * r).astype(np.uint8)
+    assert np.array_equal(oracle.surface_inside(V, T, P)[clear], want[clear])
+    s = np.array([1.0, 1.0, 5.0])
+    assert np.array_equal(oracle.surface_inside(V * s, T, P * s)[clear], want[clear])
+    assert 1000 < want[clear].sum() < clear.sum() - 1000
