@@ -23,8 +23,12 @@
  *    workspaces (sizes from the *_workspace_size calls) and all inputs and
  *    outputs.  Host pointers are read during the call only.
  *  - Every call that launches work enqueues it on the context's stream and
- *    returns without waiting, except ovs_create_grid (which synchronises the
- *    stream to size its control-cell bins) and ovs_sync / ovs_get_stats.
+ *    returns without waiting, except the set-up and control calls, which
+ *    synchronise the stream: ovs_workspace_attach, ovs_create_grid (it sizes
+ *    its control-cell bins), ovs_create_surface, ovs_set_iblank,
+ *    ovs_set_tuning, ovs_autotune, ovs_train_guess, ovs_guess_set_params,
+ *    ovs_sync, ovs_get_stats and ovs_ctx_destroy.  (A step call can also wait,
+ *    on the host, for the call two calls earlier: see OVS_LAUNCH_*.)
  *  - Return value: OVS_OK (0) or a negative OVS_ERR_* code; ovs_last_error()
  *    gives a message.  No C++ exception crosses the ABI.  A context is used by
  *    one host thread at a time.
@@ -81,6 +85,7 @@ extern "C" {
 #define OVS_GUESS_HINT 0 /* start from the donor found for the same receiver node last call, else bins */
 #define OVS_GUESS_BINS 1 /* always start from the control-cell bin of the point */
 #define OVS_GUESS_MLP 2  /* body grids with a trained guess network: start there when no hint */
+#define OVS_GUESS_MLP_ONLY 3 /* body grids with a trained guess network: always start there (hints ignored) */
 /* How a call's kernels reach the GPU.  Every call first copies its parameters (sets, frame maps, motions,
  * output pointers: one block) from a double-buffered pinned staging area to the context workspace; the
  * kernels read them there, and their grids are persistent (a multiple of the SM count), so the launch
@@ -92,7 +97,6 @@ extern "C" {
  * A call that reuses a staging buffer first waits (host) for the call that used it two calls earlier. */
 #define OVS_LAUNCH_DIRECT 0
 #define OVS_LAUNCH_GRAPH 1
-#define OVS_GUESS_MLP_ONLY 3 /* body grids with a trained guess network: always start there (hints ignored) */
 
 typedef struct ovs_ctx ovs_ctx;
 
