@@ -177,8 +177,9 @@ def newton_hex(X: np.ndarray, p: np.ndarray):
 
 def surface_inside(V: np.ndarray, T: np.ndarray, P: np.ndarray) -> np.ndarray:
     """Hole cutting (Sec. 2.2.1): 1 where a point (n, 3) is inside the closed triangulated surface (vertices
-    V (nv, 3), triangles T (nt, 3) of vertex ids), by the parity of the crossings of a ray along +x (every
-    triangle tested; the tie rules are in ovs_oracle.c)."""
+    V (nv, 3), triangles T (nt, 3) of vertex ids), by the parity of the crossings of a ray along the
+    surface's shortest bounding-box axis (the first such axis on a tie), every triangle tested; the tie
+    rules are in ovs_oracle.c (og_surface_inside)."""
     V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1, 3)
     T = np.ascontiguousarray(T, dtype=np.int32).reshape(-1, 3)
     P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1, 3)

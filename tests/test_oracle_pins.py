@@ -350,6 +350,56 @@ def test_silu_closed_form():
     assert oracle.dsilu(np.array([0.0]))[0] == pytest.approx(0.5)
 
 
+def test_mlp_forward_hand_worked_h2_network():
+    """A 3-2-2-3 network whose output is worked out by hand.  sigma(ln 3) = 1 / (1 + 1/3) = 3/4 and
+    sigma(-ln 3) = 1/4, so silu(ln 3) = (3/4) ln 3, silu(-ln 3) = -(1/4) ln 3 and silu(0) = 0.
+    Layer 1 picks x0 and x1 (x2 must not matter): z1 = (ln 3, -ln 3), h1 = ((3/4) ln 3, -(1/4) ln 3).
+    Layer 2 (W2[out][in] = [[1, 1], [2, 0]], b2 = ((1/2) ln 3, -(3/2) ln 3)): z2 = (ln 3, 0),
+    h2 = ((3/4) ln 3, 0).  Output layer, linear (no SiLU): y = W3 h2 + b3 with W3 = [[1, 0], [0, 1], [2, 3]],
+    b3 = (1, 2, 3): y = ((3/4) ln 3 + 1, 2, (3/2) ln 3 + 3).
+    A SiLU on the output (y1 = silu(2) != 2), a transposed W2 (z2_0 = (3/4) ln 3), a dropped bias, or x2
+    leaking in all change y."""
+    L3 = math.log(3.0)
+    P = {"W1": np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]), "b1": np.zeros(2),
+         "W2": np.array([[1.0, 1.0], [2.0, 0.0]]), "b2": np.array([0.5 * L3, -1.5 * L3]),
+         "W3": np.array([[1.0, 0.0], [0.0, 1.0], [2.0, 3.0]]), "b3": np.array([1.0, 2.0, 3.0])}
+    x = np.array([[L3, -L3, 5.0], [L3, -L3, -7.0]])
+    y, (_, z1, h1, z2, h2) = oracle.mlp_forward(P, x)
+    want = np.array([0.75 * L3 + 1.0, 2.0, 1.5 * L3 + 3.0])
+    assert np.allclose(y, want[None, :], rtol=0, atol=1e-14)
+    assert np.allclose(h1[0], [0.75 * L3, -0.25 * L3], rtol=0, atol=1e-15)
+    assert np.allclose(z2[0], [L3, 0.0], rtol=0, atol=1e-15)
+    assert np.allclose(h2[0], [0.75 * L3, 0.0], rtol=0, atol=1e-15)
+
+
+def test_adam_three_steps_against_closed_form_moments():
+    """Adam's moments unrolled: m_t = (1 - b1) sum_k b1^(t-k) g_k and v_t = (1 - b2) sum_k b2^(t-k) g_k^2, each
+    divided by its bias correction 1 - b^t (Kingma & Ba 2015, Algorithm 1); the step is lr m^_t / (sqrt(v^_t)
+    + eps).  Evaluated in exact rationals for a gradient sequence that changes sign and size, so a wrong power
+    in either correction (e.g. 1 - b2 in place of 1 - b2^t at t > 1) or a swapped b1 / b2 fails."""
+    from fractions import Fraction as Fr
+
+    b1, b2, lr, eps = Fr(9, 10), Fr(999, 1000), 0.05, 1e-8
+    gs = [np.array([1.0, 0.25]), np.array([-1.0, 0.5]), np.array([2.0, -3.0])]
+    P = {"a": np.array([0.3, -0.7])}
+    m = {"a": np.zeros(2)}
+    v = {"a": np.zeros(2)}
+    want = P["a"].copy()
+    for t in range(1, 4):
+        oracle.adam_step(P, {"a": gs[t - 1]}, m, v, t, lr=lr, b1=float(b1), b2=float(b2), eps=eps)
+        for c in range(2):
+            ms = (1 - b1) * sum(b1 ** (t - k) * Fr(gs[k - 1][c]) for k in range(1, t + 1)) / (1 - b1 ** t)
+            vs = (1 - b2) * sum(b2 ** (t - k) * Fr(gs[k - 1][c]) ** 2 for k in range(1, t + 1)) / (1 - b2 ** t)
+            want[c] -= lr * float(ms) / (math.sqrt(float(vs)) + eps)
+        assert np.allclose(P["a"], want, rtol=0, atol=1e-13), (t, P["a"], want)
+    # with a constant gradient the corrected moments are g and g^2 at every t: each step is lr sign(g)
+    P = {"a": np.array([1.0])}
+    m, v = {"a": np.zeros(1)}, {"a": np.zeros(1)}
+    for t in range(1, 4):
+        oracle.adam_step(P, {"a": np.array([-0.3])}, m, v, t, lr=0.1)
+    assert P["a"][0] == pytest.approx(1.3, abs=1e-6)
+
+
 def test_adam_first_step_is_signed_lr():
     """With bias correction the first Adam step moves each parameter by lr * sign(g) (|g| >> eps)."""
     P = {"a": np.array([1.0, -2.0, 3.0])}
