@@ -39,7 +39,10 @@ UNIT = "pts/s"
 BYTES_ASSEMBLE = 257
 BYTES_INTERP = 176
 BYTES_POINT = BYTES_ASSEMBLE + BYTES_INTERP
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_assemble_cfg1.txt")
+# The fused kernel (ovs_assemble_interpolate: k_assemble interpolates each point as it decides its donor) moves the
+# assembly's 257 B plus the interpolation's fields and outputs (128 + 16 B); the donor record is not re-read.
+BYTES_FUSED = BYTES_ASSEMBLE + 128 + 16
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_assemble_cfg4.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1910_09315_gb300", "csrc", f) for f in
                   ("ovs_assemble.cu", "ovs_internal.cuh", "ovs_fields.cuh")]
 WORKLOADS = {
@@ -49,9 +52,9 @@ WORKLOADS = {
     "cfg3": "school of 8 fish O-grids (48x32x32..128x64x64) in a stretched bg 384x256x128, dt=1.39e-3, FP32 fields",
     "cfg4": "school of 16 fish O-grids (64^3..160x96x96) in a stretched bg 512x384x256 (~50M nodes), FP32 fields",
 }
-# distinct time steps a run cycles through (a triangle wave over the first ones): building the fringe sets of a
-# step takes seconds on the host for the school workloads
-DISTINCT_STEPS = {"cfg3": 16, "cfg4": 8}
+# distinct time steps a run cycles through at most (a triangle wave over the first ones beyond that): building the
+# fringe sets of a school step takes seconds on the host, so they are built by a pool of host processes
+DISTINCT_STEPS = {"cfg3": 64, "cfg4": 64}
 
 
 def parse():
@@ -60,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ovs", choices=["ovs", "reference"])
-    ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cfg4", choices=sorted(WORKLOADS))
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points per CPU-baseline sample (0: auto)")
@@ -97,6 +100,20 @@ def rank0_choice(world: int, flag: bool, device="cpu") -> bool:
     t = torch.tensor([1 if flag else 0], dtype=torch.int32, device=device)
     torch.distributed.broadcast(t, 0)
     return bool(t.item())
+
+
+def guess_label(choice) -> str:
+    if choice is None:
+        return "plain: previous donor, else the control cell (--no-learned)"
+    if choice["chosen_width"] == 0:
+        return "learned guess requested; the guess autotuner kept no network (plain start was faster)"
+    H = choice["chosen_width"]
+    return f"learned: previous donor, else the 3-{H}-{H}-3 network of the donor grid (width chosen by ovs_autotune_guess)"
+
+
+def host_workers() -> int:
+    """Host processes for building the steps' fringe sets (at most 8: each holds a step's temporaries)."""
+    return max(1, min(8, os.cpu_count() or 1))
 
 
 def config_index(name: str) -> int:
@@ -202,18 +219,35 @@ def build_workload(name: str):
     return sc
 
 
-def step_inputs(sc, nsteps_total: int, distinct: int = 0):
-    """Motions and fringe sets of every step the run visits (host, precomputed outside the timed region)."""
-    cache = {}
-    out = []
+_POOL_SC = None
+
+
+def _step_job(ts):
+    m = _POOL_SC.motion(ts)
+    return ts, m, _POOL_SC.fringe_sets(ts, m)
+
+
+def step_inputs(sc, nsteps_total: int, distinct: int = 0, workers: int = 0):
+    """Motions and fringe sets of every step the run visits (host, precomputed outside the timed region).
+    workers > 1: the distinct steps are built by forked host processes (call this before any CUDA work: a process
+    forked after the first GPU call can hang)."""
+    global _POOL_SC
     n = min(sc.nsteps, distinct) if distinct else sc.nsteps
-    for s in range(nsteps_total):
-        ts = schedule(n, s)
+    need = sorted({schedule(n, s) for s in range(nsteps_total)})
+    cache = {}
+    if workers > 1 and len(need) > 1:
+        import multiprocessing as mp
+
+        _POOL_SC = sc
+        with mp.get_context("fork").Pool(min(workers, len(need))) as pool:
+            for ts, m, fs in pool.imap_unordered(_step_job, need):
+                cache[ts] = (m, fs)
+        _POOL_SC = None
+    for ts in need:
         if ts not in cache:
             m = sc.motion(ts)
             cache[ts] = (m, sc.fringe_sets(ts, m))
-        out.append(cache[ts])
-    return out
+    return [cache[schedule(n, s)] for s in range(nsteps_total)], len(need)
 
 
 # ----------------------------------------------------------------------------------------------------- ovs arm
@@ -224,11 +258,12 @@ def run_ovs(args, rank, world, local):
     from paper_1910_09315_gb300 import ovs
 
     ovs_build.build()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
+    # host inputs first: the step builder forks worker processes, which must happen before any CUDA call
     sc = build_workload(args.workload)
     K, W = args.steps, args.warmup
-    inputs = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0))
+    inputs, n_distinct = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0), workers=host_workers())
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
     max_pts = max(sum(len(s.node_ids) for s in fs) for _, fs in inputs)
     xi_dtype = ovs.OVS_F64 if sc.field_dtype == np.float64 else ovs.OVS_F32
     stream = torch.cuda.current_stream(dev)
@@ -338,8 +373,17 @@ def run_ovs(args, rank, world, local):
         interp = [tr[k][3].elapsed_time(tr[k][4]) for k in range(K)]
         return n, step, fast, slow, interp
 
-    # launch shapes: the library's autotuner on the last warm-up step (its calls run for real)
     nw = sum(int(x[1].numel()) for x in dev_sets[W - 1])
+    # the learned guess (on unless --no-learned): every body grid's network trained by the library's own kernels on
+    # samples of the grid itself, for each candidate width; the library's guess autotuner then picks the width, or
+    # no network, on the last warm-up step, and leaves its choice installed
+    guess_choice = None
+    if not args.no_learned:
+        guess_choice = train_and_pick_guess(args, sc, ctx, gids, dev_sets[W - 1], fields, donors_view(nw),
+                                            [o[:nw] for o in outs], ovs, torch)
+        for s in range(W):
+            one_step(s, dev_sets[s])
+    # launch shapes: the library's autotuner on the last warm-up step (its calls run for real)
     tuning = ctx.autotune(dev_sets[W - 1], fields, donors=donors_view(nw), out=[o[:nw] for o in outs], reps=3,
                           xi_dtype=xi_dtype)
     # launch mode: both modes timed on the (untimed) warm-up steps with the L2 flushed before each, as in the
@@ -403,9 +447,9 @@ def run_ovs(args, rank, world, local):
     for s in range(W):
         one_step(s, dev_sets[s])
     _, rec_ms, _, _, _ = timed(True, trace=False)
-    _, _, _, _, rec_interp_ms = timed(True, trace=True)
+    _, _, rec_fast_ms, _, _ = timed(True, trace=True)
     layout[0] = fields
-    interleaved = {"ms_per_step": float(np.mean(rec_ms)), "k_interp_ms": float(np.mean(rec_interp_ms)),
+    interleaved = {"ms_per_step": float(np.mean(rec_ms)), "k_assemble_ms": float(np.mean(rec_fast_ms)),
                    "note": "fields as (u, v, w, p) records per node; the headline passes four arrays per grid"}
     # plain, unbatched: one ovs_assemble_interpolate per fringe set (direct launches, default launch shapes), the
     # same steps and start (previous donor, else control cell), for the batching comparison
@@ -431,7 +475,8 @@ def run_ovs(args, rank, world, local):
         return b
 
     saved_tuning = ovs.ovs_get_tuning(ctx.ctx)
-    ctx.set_options(launch=ovs.OVS_LAUNCH_DIRECT)
+    headline_guess = ovs.ovs_get_options(ctx.ctx).guess
+    ctx.set_options(launch=ovs.OVS_LAUNCH_DIRECT, guess=ovs.OVS_GUESS_HINT)  # the plain start
     ctx.set_tuning(assemble_blocks_per_sm=0, interp_blocks_per_sm=0, slow_blocks_per_sm=0, guess_blocks_per_sm=0)
     ovs.ovs_reset_hints(ctx.ctx)  # the start of every timed pass
     for s in range(W):
@@ -446,6 +491,7 @@ def run_ovs(args, rank, world, local):
     torch.cuda.synchronize()
     unbatched_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0u, e1u)]))
     ovs.ovs_set_tuning(ctx.ctx, saved_tuning)  # the autotuned shapes and launch mode
+    ctx.set_options(guess=headline_guess)
     for s in range(W):
         one_step(s, dev_sets[s])
 
@@ -516,8 +562,8 @@ def run_ovs(args, rank, world, local):
                  "ms_per_step_one_call_per_body": ev_h[2].elapsed_time(ev_h[3]) / reps,
                  "note": "one ovs_hole_cut_many launch for all bodies (mask fill included)"}
         ovs.ovs_set_iblank(ctx.ctx, gids[0], None)
-    learned = None if args.no_learned else learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush,
-                                                            K, W, ovs, torch)
+    learned = None if args.no_learned else learned_vs_plain(guess_choice, ctx, dev_sets, one_step, timed, stream,
+                                                            flush, K, W, ovs, torch)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
     host_out = [torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)]
     host_status = torch.empty(max_pts, dtype=torch.uint8).pin_memory()
@@ -548,7 +594,7 @@ def run_ovs(args, rank, world, local):
     peak, peak_kind = measured_peak()
     fast_avg_ms = float(np.mean(fast_ms))
     pts_per_step = pts / K
-    achieved = BYTES_ASSEMBLE * pts_per_step / (fast_avg_ms / 1e3) / 1e9
+    achieved = BYTES_FUSED * pts_per_step / (fast_avg_ms / 1e3) / 1e9
     traffic = profile_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -556,26 +602,28 @@ def run_ovs(args, rank, world, local):
         "dtype": "f64 coords / f32 Newton+fields" if xi_dtype == ovs.OVS_F32 else "f64",
         "data": "synthetic (seeded generator, shapes of the stated workload)",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "points_per_step": pts_per_step,
-                   "guess": "previous-donor hint + control-cell bins (plain)", "parallelism": f"replicas x{world}",
+                   "guess": guess_label(guess_choice), "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MB write) between timed steps", "timing": "per-step CUDA events, steps enqueued back to back",
                    "call": "ovs_set_motion per grid + ovs_assemble_interpolate per step",
                    "launch": ("CUDA graph per step (captured once)" if tuning["launch"] == ovs.OVS_LAUNCH_GRAPH
                               else "direct launches") + ", persistent kernels, shapes autotuned, launch mode "
                              "picked on the warm-up steps (L2 flushed)",
-                   "tuning": tuning, "grids": len(sc.grids), "sets_per_step": len(dev_sets[W])},
+                   "tuning": tuning, "grids": len(sc.grids), "sets_per_step": len(dev_sets[W]),
+                   "distinct_time_steps": n_distinct},
         "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
-        "breakdown_ms_per_step": {"k_assemble": fast_avg_ms, "k_slow (near-face || stuck halves)": float(np.mean(slow_ms)),
-                                  "k_interp": float(np.mean(interp_ms))},
+        "breakdown_ms_per_step": {"k_assemble (with the interpolation of its points)": fast_avg_ms,
+                                  "k_slow (near-face || stuck halves, with the interpolation of their points)":
+                                      float(np.mean(slow_ms))},
         "launch_modes_ms_per_step": {"graph": mode_ms["graph"], "direct": mode_ms["direct"],
                                      "direct_traced": float(np.mean(traced_ms)),
                                      "separate_calls": float(np.mean(sep_ms))},
         "roofline": {"kernel": "k_assemble", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": f"{peak_kind} hbm_gbs (copy)", "bytes_per_point": BYTES_ASSEMBLE,
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)", "bytes_per_point": BYTES_FUSED,
                      "traffic": traffic},
         "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                 "d2h_bytes_per_step": d2h // K},
-        "gpu_launches": 3 * K,  # per step: k_assemble, k_slow, k_interp
+        "gpu_launches": 2 * K,  # per step: k_assemble and k_slow (both interpolating)
         "clocks": ck,
         "walk_stats": stats,
         "plain_unbatched_ms_per_step": unbatched_ms,
@@ -590,33 +638,63 @@ def run_ovs(args, rank, world, local):
     return line
 
 
-def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, W, ovs, torch):
-    """Train every body grid's guess network (3-H-H-3 SiLU, 2M samples of the grid itself, by the library's
-    kernels) for H = 32, 64, 128; time the same steps with the plain start (previous donor, else the control
-    cell) and the learned one, cold (no previous donors: the first step of a run) and warm (a time loop); the
-    width with the fastest cold step is kept (the MLP-width part of the autotuning).  ms_per_step: the median
-    step, in the autotuned launch mode (the mean beside it); phases: a second, traced pass (direct launches)."""
+GUESS_WIDTHS = (32, 64)
+GUESS_SAMPLES = 2_000_000
+GUESS_EPOCHS = 40
+
+
+def train_and_pick_guess(args, sc, ctx, gids, sets, fields, donors, outs, ovs, torch):
+    """Train every body grid's guess network (3-H-H-3 SiLU, GUESS_SAMPLES samples of the grid itself, by the
+    library's kernels) for each width of GUESS_WIDTHS, then let the library's guess autotuner (ovs_autotune_guess)
+    pick one width or none on `sets`: its score is one cold plus one warm call.  Leaves options.guess = MLP and the
+    chosen networks installed."""
     import gen
 
-    out = {"network": "3-H-H-3 SiLU, FP16 tensor-core inference (FP32 accumulation in layers 1 and 3), trained by "
-                      "the library's kernels on 2M samples per body grid"}
     bodies = [gi for gi, g in enumerate(sc.grids) if g.role == 1]
-
-    def train(H):
+    params, train = {}, {}
+    for H in GUESS_WIDTHS:
         t0 = time.perf_counter()
         losses = []
+        per_grid = [None] * len(gids)
         for gi in bodies:
             g = sc.grids[gi]
-            cells, xi = gen.mlp_training_samples(config_index(args.workload), g, 2_000_000)
+            cells, xi = gen.mlp_training_samples(config_index(args.workload), g, GUESS_SAMPLES)
             rng = np.random.default_rng(100 + gi)
             init = np.concatenate([rng.normal(0, 0.8, 3 * H), np.zeros(H), rng.normal(0, 1 / np.sqrt(H), H * H),
                                    np.zeros(H), rng.normal(0, 1 / np.sqrt(H), 3 * H), np.zeros(3)]).astype(np.float32)
-            losses.append(ctx.train_guess(gids[gi], cells, xi.astype(np.float32), init, hidden=H, epochs=60,
+            losses.append(ctx.train_guess(gids[gi], cells, xi.astype(np.float32), init, hidden=H, epochs=GUESS_EPOCHS,
                                           batch=8192, lr=3e-3, lr_final=1e-5))
+            p = torch.empty(ovs.ovs_guess_param_count(H), dtype=torch.float32, device=ctx.device)
+            assert ovs.ovs_guess_get_params(ctx.ctx, gids[gi], p.data_ptr()) == H
+            per_grid[gi] = p
         torch.cuda.synchronize()
-        return time.perf_counter() - t0, float(np.mean(losses))
+        params[H] = per_grid
+        train[H] = {"train_s": time.perf_counter() - t0, "train_mse": float(np.mean(losses))}
+    ctx.set_options(guess=ovs.OVS_GUESS_MLP)
+    hidden = list(GUESS_WIDTHS) + [0]
+    cand = [params[H] for H in GUESS_WIDTHS] + [[None] * len(gids)]
+    best, ms = ctx.autotune_guess(sets, fields, hidden, cand, donors=donors, out=outs, reps=3)
+    return {"network": "3-H-H-3 SiLU per body grid, FP16 tensor-core inference (FP32 accumulation in layers 1 and 3)"
+                       f" inside k_assemble, trained by the library's kernels on {GUESS_SAMPLES} samples x "
+                       f"{GUESS_EPOCHS} epochs per body grid",
+            "bodies": len(bodies), "training": {str(H): v for H, v in train.items()},
+            "autotune_guess_ms_cold_warm": {str(h): list(m) for h, m in zip(hidden, ms)},
+            "chosen_width": hidden[best]}
 
-    def run(mode, steps, cold):
+
+def learned_vs_plain(choice, ctx, dev_sets, one_step, timed, stream, flush, K, W, ovs, torch):
+    """The same steps with the plain start (previous donor, else the control cell) and the learned one (previous
+    donor, else the network), warm (a time loop: every pass from reset hints plus the W warm-up steps) and cold (no
+    previous donors: a step after ovs_reset_hints), in the headline's launch mode; mean ms per step, L2 flushed
+    before each step; walk statistics from one more pass of each.  Leaves options.guess = MLP."""
+    out = dict(choice)
+
+    def warm(mode):
+        ctx.set_options(guess=mode)
+        _, ms, _, _, _ = timed(True, trace=False)
+        return float(np.mean(ms))
+
+    def cold(mode, steps):
         ctx.set_options(guess=mode)
         e0 = [torch.cuda.Event(enable_timing=True) for _ in steps]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in steps]
@@ -625,70 +703,35 @@ def learned_vs_plain(args, sc, ctx, gids, dev_sets, one_step, stream, flush, K, 
         torch.cuda.synchronize()
         for k, s in enumerate(steps):
             flush.zero_()
-            if cold:
-                ovs.ovs_reset_hints(ctx.ctx)
+            ovs.ovs_reset_hints(ctx.ctx)
             e0[k].record(stream)
             one_step(s, dev_sets[s])
             e1[k].record(stream)
         torch.cuda.synchronize()
-        per_step = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-        ms = float(np.median(per_step))  # the median step: a one-off stall of the host does not decide it
-        ms_mean = float(np.mean(per_step))
-        # traced pass: per-phase times and walk statistics (direct launches)
-        if not cold:
-            for s in range(W):
-                one_step(s, dev_sets[s])
-        ctx.set_options(collect_stats=1)
-        ctx.stats(reset=True)
-        tr = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in steps]
-        for row in tr:
-            for e in row:
-                e.record(stream)
-        torch.cuda.synchronize()
-        for k, s in enumerate(steps):
-            flush.zero_()
-            if cold:
-                ovs.ovs_reset_hints(ctx.ctx)
-            ovs.ovs_set_trace_events(ctx.ctx, tr[k])
-            one_step(s, dev_sets[s])
-        torch.cuda.synchronize()
-        ovs.ovs_set_trace_events(ctx.ctx, [])
-        st = ctx.stats(reset=True)
-        ctx.set_options(collect_stats=0)
-        learned_mode = mode in (ovs.OVS_GUESS_MLP, ovs.OVS_GUESS_MLP_ONLY)
-        return {"ms_per_step": ms, "ms_per_step_mean": ms_mean, "walk_steps_per_step": st["walk_steps"] / len(steps),
-                "guess_kernels_ms": float(np.mean([r[5].elapsed_time(r[6]) for r in tr])) if learned_mode else 0.0,
-                "k_assemble_ms": float(np.mean([r[0].elapsed_time(r[1]) for r in tr])),
-                "slow_kernels_ms": float(np.mean([r[1].elapsed_time(r[2]) for r in tr])),
-                "fallbacks_per_step": st["fallback"] / len(steps)}
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
 
-    cold_steps = list(range(W, W + 5))
-    warm = list(range(W, W + min(K, 50)))
-    res = {"cold_plain_control_cell": run(ovs.OVS_GUESS_BINS, cold_steps, True)}
-    widths = {}
-    best_h, best_ms = None, None
-    for H in (32, 64, 128):
-        ts, mse = train(H)
-        r = run(ovs.OVS_GUESS_MLP_ONLY, cold_steps, True)
-        widths[H] = {"train_s": ts, "train_mse": mse, "cold_ms_per_step": r["ms_per_step"],
-                     "cold_walk_steps_per_step": r["walk_steps_per_step"], "guess_kernels_ms": r["guess_kernels_ms"]}
-        if best_ms is None or r["ms_per_step"] < best_ms:
-            best_h, best_ms = H, r["ms_per_step"]
-    out["widths"] = widths
-    out["chosen_width"] = best_h
-    if best_h != 128:
-        train(best_h)
-    res["cold_learned_network"] = run(ovs.OVS_GUESS_MLP_ONLY, cold_steps, True)
-    for name, mode in (("warm_plain_previous_donor", ovs.OVS_GUESS_HINT),
-                       ("warm_learned_previous_donor_else_network", ovs.OVS_GUESS_MLP),
-                       ("warm_learned_network_only", ovs.OVS_GUESS_MLP_ONLY)):
+    def stats(mode, is_cold):
+        ctx.set_options(guess=mode, collect_stats=1)
+        ovs.ovs_reset_hints(ctx.ctx)
         for s in range(W):
             one_step(s, dev_sets[s])
-        res[name] = run(mode, warm, False)
-    ctx.set_options(guess=ovs.OVS_GUESS_HINT)
+        if is_cold:
+            ovs.ovs_reset_hints(ctx.ctx)
+        ctx.stats(reset=True)
+        one_step(W, dev_sets[W])
+        st = ctx.stats(reset=True)
+        ctx.set_options(collect_stats=0)
+        return st
+
+    cold_steps = list(range(W, W + min(K, 5)))
+    res = {}
+    for name, mode in (("plain", ovs.OVS_GUESS_HINT), ("learned", ovs.OVS_GUESS_MLP)):
+        res[name] = {"warm_ms_per_step": warm(mode), "cold_ms_per_step": cold(mode, cold_steps),
+                     "warm_stats": stats(mode, False), "cold_stats": stats(mode, True)}
+    ctx.set_options(guess=ovs.OVS_GUESS_MLP)
     out.update(res)
-    cp, cl = res["cold_plain_control_cell"]["ms_per_step"], res["cold_learned_network"]["ms_per_step"]
-    out["cold_speedup_learned_over_plain"] = cp / cl
+    out["warm_plain_over_learned"] = res["plain"]["warm_ms_per_step"] / res["learned"]["warm_ms_per_step"]
+    out["cold_plain_over_learned"] = res["plain"]["cold_ms_per_step"] / res["learned"]["cold_ms_per_step"]
     return out
 
 
@@ -746,7 +789,7 @@ def run_reference(args, rank, world):
     oracle.build()
     sc = build_workload(args.workload)
     K, W = args.steps, args.warmup
-    inputs = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0))
+    inputs, _ = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0), workers=host_workers())
     rng = np.random.default_rng(11)
     per_step = 20_000
     grids = None

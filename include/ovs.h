@@ -91,9 +91,10 @@ extern "C" {
  * kernels read them there, and their grids are persistent (a multiple of the SM count), so the launch
  * sequence of a call depends only on which kernels it needs.
  *   GRAPH:  that sequence is captured once per kind of call (assemble, assemble+interpolate in FP32 or FP64,
- *           the set of guess-network widths, the no-allocation queue) as a CUDA graph, two instances (one per
- *           staging buffer), and every later call of the same kind is one cudaGraphLaunch on the context stream.
- *   DIRECT: the same copy and kernels launched one by one (always the case while trace events are set).
+ *           the set of guess-network widths) as a CUDA graph, two instances (one per staging buffer), and every
+ *           later call of the same kind is one cudaGraphLaunch on the context stream.
+ *   DIRECT: the same copy and kernels launched one by one (always the case while trace events are set, and
+ *           always for ovs_assemble_noalloc).
  * A call that reuses a staging buffer first waits (host) for the call that used it two calls earlier. */
 #define OVS_LAUNCH_DIRECT 0
 #define OVS_LAUNCH_GRAPH 1
@@ -160,6 +161,11 @@ typedef struct {
     int64_t refined;     /* points decided by FP64 Newton */
     int64_t fallback;    /* points decided by the exhaustive control-cell search */
     int64_t guess_used;  /* points started from a guess network */
+    int64_t newton_iterations; /* FP32 Newton iterations of the walk */
+    int64_t warp_walk_steps;   /* sum over the warps' 32-point work items of the most walk steps of one of them
+                                  (walk_steps / (32 warp_walk_steps) = the share of lanes busy while a warp walks) */
+    int64_t near_face;   /* points handed to the near-face decision among a cell's neighbours */
+    int64_t stuck;       /* points handed to the exhaustive control-cell search (walk stuck or outside) */
 } ovs_stats;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL = legacy
@@ -243,7 +249,9 @@ int ovs_assemble(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const 
 
 /* ovs_assemble followed by ovs_interpolate for the same sets, fields and motions, in one call (one time step
  * of the method: donors, then the interpolated boundary values).  Writes the same donors and field values as
- * the two calls (`out` as in ovs_assemble, `fields`/`fout` as in ovs_interpolate). */
+ * the two calls (`out` as in ovs_assemble, `fields`/`fout` as in ovs_interpolate), in one pass per point: the
+ * assembly kernels interpolate each point from the local coordinates as stored in `out` as soon as its donor is
+ * decided. */
 int ovs_assemble_interpolate(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
                              const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout);
 
@@ -332,12 +340,13 @@ int ovs_set_donors(ovs_ctx* ctx, int32_t grid_id, const uint32_t* src);
 
 /* Launch shapes of the persistent kernels: blocks per SM of each grid (a kernel's grid is this many blocks
  * times the SM count, whatever the call's size).  0 = the default: assembly 3 (its launch bound), interpolation
- * the occupancy calculator's figure, slow path 1, learned guess 8. */
+ * the occupancy calculator's figure, slow path 1. */
 typedef struct {
     int32_t assemble_blocks_per_sm; /* k_assemble, 256 threads a block: 1..12 */
     int32_t interp_blocks_per_sm;   /* k_interp, 256 threads a block: 1..32 */
     int32_t slow_blocks_per_sm;     /* k_slow, 256 threads a block, per SM for each of its two halves: 1..8 */
-    int32_t guess_blocks_per_sm;    /* k_guess, 128 threads a block: 1..32 */
+    int32_t guess_blocks_per_sm;    /* 0..32, accepted and kept but without effect: the learned guess runs inside
+                                       the assembly kernel, in its launch shape */
     int32_t launch;                 /* OVS_LAUNCH_GRAPH or OVS_LAUNCH_DIRECT (the option of ovs_set_options);
                                        0 in ovs_set_tuning: leave the launch mode as it is */
 } ovs_tuning;
@@ -356,10 +365,27 @@ int ovs_autotune(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const 
                  const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t reps,
                  ovs_tuning* best);
 
+/* Autotuner of the learned guess (its network width, or none): ncand candidates, candidate k = networks of width
+ * hidden[k] (32, 64 or 128; 0 = no networks, the plain start from hints and control cells), with the device FP32
+ * parameters (layout of ovs_guess_set_params) of grid g at params[k * ngrids + g] (NULL: grid g gets no network;
+ * params may be NULL when every width is 0).  For each candidate it installs the networks and times `reps` calls
+ * of ovs_assemble_interpolate(sets, ..., fout) (fout NULL: ovs_assemble) started cold (donor hints reset before
+ * each) and `reps` started warm (after a call of the same sets), with CUDA events on the context stream, after one
+ * untimed call of each kind.  The score of a candidate is its mean cold plus its mean warm call time (a time loop
+ * pays both: the first step, and every step after it); the candidate with the lowest score stays installed and its
+ * index is written to *best; ms (may be NULL): [ncand][2] mean cold and warm milliseconds per call.  Requires
+ * options.guess = OVS_GUESS_MLP or OVS_GUESS_MLP_ONLY (else OVS_ERR_STATE).  The calls run for real (outputs and
+ * hints are those of the last one).  Synchronises the stream. */
+int ovs_autotune_guess(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                       const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t ncand,
+                       const int32_t* hidden, const float* const* params, int32_t reps, float* ms, int32_t* best);
+
 /* Tracing: record caller-created CUDA events (cudaEvent_t, NULL to skip one) on the context's stream at
  * fixed points of later calls: ev[0] before the fast assembly kernel, ev[1] after it, ev[2] after the
- * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it, ev[5] before
- * the learned-guess pass and ev[6] after it (OVS_GUESS_MLP / OVS_GUESS_MLP_ONLY only).
+ * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it; ev[5] and ev[6]
+ * are not recorded (the learned guess runs inside the fast assembly kernel, between ev[0] and ev[1]).  In
+ * ovs_assemble_interpolate the two assembly kernels interpolate each point as they decide its donor (there is
+ * no interpolation kernel): ev[3] and ev[4] are then both recorded after the slow-path kernel.
  * n = 0 (or ev = NULL) switches tracing off.  The events must outlive their use. */
 int ovs_set_trace_events(ovs_ctx* ctx, void* const* ev, int32_t n);
 
@@ -367,11 +393,13 @@ int ovs_set_trace_events(ovs_ctx* ctx, void* const* ev, int32_t n);
  *
  * The paper has no counterpart: this is a property of the library, not of the method.  ovs_assemble needs
  * a context workspace sized for the largest call (ovs_workspace_size(max_points)), so a caller whose
- * point count grows must allocate a larger one.  Some callers cannot: code running while a CUDA stream is
- * being captured (cudaMalloc is not allowed there), solver plug-ins whose host application owns all device
- * memory, and time loops that must not take the implicit device synchronisation of cudaMalloc/cudaFree.
- * This entry point behaves exactly like ovs_assemble but keeps its only per-call scratch (the slow-path
- * queue of points decided in FP64) in a fixed array inside the library instead of the context workspace.
+ * point count grows must allocate a larger one.  Some callers cannot: solver plug-ins whose host
+ * application owns all device memory and hands them none, and time loops that must not take the implicit
+ * device synchronisation of cudaMalloc/cudaFree in the middle of a step.  This entry point computes what
+ * ovs_assemble computes (the same donors, hints, statistics and guess modes) but keeps its only per-call
+ * scratch (the slow-path queue of points decided near a face or by the exhaustive search) in a fixed array
+ * inside the library instead of the context workspace.  It differs from ovs_assemble in how it launches:
+ * always as direct kernel launches, never as a captured CUDA graph (the launch option is ignored).
  *
  *  - Limit: at most OVS_NOALLOC_MAX_POINTS points per call (sum over the sets); larger calls return
  *    OVS_ERR_WORKSPACE without launching anything.  The array is 24 MiB of device memory

@@ -720,13 +720,34 @@ void fill_interp(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
     }
 }
 
-// Kinds of call (bit set): which kernels a call launches.  Bits 4-6: guess-network widths 32 / 64 / 128.
+// Kinds of call (bit set): which kernels a call launches.
 constexpr uint32_t kStepAssemble = 1, kStepInterp = 2, kStepInterpF64 = 4, kStepNoAlloc = 8;
 
-int guess_width_mask(const ovs_ctx* c) {
-    int m = 0;
-    for (int g = 0; g < c->ngrids; ++g) m |= c->hidden[g] == 32 ? 1 : c->hidden[g] == 64 ? 2 : c->hidden[g] == 128 ? 4 : 0;
-    return m;
+// The learned guess of a call: with OVS_GUESS_MLP / OVS_GUESS_MLP_ONLY, every grid's network (width, box, input
+// normalisation as in its header, region) for the assembly kernel, which evaluates it for the points that have no
+// usable hint.  Returns whether any grid has one.
+bool fill_guess(const ovs_ctx* c, AsmParams* P) {
+    const bool mlp = c->opts.guess == OVS_GUESS_MLP || c->opts.guess == OVS_GUESS_MLP_ONLY;
+    bool any = false;
+    for (int g = 0; g < OVS_MAX_GRIDS; ++g) {
+        GuessDev& d = P->gn[g];
+        memset(&d, 0, sizeof d);
+        if (!mlp || g >= c->ngrids || !c->hidden[g]) continue;
+        const GridDev& gr = c->grids[g];
+        for (int a = 0; a < 3; ++a) {
+            d.lo[a] = (float)gr.lo[a];
+            d.hi[a] = (float)gr.hi[a];
+            d.centre[a] = (float)(0.5 * (gr.lo[a] + gr.hi[a]));
+            d.inv_half[a] = (float)(2.0 / (gr.hi[a] - gr.lo[a]));
+        }
+        d.hidden = c->hidden[g];
+        d.region = gr.mlp;
+        any = true;
+    }
+    P->guess_mlp = any ? 1 : 0;
+    P->guess_always = any && c->opts.guess == OVS_GUESS_MLP_ONLY;
+    P->guess_used = any && c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr;
+    return any;
 }
 
 // The staging buffer for the next call, once the call that last read it has finished.
@@ -745,17 +766,15 @@ cudaError_t acquire_stage(ovs_ctx* c, int* b) {
 cudaError_t enqueue_step(ovs_ctx* c, int b, uint32_t kind, uint32_t* qcount, cudaStream_t st, bool trace) {
     cudaError_t e = cudaMemcpyAsync(c->d_step, c->h_step[b], sizeof(StepParams), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    const int hmask = (int)((kind >> 4) & 7);
-    if (hmask) {
-        if (trace && c->trace[5]) cudaEventRecord(c->trace[5], st);
-        if ((e = launch_guess(c->d_step, c->d_grids, hmask, c->nsm, c->tune.guess_blocks_per_sm, st)) != cudaSuccess)
-            return e;
-        if (trace && c->trace[6]) cudaEventRecord(c->trace[6], st);
-    }
     if (kind & kStepAssemble) {
-        e = launch_assemble(&c->d_step->a, qcount, c->d_grids, c->nsm, c->tune.assemble_blocks_per_sm,
+        // with fields, the assembly kernels interpolate every point as they decide its donor (one pass)
+        const int im = (kind & kStepInterp) ? ((kind & kStepInterpF64) ? 2 : 1) : 0;
+        e = launch_assemble(c->d_step, im, qcount, c->d_grids, c->nsm, c->tune.assemble_blocks_per_sm,
                             c->tune.slow_blocks_per_sm, st, trace ? c->trace : nullptr);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess || !im) return e;
+        if (trace && c->trace[3]) cudaEventRecord(c->trace[3], st);
+        if (trace && c->trace[4]) cudaEventRecord(c->trace[4], st);
+        return cudaSuccess;
     }
     if (kind & kStepInterp)
         e = launch_interp(&c->d_step->i, (kind & kStepInterpF64) != 0, c->d_grids, c->nsm,
@@ -838,7 +857,8 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     P->nsets = nsets;
     P->xi_f64 = out->xi_dtype == OVS_F64;
     P->max_walk = c->opts.max_walk;
-    // the learned guess writes its cells into the hints, which the assembly then starts from
+    // learned guess: the assembly kernel starts the points without a usable hint where the network says, the
+    // others from their hints
     const bool mlp = c->opts.guess == OVS_GUESS_MLP || c->opts.guess == OVS_GUESS_MLP_ONLY;
     P->guess = mlp ? OVS_GUESS_HINT : c->opts.guess;
     P->stats = c->opts.collect_stats;
@@ -852,21 +872,15 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     P->queue_count = c->d_qcount;
     P->counters = c->d_counters;
     P->err = c->d_err;
-    P->guess_used = c->opts.collect_stats ? c->d_counters + kCtrGuess : nullptr;
-    P->guess_always = c->opts.guess == OVS_GUESS_MLP_ONLY;
     fill_sets(sets, nsets, P->s);
     fill_xforms(c, sets, nsets, P->xf);
     memcpy(P->m, c->motion, sizeof P->m);
+    fill_guess(c, P);
     uint32_t kind = kStepAssemble;
     if (fout) {
         memset(&S.i, 0, offsetof(InterpParams, s));
         fill_interp(c, sets, nsets, out, fields, fout, total, &S.i);
         kind |= kStepInterp | (S.i.f64 ? kStepInterpF64 : 0);
-    }
-    const int hmask = mlp ? guess_width_mask(c) : 0;
-    if (hmask) {
-        fill_guess_work(*P, c->hidden, S.w);
-        kind |= (uint32_t)hmask << 4;
     }
     cudaError_t e = run_step(c, b, kind, c->d_qcount, true);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble launch");
@@ -1097,6 +1111,10 @@ int ovs_get_stats(ovs_ctx* c, ovs_stats* out, int reset) {
     out->refined = (int64_t)h[kCtrRefined];
     out->fallback = (int64_t)h[kCtrFallback];
     out->guess_used = (int64_t)h[kCtrGuess];
+    out->newton_iterations = (int64_t)h[kCtrNewton];
+    out->warp_walk_steps = (int64_t)h[kCtrWarpWalk];
+    out->near_face = (int64_t)h[kCtrNear];
+    out->stuck = (int64_t)h[kCtrStuck];
     if (reset) OVS_CUDA(c, cudaMemsetAsync(c->d_counters, 0, sizeof h, c->stream));
     return OVS_OK;
 }
@@ -1250,15 +1268,11 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
         return OVS_OK;
     };
     const int occ = interp_default_blocks_per_sm(false);
-    ovs_tuning cur = {3, occ > 0 ? occ : 4, 1, kGuessBlocksPerSM};
-    const bool learned = (c->opts.guess == OVS_GUESS_MLP || c->opts.guess == OVS_GUESS_MLP_ONLY) && guess_width_mask(c);
+    ovs_tuning cur = {3, occ > 0 ? occ : 4, 1, 0};
     float best_ms = 0.f;
     int rc = trial(cur, &best_ms);
     const int cand_asm[] = {1, 2, 3, 4, 6};
     const int cand_slow[] = {1, 2, 4, 8};
-    const int cand_guess[] = {4, 8, 16};
-    int cand_interp[4] = {std::max(1, cur.interp_blocks_per_sm / 2), cur.interp_blocks_per_sm,
-                          std::min(32, 2 * cur.interp_blocks_per_sm), std::min(32, 4 * cur.interp_blocks_per_sm)};
     auto sweep = [&](int32_t ovs_tuning::*knob, const int* vals, int nv) {
         for (int k = 0; k < nv && rc == OVS_OK; ++k) {
             if (vals[k] == cur.*knob) continue;
@@ -1274,8 +1288,6 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
     };
     if (rc == OVS_OK) sweep(&ovs_tuning::assemble_blocks_per_sm, cand_asm, 5);
     if (rc == OVS_OK) sweep(&ovs_tuning::slow_blocks_per_sm, cand_slow, 4);
-    if (rc == OVS_OK && fout) sweep(&ovs_tuning::interp_blocks_per_sm, cand_interp, 4);
-    if (rc == OVS_OK && learned) sweep(&ovs_tuning::guess_blocks_per_sm, cand_guess, 3);
     // the launch mode for the chosen shapes: a CUDA graph per call (captured by the untimed call) or direct
     int launch = saved_launch;
     if (rc == OVS_OK) {
@@ -1303,6 +1315,86 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
         *best = cur;
         best->launch = launch;
     }
+    return OVS_OK;
+}
+
+int ovs_autotune_guess(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
+                       const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t ncand,
+                       const int32_t* hidden, const float* const* params, int32_t reps, float* ms, int32_t* best) {
+    if (!c) return OVS_ERR_ARG;
+    if (ncand < 1 || ncand > 16 || !hidden || !best) return fail(c, OVS_ERR_ARG, "ncand = %d (1..16), hidden, best", ncand);
+    if (reps < 1 || reps > 1000) return fail(c, OVS_ERR_ARG, "reps = %d (1..1000)", reps);
+    for (int k = 0; k < ncand; ++k) {
+        if (hidden[k] != 0 && hidden[k] != 32 && hidden[k] != 64 && hidden[k] != 128)
+            return fail(c, OVS_ERR_ARG, "candidate %d: hidden width %d (0, 32, 64 or 128)", k, hidden[k]);
+        if (hidden[k] && !params) return fail(c, OVS_ERR_ARG, "candidate %d has a width but params is NULL", k);
+    }
+    if (c->opts.guess != OVS_GUESS_MLP && c->opts.guess != OVS_GUESS_MLP_ONLY)
+        return fail(c, OVS_ERR_STATE, "set options.guess to OVS_GUESS_MLP (or MLP_ONLY) before tuning the guess");
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    // candidate k's networks: params[k * ngrids + g] for grid g (NULL: grid g has none); width 0: no networks
+    auto install = [&](int k) -> int {
+        for (int g = 0; g < c->ngrids; ++g) {
+            const float* p = hidden[k] ? params[(size_t)k * c->ngrids + g] : nullptr;
+            if (p) {
+                int rc = ovs_guess_set_params(c, g, hidden[k], p);
+                if (rc != OVS_OK) return rc;
+            } else {
+                c->hidden[g] = 0;  // the assembly then starts this grid's points from hints and control cells
+            }
+        }
+        return OVS_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, cudaGetLastError(), "autotune events");
+    }
+    // one call timed alone (events around it on the context stream); cold = after the hints were reset
+    auto timed_call = [&](bool cold, float* acc) -> int {
+        if (cold) {
+            int rc = ovs_reset_hints(c);
+            if (rc != OVS_OK) return rc;
+        }
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "autotune");
+        int rc = assemble_impl(c, sets, nsets, out, fields, nfields, fout);
+        if (rc != OVS_OK) return rc;
+        cudaError_t e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune timing");
+        *acc += t;
+        return OVS_OK;
+    };
+    int rc = OVS_OK, kbest = -1;
+    float best_score = 0.f;
+    for (int k = 0; k < ncand && rc == OVS_OK; ++k) {
+        rc = install(k);
+        float cold = 0.f, warm = 0.f, scratch = 0.f;
+        if (rc == OVS_OK) rc = timed_call(true, &scratch);  // untimed: graph capture, caches
+        for (int r = 0; r < reps && rc == OVS_OK; ++r) rc = timed_call(true, &cold);
+        if (rc == OVS_OK) rc = timed_call(false, &scratch);  // hints now warm
+        for (int r = 0; r < reps && rc == OVS_OK; ++r) rc = timed_call(false, &warm);
+        if (rc != OVS_OK) break;
+        cold /= (float)reps;
+        warm /= (float)reps;
+        if (ms) {
+            ms[2 * k] = cold;
+            ms[2 * k + 1] = warm;
+        }
+        // a time loop pays the cold call once and warm calls after it: both count
+        const float score = cold + warm;
+        if (kbest < 0 || score < best_score) {
+            kbest = k;
+            best_score = score;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == OVS_OK) rc = install(kbest);
+    if (rc != OVS_OK) return rc;
+    *best = kbest;
     return OVS_OK;
 }
 
@@ -1370,16 +1462,19 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
         }
         base = g_noalloc_ptr[c->device];
     }
-    // parameters in the context's pinned staging buffer (made with the context), launched directly: capturing a
-    // graph would allocate
+    // parameters in the context's pinned staging buffer (made with the context), launched directly (no graph is
+    // captured on this path)
     int b = 0;
     OVS_CUDA(c, acquire_stage(c, &b));
-    AsmParams& P = c->h_step[b]->a;
+    StepParams& S = *c->h_step[b];
+    AsmParams& P = S.a;
     memset(&P, 0, offsetof(AsmParams, s));
     P.nsets = nsets;
     P.xi_f64 = out->xi_dtype == OVS_F64;
     P.max_walk = c->opts.max_walk;
-    P.guess = c->opts.guess;
+    // the guess modes as in ovs_assemble (the learned guess runs inside the assembly kernel)
+    const bool mlp = c->opts.guess == OVS_GUESS_MLP || c->opts.guess == OVS_GUESS_MLP_ONLY;
+    P.guess = mlp ? OVS_GUESS_HINT : c->opts.guess;
     P.stats = c->opts.collect_stats;
     P.total = total;
     P.queue_cap = OVS_NOALLOC_MAX_POINTS;
@@ -1394,6 +1489,7 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     fill_sets(sets, nsets, P.s);
     fill_xforms(c, sets, nsets, P.xf);
     memcpy(P.m, c->motion, sizeof P.m);
+    fill_guess(c, &P);
     cudaError_t e = run_step(c, b, kStepAssemble | kStepNoAlloc, (uint32_t*)base, false);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble (no-alloc) launch");
     return OVS_OK;

@@ -12,7 +12,13 @@
 //   k_slow_stuck     one block per stuck walk: the exhaustive search of the point's control cell of
 //                    Sec. 2.2.5 (the paper's brute-force fallback); all threads filter the list, warp 0 decides.
 //   Both continue with the later grids of the set's priority list (Sec. 2.4 item 1).
-#include "ovs_internal.cuh"
+//
+// In a call that also interpolates (ovs_assemble_interpolate) both kernels go on, for every point whose donor
+// they decide, to the trilinear interpolation of u, v, w, p and the frame velocity transform (Sec. 2.2.6,
+// Sec. 2.1; ovs_fields.cuh) while donor, local coordinates and receiver node are at hand: one pass per point,
+// no separate interpolation kernel re-reading the donor records.
+#include "ovs_fields.cuh"
+#include "ovs_mlp.cuh"
 
 namespace ovs {
 
@@ -26,7 +32,7 @@ enum WalkResult { kWalkFound = 0, kWalkStuck = 1 };
 // FP32 walk from `cell` toward the donor-frame point xd (FP32 pairs).  On kWalkFound, cell/u/v/w hold a cell
 // whose FP32 local coordinates lie within kAccept32 of [0,1]^3.
 __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t& cell, float& u, float& v, float& w,
-                                      float& tau, int max_walk, int& steps, bool& blocked) {
+                                      float& tau, int max_walk, int& steps, int& iters, bool& blocked) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
     u = v = w = 0.5f;
@@ -39,7 +45,7 @@ __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t&
         float dx = __fadd_rn(__fsub_rn(xd[0].hi, r.x0h[0]), __fsub_rn(xd[0].lo, r.x0l[0]));
         float dy = __fadd_rn(__fsub_rn(xd[1].hi, r.x0h[1]), __fsub_rn(xd[1].lo, r.x0l[1]));
         float dz = __fadd_rn(__fsub_rn(xd[2].hi, r.x0h[2]), __fsub_rn(xd[2].lo, r.x0l[2]));
-        bool conv = newton32(r, dx, dy, dz, u, v, w);
+        bool conv = newton32(r, dx, dy, dz, u, v, w, kNewtonMaxIt32, &iters);
         if (!(fabsf(u) < 1e30f && fabsf(v) < 1e30f && fabsf(w) < 1e30f)) return kWalkStuck;
         bool in = u >= -kAccept32 && u <= 1.f + kAccept32 && v >= -kAccept32 && v <= 1.f + kAccept32 &&
                   w >= -kAccept32 && w <= 1.f + kAccept32;
@@ -133,35 +139,160 @@ __device__ __forceinline__ void write_none(const AsmParams& P, int64_t t, uint8_
     P.out_status[t] = status;
 }
 
+// Field type of a call: IM = 0 assembly only, 1 FP32 fields, 2 FP64 fields.
+template <int IM>
+struct FieldT {
+    using T = float;
+};
+template <>
+struct FieldT<2> {
+    using T = double;
+};
+
 __device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned v) {
     unsigned s = __reduce_add_sync(0xffffffffu, v);
     if (lane_id() == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
+// Per-warp shared staging of the learned guess: the network inputs of the warp's points that take a guess (one
+// 16-byte row each) and the cells the network gives them.
+struct GuessStage {
+    float4 rows[32];
+    uint32_t cell[32];
+};
+
+// The cell a network output points at: y = normalised curvilinear coordinates ((i + xi)/Ci, ...); the cell index
+// floor(y C) per axis, wrapped on a periodic axis and clamped to the grid on the others.
+__device__ __forceinline__ uint32_t guess_cell(const GridDev& g, const float y[3]) {
+    int ijk[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float Cf = (float)g.C[c];
+        float f = fminf(fmaxf(y[c] * Cf, -1e6f), 1e6f);
+        if (g.per[c]) f -= Cf * floorf(f / Cf);
+        ijk[c] = min(max((int)floorf(f), 0), g.C[c] - 1);
+    }
+    return (uint32_t)ijk[0] + (uint32_t)g.C[0] * ((uint32_t)ijk[1] + (uint32_t)g.C[1] * (uint32_t)ijk[2]);
+}
+
+template <int H>
+__device__ __forceinline__ void guess_tiles(const GuessDev& gn, const GridDev& g, GuessStage& st, int nrow) {
+    const MlpGlobal<H> W(gn.region);
+    const int lane = (int)lane_id();
+    for (int t0 = 0; t0 < nrow; t0 += 16) {
+        float y[2][3];
+        mlp_tile<H>(W, st.rows + t0, y);
+        if ((lane & 3) == 0) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int row = t0 + (lane >> 2) + 8 * rr;
+                if (row < nrow) st.cell[row] = guess_cell(g, y[rr]);
+            }
+        }
+    }
+}
+
+// Learned initial guess for the lanes with `want` (warp-collective: every lane calls it).  The lanes are grouped by
+// their donor grid's network (a warp's 32 points are consecutive in the call, so they usually share one set); each
+// group's inputs go to the warp's shared rows, 16 to a tensor-core tile.  Returns the guessed cell, or -1.
+__device__ __forceinline__ int64_t learned_guess(const AsmParams& P, const GridDev* __restrict__ G, GuessStage& st,
+                                                 bool want, int gd0, const float xn[3]) {
+    const unsigned lane = lane_id();
+    int64_t cell = -1;
+    unsigned pending = __ballot_sync(0xffffffffu, want);
+    while (pending) {
+        const int gsel = __shfl_sync(0xffffffffu, gd0, __ffs(pending) - 1);
+        const bool mine = want && gd0 == gsel;
+        const unsigned grp = __ballot_sync(0xffffffffu, mine);
+        pending &= ~grp;
+        const int nrow = __popc(grp);
+        const int row = __popc(grp & ((1u << lane) - 1u));
+        __syncwarp();
+        if (mine) st.rows[row] = make_float4(xn[0], xn[1], xn[2], 0.f);
+        if ((int)lane >= nrow && (int)lane < ((nrow + 15) & ~15)) st.rows[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        const GuessDev& gn = P.gn[gsel];
+        const GridDev& g = G[gsel];
+        if (gn.hidden == 32) guess_tiles<32>(gn, g, st, nrow);
+        else if (gn.hidden == 64) guess_tiles<64>(gn, g, st, nrow);
+        else guess_tiles<128>(gn, g, st, nrow);
+        __syncwarp();
+        if (mine) cell = st.cell[row];
+    }
+    __syncwarp();
+    return cell;
+}
+
 // One query point per thread (t may lie past the end: the lane then only takes part in the warp's collective
 // steps).  All lanes of a warp call it together.
-__device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev* __restrict__ G, const int64_t t) {
+template <int IM>
+__device__ __forceinline__ void assemble_point(const StepParams& S, const GridDev* __restrict__ G, GuessStage& gs,
+                                               const int64_t t) {
+    using T = typename FieldT<IM>::T;
+    const AsmParams& P = S.a;
     const bool active = t < P.total;
     bool slow = false;
     SlowEntry e;
-    int steps = 0;
+    int steps = 0, iters = 0;
+    // the receiver node as FP32 pairs and its image in the first donor's frame
+    int si = 0;
+    int32_t node = -1;
+    bool node_ok = false;
+    ff xd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (active) {
-        const int si = find_set(P.s, P.nsets, t);
+        si = find_set(P.s, P.nsets, t);
         const SetDev& s = P.s[si];
-        const int32_t node = __ldg(s.node_ids + (t - s.begin));
+        node = __ldg(s.node_ids + (t - s.begin));
         const GridDev& gr = G[s.receiver];
         const int64_t nn = gr.nnodes;
-        const bool node_ok = node >= 0 && node < nn;
+        node_ok = node >= 0 && node < nn;
         if (!node_ok) atomicOr(P.err, kErrBadNode);
-        // receiver node as FP32 pairs and its image in the first donor's frame
-        ff x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, xd[3];
+        ff x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         if (node_ok) {
             const float* xf = gr.xff;
 #pragma unroll
             for (int c = 0; c < 3; ++c) x[c] = {__ldg(xf + 2 * c * nn + node), __ldg(xf + (2 * c + 1) * nn + node)};
         }
         xf_apply(P.xf[si], x, xd);
-        bool fast_ok = ff_finite(xd[0]) && ff_finite(xd[1]) && ff_finite(xd[2]);
+    }
+    const bool fast_ok = ff_finite(xd[0]) && ff_finite(xd[1]) && ff_finite(xd[2]);
+    // learned guess (not in the paper): points whose first donor grid has a network and that have no usable hint
+    // start where the network says.  Its input needs no more than FP32: the point in the donor frame, inside the
+    // grid's padded box, normalised as in training.
+    int64_t gcell = -1;
+    if (P.guess_mlp) {  // uniform over the call
+        bool want = false;
+        int gd0 = -1;
+        float xn[3] = {0.f, 0.f, 0.f};
+        if (active && node_ok && fast_ok) {
+            const SetDev& s = P.s[si];
+            gd0 = s.donors[0];
+            const GuessDev& gn = P.gn[gd0];
+            if (gn.hidden) {
+                bool valid = false;
+                if (!P.guess_always) {
+                    const uint32_t h = G[s.receiver].hint[node];
+                    valid = h != kNoHint && (int)(h >> kCellBits) == gd0 &&
+                            (int64_t)(h & ((1u << kCellBits) - 1)) < G[gd0].ncells;
+                }
+                if (!valid) {
+                    bool inside = true;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float v = __fadd_rn(xd[c].hi, xd[c].lo);
+                        inside = inside && v >= gn.lo[c] && v <= gn.hi[c];
+                        xn[c] = (v - gn.centre[c]) * gn.inv_half[c];
+                    }
+                    want = inside;
+                }
+            }
+        }
+        gcell = learned_guess(P, G, gs, want, gd0, xn);
+        if (P.guess_used) warp_add(P.guess_used, gcell >= 0 ? 1u : 0u);
+    }
+    if (active) {
+        const SetDev& s = P.s[si];
+        const GridDev& gr = G[s.receiver];
         // FP64 route: later donors of the list, and points whose FP32-pair image is not finite
         bool have64 = false, bad = !node_ok;
         double3 xin = make_double3(0.0, 0.0, 0.0);
@@ -194,8 +325,8 @@ __device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev
                     continue;
                 }
             }
-            int64_t cell = -1;
-            if (P.guess == OVS_GUESS_HINT) {
+            int64_t cell = di == 0 ? gcell : -1;
+            if (cell < 0 && P.guess == OVS_GUESS_HINT) {
                 uint32_t h = gr.hint[node];
                 if (h != kNoHint && (int)(h >> kCellBits) == gd) cell = h & ((1u << kCellBits) - 1);
                 if (cell >= g.ncells) cell = -1;
@@ -218,13 +349,13 @@ __device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev
             float u, v, w, tau = 0.25f;
             bool blocked = false;
             int r = walk32(g, xd, cell, u, v, w, tau, from_hint ? min(P.max_walk, kHintWalk) : P.max_walk, steps,
-                           blocked);
+                           iters, blocked);
             if (r != kWalkFound && from_hint) {
                 // a walk from the previous donor or the learned guess that got stuck (on the grid's boundary, or
                 // after kHintWalk steps) starts again from the control cell before the exhaustive search
                 cell = control_cell();
                 if (cell < 0) continue;
-                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps, blocked);
+                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps, iters, blocked);
             }
             e.t = (int32_t)t;
             e.di = di;
@@ -236,6 +367,11 @@ __device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev
                     write_donor32(P, t, gd, cell, u, v, w, OVS_STATUS_FOUND);
                     gr.hint[node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
                     done = true;
+                    if (IM) {
+                        const InterpParams& I = S.i;
+                        interp_point<T>(g, gr, I.fields[gd], I.mode, I.mf[gd], I.mf[s.receiver], I.m[gd],
+                                        I.m[s.receiver], node, cell, (T)u, (T)v, (T)w, I.out, t);
+                    }
                 } else {
                     // near a face (FP64 decision among the neighbours), or FP64 precision (FP64 refinement)
                     slow = true;
@@ -253,7 +389,7 @@ __device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev
         }
         if (bad) write_none(P, t, OVS_STATUS_BADINPUT);
         else if (!done && !slow) write_none(P, t, OVS_STATUS_ORPHAN);
-
+        if (IM && (bad || (!done && !slow))) zero_point<T>(S.i.out, t);  // no donor: 0, as ovs_interpolate
     }
     // warp-aggregated append to the slow queues: points near a face (a candidate cell is known) from the front
     // of the buffer, stuck walks from the back.  Each point is queued at most once, so the two never meet.
@@ -277,23 +413,31 @@ __device__ __forceinline__ void assemble_point(const AsmParams& P, const GridDev
     if (P.stats) {
         warp_add(P.counters + kCtrPoints, active ? 1u : 0u);
         warp_add(P.counters + kCtrWalk, (unsigned)steps);
+        warp_add(P.counters + kCtrNewton, (unsigned)iters);
+        warp_add(P.counters + kCtrNear, near ? 1u : 0u);
+        warp_add(P.counters + kCtrStuck, slow && !near ? 1u : 0u);
+        const unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)steps);
+        if (lane == 0 && mx) atomicAdd(P.counters + kCtrWarpWalk, (unsigned long long)mx);
     }
 }
 
 // Persistent: a fixed grid (a multiple of the SM count, so that a captured step graph fits every call) whose
 // warps take work items of 32 consecutive points of the call (all sets of all grids in one index space) from a
 // counter, so that uneven walks balance across the GPU.
-__global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const AsmParams* __restrict__ Pp,
+template <int IM>
+__global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const StepParams* __restrict__ Sp,
                                                                          const GridDev* __restrict__ G) {
-    const AsmParams& P = *Pp;
+    const AsmParams& P = Sp->a;
     const int64_t total = P.total;
     const unsigned lane = lane_id();
+    __shared__ GuessStage gstage[kAsmThreads / 32];
+    GuessStage& gs = gstage[threadIdx.x >> 5];
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(P.queue_count + 2, 32u);
         base = __shfl_sync(0xffffffffu, base, 0);
         if ((int64_t)base >= total) break;
-        assemble_point(P, G, (int64_t)base + lane);
+        assemble_point<IM>(*Sp, G, gs, (int64_t)base + lane);
     }
 }
 
@@ -533,20 +677,36 @@ __device__ __forceinline__ bool point_ff(const AsmParams& P, const GridDev* G, c
     return ff_finite(pf[0]) && ff_finite(pf[1]) && ff_finite(pf[2]);
 }
 
-__device__ __forceinline__ void finish(const AsmParams& P, const GridDev* G, const SlowPoint& sp, int gd, int64_t cell,
-                                       double u, double v, double w, uint8_t st) {
+template <int IM>
+__device__ __forceinline__ void finish(const StepParams& S, const GridDev* G, const SlowPoint& sp, int gd,
+                                       int64_t cell, double u, double v, double w, uint8_t st) {
+    const AsmParams& P = S.a;
     write_donor(P, sp.t, gd, cell, u, v, w, st);
-    G[P.s[sp.si].receiver].hint[sp.node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
+    const int32_t r = P.s[sp.si].receiver;
+    G[r].hint[sp.node] = ((uint32_t)gd << kCellBits) | (uint32_t)cell;
+    if (IM) {
+        // the local coordinates as stored in the donor record (FP32 or FP64)
+        using T = typename FieldT<IM>::T;
+        const T a = P.xi_f64 ? (T)u : (T)(float)u, b = P.xi_f64 ? (T)v : (T)(float)v,
+                c = P.xi_f64 ? (T)w : (T)(float)w;
+        const InterpParams& I = S.i;
+        interp_point<T>(G[gd], G[r], I.fields[gd], I.mode, I.mf[gd], I.mf[r], I.m[gd], I.m[r], sp.node, cell, a, b, c,
+                        I.out, sp.t);
+    }
 }
 
-__device__ __forceinline__ void finish_none(const AsmParams& P, int64_t t) {
-    write_none(P, t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+template <int IM>
+__device__ __forceinline__ void finish_none(const StepParams& S, int64_t t) {
+    write_none(S.a, t, OVS_STATUS_ORPHAN | OVS_STATUS_FALLBACK);
+    if (IM) zero_point<typename FieldT<IM>::T>(S.i.out, t);
 }
 
 // Points near a face: one warp each, one lane per candidate cell.  A point whose candidates all fail (or a
 // later donor of its list) gets the warp-level exhaustive search.
-__device__ __forceinline__ void slow_near_body(const AsmParams& P, const GridDev* __restrict__ G, unsigned bid,
+template <int IM>
+__device__ __forceinline__ void slow_near_body(const StepParams& S, const GridDev* __restrict__ G, unsigned bid,
                                                unsigned nblk) {
+    const AsmParams& P = S.a;
     uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
     unsigned nref = 0, nfb = 0;
@@ -580,12 +740,12 @@ __device__ __forceinline__ void slow_near_body(const AsmParams& P, const GridDev
                 ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
             }
             if (ok) {
-                if (lane == 0) finish(P, G, sp, gd, cell, u, v, w, st);
+                if (lane == 0) finish<IM>(S, G, sp, gd, cell, u, v, w, st);
                 done = true;
                 ++nref;
             }
         }
-        if (!done && lane == 0) finish_none(P, sp.t);
+        if (!done && lane == 0) finish_none<IM>(S, sp.t);
     }
     if (P.stats && lane == 0) {
         if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
@@ -597,8 +757,10 @@ constexpr int kMaxCand = 128;
 
 // Stuck walks (points outside the grid, or where the walk gave up): one block each.  All threads filter the
 // control cell's list (box, slabs, FP32 Newton); warp 0 applies the donor predicate to the survivors.
-__device__ __forceinline__ void slow_stuck_body(const AsmParams& P, const GridDev* __restrict__ G, unsigned bid,
+template <int IM>
+__device__ __forceinline__ void slow_stuck_body(const StepParams& S, const GridDev* __restrict__ G, unsigned bid,
                                                 unsigned nblk) {
+    const AsmParams& P = S.a;
     static_assert(kMaxCand <= kSlowThreads, "one thread per candidate");
     constexpr long long kNoCellLL = 0x7FFFFFFFFFFFFFFFll;
     __shared__ uint32_t cand[kMaxCand];
@@ -686,14 +848,14 @@ __device__ __forceinline__ void slow_stuck_body(const AsmParams& P, const GridDe
             ++nfb;
             if (found) {
                 if (threadIdx.x == 0)
-                    finish(P, G, sp, gd, fcell, fuvw[0], fuvw[1], fuvw[2],
-                           OVS_STATUS_FOUND | OVS_STATUS_REFINED | OVS_STATUS_FALLBACK);
+                    finish<IM>(S, G, sp, gd, fcell, fuvw[0], fuvw[1], fuvw[2],
+                               OVS_STATUS_FOUND | OVS_STATUS_REFINED | OVS_STATUS_FALLBACK);
                 done = true;
                 ++nref;
             }
             __syncthreads();
         }
-        if (!done && threadIdx.x == 0) finish_none(P, sp.t);
+        if (!done && threadIdx.x == 0) finish_none<IM>(S, sp.t);
     }
     if (P.stats && threadIdx.x == 0) {
         if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
@@ -705,16 +867,17 @@ __device__ __forceinline__ void slow_stuck_body(const AsmParams& P, const GridDe
 // blocks the near-face points (a warp per entry).  Interleaved, the first wave of blocks holds both kinds, so
 // the long stuck walks do not keep the near-face points waiting; one kernel keeps them concurrent without a
 // second stream (or a fork in the step graph).
-__global__ void __launch_bounds__(kSlowThreads) k_slow(const AsmParams* __restrict__ Pp, const GridDev* __restrict__ G) {
-    const AsmParams& P = *Pp;
+template <int IM>
+__global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restrict__ Sp,
+                                                       const GridDev* __restrict__ G) {
     const unsigned half = gridDim.x >> 1;
-    if (blockIdx.x & 1) slow_stuck_body(P, G, blockIdx.x >> 1, half);
-    else slow_near_body(P, G, blockIdx.x >> 1, half);
+    if (blockIdx.x & 1) slow_stuck_body<IM>(*Sp, G, blockIdx.x >> 1, half);
+    else slow_near_body<IM>(*Sp, G, blockIdx.x >> 1, half);
 }
 
 }  // namespace
 
-cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const GridDev* dgrids, int nsm,
+cudaError_t launch_assemble(const StepParams* dS, int interp, uint32_t* queue_count, const GridDev* dgrids, int nsm,
                             int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev) {
     const unsigned ab = (unsigned)(nsm * (asm_bps > 0 ? asm_bps : kAsmMinBlocks));
     const unsigned sb = (unsigned)(nsm * (slow_bps > 0 ? slow_bps : 1));
@@ -722,11 +885,15 @@ cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const Gr
     cudaError_t err = cudaMemsetAsync(queue_count, 0, 3 * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    k_assemble<<<ab, kAsmThreads, 0, st>>>(dP, dgrids);
+    if (interp == 1) k_assemble<1><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+    else if (interp == 2) k_assemble<2><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+    else k_assemble<0><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    k_slow<<<2 * sb, kSlowThreads, 0, st>>>(dP, dgrids);
+    if (interp == 1) k_slow<1><<<2 * sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else if (interp == 2) k_slow<2><<<2 * sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else k_slow<0><<<2 * sb, kSlowThreads, 0, st>>>(dS, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

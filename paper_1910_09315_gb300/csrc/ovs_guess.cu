@@ -8,15 +8,12 @@
 //                    memory, weight gradients reduced per block (FP32)
 //   k_adam           Adam update of the FP32 parameters
 //   k_pack           FP32 copy of the biases and FP16 mma.sync fragments of the three layers for inference
-//   k_guess          points of a call that have no usable hint and a donor grid with a trained network, gathered
-//                    per chunk into 16-row tiles -> the network (all layers in FP16 on tensor cores, mma.sync
-//                    m16n8k16, FP32 accumulation) -> the guessed cell becomes the receiver node's hint
+//   k_guess_eval     the network on given inputs (ovs_guess_eval; the same tile code, ovs_mlp.cuh, runs inside
+//                    k_assemble for the points of a call that have no usable hint)
 //
 // Parameter layout (FP32): W1 [H x 3] row-major, b1 [H], W2 [H x H] row-major (W2[out][in]), b2 [H], W3 [3 x H],
 // b3 [3]: H*H + 8*H + 3 values.
-#include <cuda_fp16.h>
-
-#include "ovs_guess.cuh"
+#include "ovs_mlp.cuh"
 
 namespace ovs {
 
@@ -176,11 +173,6 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __re
 }
 
 // ---------------------------------------------------------------------------------------------- inference
-// FP16 pair, low half = first argument
-__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
-    __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
 
 // B fragments for mma.m16n8k16 (B[k][n]: k = 2t, 2t+1 in b0 and 2t+8, 2t+9 in b1, n = 8 * tile + lane / 4,
 // t = lane % 4), FP16:
@@ -190,11 +182,13 @@ __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
 //   layer 2: W2[n][k], two consecutive k-steps per 16-byte entry, per (n-tile, k-step pair, lane), accumulated in
 //     FP16 (its outputs feed the next FP16 operand directly);
 //   layer 3, one n-tile: n = 0-2 W3hi[n][k], 3-5 W3lo[n - 3][k], 6-7 zero; output o is column o plus column o + 3.
+// b2h: b2 as FP16 pairs (the initial values of the layer-2 FP16 accumulators).
 __global__ void k_pack(const float* __restrict__ params, int H, float* __restrict__ fw, uint2* __restrict__ w1frag,
-                       uint4* __restrict__ w2frag, uint2* __restrict__ w3frag) {
+                       uint4* __restrict__ w2frag, uint2* __restrict__ w3frag, uint32_t* __restrict__ b2h) {
     const int NP = H * H + 8 * H + 3;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     for (int q = tid; q < NP; q += nth) fw[q] = params[q];
+    for (int q = tid; q < H / 2; q += nth) b2h[q] = pack_f16(params[4 * H + H * H + 2 * q], params[4 * H + H * H + 2 * q + 1]);
     const float* W1 = params;
     const float* b1 = params + 3 * H;
     const float* W2 = params + 4 * H;
@@ -236,131 +230,6 @@ __global__ void k_pack(const float* __restrict__ params, int H, float* __restric
     }
 }
 
-__device__ __forceinline__ void mma_f16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint2 b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
-}
-
-// FP16 accumulators: d (rows g, g+8 as FP16 pairs) += A B
-__device__ __forceinline__ void mma_f16_acc16(uint32_t d[2], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                              uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f16.f16.f16.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, {%0,%1};\n"
-                 : "+r"(d[0]), "+r"(d[1])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// SiLU of an FP16 pair: z * sigmoid(z) = z/2 * (1 + tanh(z/2)), one hardware tanh for both (its error, about
-// 2^-11, is that of the FP16 rounding itself; the guess only picks the walk's start, donors do not depend on it)
-__device__ __forceinline__ uint32_t silu_h2(uint32_t zb) {
-    const __half2 h = __hmul2(*reinterpret_cast<const __half2*>(&zb), __float2half2_rn(0.5f));
-    const uint32_t hb = *reinterpret_cast<const uint32_t*>(&h);
-    uint32_t tb;
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(hb));
-    const __half2 r = __hfma2(h, *reinterpret_cast<const __half2*>(&tb), h);
-    return *reinterpret_cast<const uint32_t*>(&r);
-}
-
-// One grid's network in shared memory: the FP16 fragments k_pack wrote, b2 as FP16 pairs (the layer-2
-// accumulators start from it) and b3
-template <int H>
-struct MlpSmem {
-    uint2 w1[(H / 8) * 32];
-    uint4 w2[(H / 8) * (H / 32) * 32];
-    uint2 w3[(H / 16) * 32];
-    uint32_t b2[H / 2];
-    float4 b3;
-};
-
-template <int H>
-__device__ __forceinline__ void stage_mlp(MlpSmem<H>& S, const void* region) {
-    const float* fw = (const float*)((const char*)region + kMlpFwOffset);
-    const uint2* w1 = (const uint2*)((const char*)region + kMlpW1FragOffset);
-    const uint4* w2 = (const uint4*)((const char*)region + kMlpW2FragOffset);
-    const uint2* w3 = (const uint2*)((const char*)region + kMlpW3FragOffset);
-    for (int q = threadIdx.x; q < (H / 8) * 32; q += blockDim.x) S.w1[q] = w1[q];
-    for (int q = threadIdx.x; q < (H / 8) * (H / 32) * 32; q += blockDim.x) S.w2[q] = w2[q];
-    for (int q = threadIdx.x; q < (H / 16) * 32; q += blockDim.x) S.w3[q] = w3[q];
-    for (int q = threadIdx.x; q < H / 2; q += blockDim.x)
-        S.b2[q] = pack_f16(fw[4 * H + H * H + 2 * q], fw[4 * H + H * H + 2 * q + 1]);
-    if (threadIdx.x == 0) {
-        const float* b3 = fw + 8 * H + H * H;
-        S.b3 = make_float4(b3[0], b3[1], b3[2], 0.f);
-    }
-}
-
-// The network on a tile of 16 inputs (xin[r].xyz, one row per point) held by one warp, all three layers on tensor
-// cores (mma.sync m16n8k16, FP16 operands).  An m16n8 accumulator pair (n-tiles 2k, 2k + 1) has the layout of the
-// m16k16 A operand of the next layer's k-step k, so activations stay in registers:
-//   layer 1: x split into FP16 hi/lo against (W1hi, W1lo, b1hi, b1lo), FP32 accumulation -> z1 to ~FP32;
-//   layer 2: SiLU(z1) in FP16 against W2 in FP16, FP16 accumulators starting from b2;
-//   layer 3: SiLU(z2) in FP16 against W3 split into hi and lo columns, FP32 accumulation; y_o = column o +
-//   column o + 3 + b3_o.
-// On return, lanes with t = lane % 4 == 0 hold y for rows g and g + 8 (g = lane / 4).
-template <int H>
-__device__ __forceinline__ void mlp_tile(const MlpSmem<H>& S, const float4* xin, float y[2][3]) {
-    const int lane = (int)lane_id(), g = lane >> 2, t = lane & 3;
-    constexpr int KS = H / 16, NT = H / 8;
-    // layer-1 A fragment (columns 2t, 2t+1 in a0 row g / a1 row g+8; 2t+8, 2t+9 in a2 / a3): component t's
-    // (x_hi, x_lo) and (x_hi, 0) for t < 3, (1, 1) and (0, 0) for t = 3
-    uint32_t a1f[4];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const float4 r = xin[g + 8 * rr];
-        const float xt = t == 0 ? r.x : (t == 1 ? r.y : r.z);
-        const float xh = __half2float(__float2half_rn(xt));
-        const float xl = xt - xh;
-        a1f[rr] = t == 3 ? pack_f16(1.f, 1.f) : pack_f16(xh, xl);
-        a1f[2 + rr] = t == 3 ? 0u : pack_f16(xh, 0.f);
-    }
-    // layer 1 -> SiLU -> A fragments of layer 2
-    uint32_t A[KS][4];
-#pragma unroll
-    for (int n8 = 0; n8 < NT; ++n8) {
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_f16(c, a1f[0], a1f[1], a1f[2], a1f[3], S.w1[n8 * 32 + lane]);
-        A[n8 >> 1][(n8 & 1) * 2] = silu_h2(pack_f16(c[0], c[1]));
-        A[n8 >> 1][(n8 & 1) * 2 + 1] = silu_h2(pack_f16(c[2], c[3]));
-    }
-    // layer 2 -> SiLU -> layer 3: n-tiles 2k and 2k + 1 of layer 2 make the A fragment of layer 3's k-step k
-    float c3[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int kk = 0; kk < KS; ++kk) {
-        uint32_t a3[4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int n8 = 2 * kk + h;
-            const uint32_t bb = S.b2[4 * n8 + t];
-            uint32_t d[2] = {bb, bb};
-#pragma unroll
-            for (int kp = 0; kp < KS / 2; ++kp) {
-                const uint4 b = S.w2[(n8 * (KS / 2) + kp) * 32 + lane];
-                mma_f16_acc16(d, A[2 * kp][0], A[2 * kp][1], A[2 * kp][2], A[2 * kp][3], b.x, b.y);
-                mma_f16_acc16(d, A[2 * kp + 1][0], A[2 * kp + 1][1], A[2 * kp + 1][2], A[2 * kp + 1][3], b.z, b.w);
-            }
-            a3[2 * h] = silu_h2(d[0]);
-            a3[2 * h + 1] = silu_h2(d[1]);
-        }
-        mma_f16(c3, a3[0], a3[1], a3[2], a3[3], S.w3[kk * 32 + lane]);
-    }
-    // lane t holds columns 2t, 2t+1 of rows g (c3[0], c3[1]) and g+8 (c3[2], c3[3])
-    float s1[4], s2[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        s1[e] = __shfl_down_sync(0xffffffffu, c3[e], 1);  // columns 2, 3
-        s2[e] = __shfl_down_sync(0xffffffffu, c3[e], 2);  // columns 4, 5
-    }
-    const float4 b3 = S.b3;
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        y[rr][0] = c3[2 * rr] + s1[2 * rr + 1] + b3.x;
-        y[rr][1] = c3[2 * rr + 1] + s2[2 * rr] + b3.y;
-        y[rr][2] = s1[2 * rr] + s2[2 * rr + 1] + b3.z;
-    }
-}
-
 // network evaluation on arbitrary normalised inputs (tests and direct use)
 template <int H>
 __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ region, const float* __restrict__ xn,
@@ -389,141 +258,6 @@ __global__ void __launch_bounds__(128) k_guess_eval(const void* __restrict__ reg
             }
         }
         __syncwarp();
-    }
-}
-
-// Persistent blocks over the chunks of the sets that take a guess.  Per chunk, phase A (every thread, four points
-// each, independent loads): the points without a usable hint whose position lies in the donor grid's box are
-// gathered into shared memory (network input and receiver node); phase B (warps, 16 rows a tile): the network
-// on the gathered rows, and the guessed cell becomes the receiver node's hint.  A block stages a network only
-// when its chunk's donor grid changes.
-template <int H>
-__global__ void __launch_bounds__(128, kGuessBlocksPerSM) k_guess(const StepParams* __restrict__ Sp,
-                                                                   const GridDev* __restrict__ G) {
-    const AsmParams& P = Sp->a;
-    const GuessWork& W = Sp->w[H == 32 ? 0 : (H == 64 ? 1 : 2)];
-    const int always = P.guess_always;
-    unsigned long long* __restrict__ used = P.guess_used;
-    constexpr int kPer = kGuessChunk / 128;
-    __shared__ MlpSmem<H> S;
-    __shared__ float4 rows[kGuessChunk + 16];  // xyz = network input, w = receiver node (bits)
-    __shared__ int nrows;
-    __shared__ struct {
-        float lo[3], hi[3], centre[3], inv_half[3], Cf[3], invC[3];
-        int C[3], per[3];
-    } K;  // the chunk's donor grid: box, input normalisation, cell counts
-    const int wp = threadIdx.x >> 5, lane = (int)lane_id();
-    const int64_t nchunks = W.chunk_begin[W.nsets];
-    int staged = -1;
-    unsigned nused = 0;
-    for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-        int w = 0;
-        while (w + 1 < W.nsets && W.chunk_begin[w + 1] <= chunk) ++w;
-        const int si = W.set[w];
-        const SetDev& s = P.s[si];
-        const int gd = s.donors[0];
-        const GridDev& g = G[gd];
-        const GridDev& gr = G[s.receiver];
-        __syncthreads();  // the previous chunk's rows (and network) are no longer read
-        if (gd != staged) {
-            stage_mlp<H>(S, g.mlp);
-            staged = gd;
-        }
-        if (threadIdx.x == 0) {
-            nrows = 0;
-            const MlpHeader* hd = (const MlpHeader*)g.mlp;
-            for (int c = 0; c < 3; ++c) {
-                K.lo[c] = (float)g.lo[c];
-                K.hi[c] = (float)g.hi[c];
-                K.centre[c] = hd->centre[c];
-                K.inv_half[c] = hd->inv_half[c];
-                K.Cf[c] = (float)g.C[c];
-                K.invC[c] = 1.f / (float)g.C[c];
-                K.C[c] = g.C[c];
-                K.per[c] = g.per[c];
-            }
-        }
-        __syncthreads();
-        const int64_t nn = gr.nnodes;
-        const uint32_t ncells = (uint32_t)g.ncells;
-        uint32_t* __restrict__ hint = gr.hint;
-        const int64_t c0 = (chunk - W.chunk_begin[w]) * kGuessChunk;
-        const int64_t c1 = min(c0 + (int64_t)kGuessChunk, s.n);
-        // phase A
-        int32_t node[kPer];
-        uint32_t h[kPer];
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int64_t q = c0 + 128 * k + threadIdx.x;
-            node[k] = q < c1 ? __ldg(s.node_ids + q) : -1;
-        }
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) h[k] = (node[k] >= 0 && node[k] < nn) ? hint[node[k]] : 0u;
-        const XfFF& xf = P.xf[si];
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            bool want = false;
-            float4 r;
-            if (node[k] >= 0 && node[k] < nn) {
-                const bool valid = !always && h[k] != kNoHint && (int)(h[k] >> kCellBits) == gd &&
-                                   (h[k] & ((1u << kCellBits) - 1)) < ncells;
-                if (!valid) {
-                    // the network's input needs no more than FP32: the high parts of position and map
-                    float x[3], v[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) x[c] = __ldg(gr.xff + 2 * c * nn + node[k]);
-                    bool inside = true;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        v[c] = fmaf(xf.Mh[3 * c + 2], x[2],
-                                    fmaf(xf.Mh[3 * c + 1], x[1], fmaf(xf.Mh[3 * c], x[0], xf.th[c])));
-                        inside = inside && v[c] >= K.lo[c] && v[c] <= K.hi[c];
-                        v[c] = (v[c] - K.centre[c]) * K.inv_half[c];
-                    }
-                    r = make_float4(v[0], v[1], v[2], __int_as_float(node[k]));
-                    want = inside;
-                }
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, want);
-            int base = 0;
-            if (lane == 0 && bal) base = atomicAdd(&nrows, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (want) rows[base + __popc(bal & ((1u << lane) - 1u))] = r;
-        }
-        __syncthreads();
-        const int n = nrows;
-        if ((int)threadIdx.x < ((n + 15) & ~15) - n) rows[n + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        // phase B
-        const int t = lane & 3, gq = lane >> 2;
-        for (int t0 = 16 * wp; t0 < n; t0 += 64) {
-            float y[2][3];
-            mlp_tile<H>(S, rows + t0, y);
-            // lane 4g keeps row g, lane 4g + 1 takes row g + 8
-            float yr[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float o = __shfl_up_sync(0xffffffffu, y[1][c], 1);
-                yr[c] = t == 0 ? y[0][c] : o;
-            }
-            const int row = t0 + gq + 8 * t;
-            if (t < 2 && row < n) {
-                int ijk[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float f = fminf(fmaxf(yr[c] * K.Cf[c], -1e6f), 1e6f);
-                    if (K.per[c]) f -= K.Cf[c] * floorf(f * K.invC[c]);
-                    ijk[c] = min(max((int)floorf(f), 0), K.C[c] - 1);
-                }
-                hint[__float_as_int(rows[row].w)] =
-                    ((uint32_t)gd << kCellBits) | (uint32_t)(ijk[0] + K.C[0] * (ijk[1] + K.C[1] * ijk[2]));
-                ++nused;
-            }
-        }
-    }
-    if (used) {
-        const unsigned tot = __reduce_add_sync(0xffffffffu, nused);
-        if (lane == 0 && tot) atomicAdd(used, (unsigned long long)tot);
     }
 }
 
@@ -571,7 +305,8 @@ cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t s
     uint2* w1 = (uint2*)((char*)region + kMlpW1FragOffset);
     uint4* w2 = (uint4*)((char*)region + kMlpW2FragOffset);
     uint2* w3 = (uint2*)((char*)region + kMlpW3FragOffset);
-    k_pack<<<64, 256, 0, st>>>(params, H, fw, w1, w2, w3);
+    uint32_t* b2h = (uint32_t*)((char*)region + kMlpB2hOffset);
+    k_pack<<<64, 256, 0, st>>>(params, H, fw, w1, w2, w3, b2h);
     return cudaGetLastError();
 }
 
@@ -585,32 +320,6 @@ cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_
         case 128: k_guess_eval<128><<<blocks, 128, 0, st>>>(region, xn, n, out); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
-}
-
-void fill_guess_work(const AsmParams& P, const int* hidden, GuessWork Wk[3]) {
-    const int widths[3] = {32, 64, 128};
-    for (int h = 0; h < 3; ++h) {
-        GuessWork& W = Wk[h];
-        W.nsets = 0;
-        int64_t chunks = 0;
-        for (int s = 0; s < P.nsets; ++s) {
-            if (hidden[P.s[s].donors[0]] != widths[h] || P.s[s].n <= 0) continue;
-            W.set[W.nsets] = s;
-            W.chunk_begin[W.nsets] = chunks;
-            chunks += (P.s[s].n + kGuessChunk - 1) / kGuessChunk;
-            ++W.nsets;
-        }
-        W.chunk_begin[W.nsets] = chunks;
-    }
-}
-
-cudaError_t launch_guess(const StepParams* dS, const GridDev* dgrids, int hmask, int nsm, int bps, cudaStream_t st) {
-    // one persistent launch per network width present; its blocks walk that width's chunk list (possibly empty)
-    const unsigned blocks = (unsigned)(nsm * (bps > 0 ? bps : kGuessBlocksPerSM));
-    if (hmask & 1) k_guess<32><<<blocks, 128, 0, st>>>(dS, dgrids);
-    if (hmask & 2) k_guess<64><<<blocks, 128, 0, st>>>(dS, dgrids);
-    if (hmask & 4) k_guess<128><<<blocks, 128, 0, st>>>(dS, dgrids);
     return cudaGetLastError();
 }
 

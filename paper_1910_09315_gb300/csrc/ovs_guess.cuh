@@ -7,8 +7,8 @@
 namespace ovs {
 
 // Per-grid region (inside the grid workspace), sized for the widest network (H = 128):
-//   header | inference copy of the FP32 parameters | FP16 mma fragments of the three layers | training: FP32
-//   parameters, Adam first and second moments, gradients, loss accumulator
+//   header | inference copy of the FP32 parameters | FP16 mma fragments of the three layers | b2 as FP16 pairs |
+//   training: FP32 parameters, Adam first and second moments, gradients, loss accumulator
 struct MlpHeader {
     int32_t hidden;     // 0: no network
     int32_t ready;      // 1 once trained (or set) and packed
@@ -25,7 +25,8 @@ constexpr size_t kMlpFwOffset = 256;
 constexpr size_t kMlpW2FragOffset = kMlpFwOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpW1FragOffset = kMlpW2FragOffset + kMlpAlign(2 * kMlpMaxHidden * kMlpMaxHidden);
 constexpr size_t kMlpW3FragOffset = kMlpW1FragOffset + kMlpAlign(32 * kMlpMaxHidden);
-constexpr size_t kMlpParamsOffset = kMlpW3FragOffset + kMlpAlign(16 * kMlpMaxHidden);
+constexpr size_t kMlpB2hOffset = kMlpW3FragOffset + kMlpAlign(16 * kMlpMaxHidden);
+constexpr size_t kMlpParamsOffset = kMlpB2hOffset + kMlpAlign(2 * kMlpMaxHidden);
 constexpr size_t kMlpMOffset = kMlpParamsOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpVOffset = kMlpMOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
 constexpr size_t kMlpGOffset = kMlpVOffset + kMlpAlign(sizeof(float) * kMlpMaxParams);
@@ -42,10 +43,5 @@ cudaError_t launch_train_grad(int H, const float* params, const float* X, const 
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int np, float lr, int step, cudaStream_t st);
 cudaError_t launch_pack(const float* params, int H, void* region, cudaStream_t st);
 cudaError_t launch_guess_eval(int H, const void* region, const float* xn, int64_t n, float* out, cudaStream_t st);
-// always = 1: every point of a set whose first donor has a network gets its guess (hints ignored).
-// hmask: bit 0/1/2 for networks of width 32/64/128 present on some grid (one launch each)
-cudaError_t launch_guess(const StepParams* dS, const GridDev* dgrids, int hmask, int nsm, int bps, cudaStream_t st);
-// host side: the work lists of a call, from the set table and the grids' network widths
-void fill_guess_work(const AsmParams& P, const int* hidden, GuessWork W[3]);
 
 }  // namespace ovs

@@ -156,7 +156,28 @@ __device__ __forceinline__ int near_mask(float u, float v, float w, float tau) {
     return m;
 }
 
-enum Counter { kCtrPoints = 0, kCtrWalk, kCtrRefined, kCtrFallback, kCtrGuess, kNumCounters };
+enum Counter {
+    kCtrPoints = 0,
+    kCtrWalk,
+    kCtrRefined,
+    kCtrFallback,
+    kCtrGuess,
+    kCtrNewton,    // FP32 Newton iterations of the walk
+    kCtrWarpWalk,  // per warp and work item: the most walk steps of its lanes
+    kCtrNear,      // points queued for the near-face decision
+    kCtrStuck,     // points queued for the exhaustive search
+    kNumCounters
+};
+
+// A donor grid's learned-guess network as a call sees it (hidden = 0: none): its padded bounding box and the input
+// normalisation xn = (x - centre) * inv_half in FP32, and its region (packed fragments, ovs_guess.cuh).
+struct GuessDev {
+    float lo[3], hi[3];
+    float centre[3], inv_half[3];
+    int32_t hidden;
+    int32_t pad;
+    const void* region;
+};
 
 struct AsmParams {
     int32_t nsets;
@@ -176,11 +197,12 @@ struct AsmParams {
     unsigned long long* counters;
     int32_t* err;
     unsigned long long* guess_used;  // learned-guess statistics counter, or NULL
+    int32_t guess_mlp;               // 1: points without a usable hint start where their first donor's network says
     int32_t guess_always;            // 1: every point of a set with a network gets a guess (hints ignored)
-    int32_t pad2;
     SetDev s[OVS_MAX_SETS];
     XfFF xf[OVS_MAX_SETS];
     MotionDev m[OVS_MAX_GRIDS];
+    GuessDev gn[OVS_MAX_GRIDS];
 };
 
 struct InterpParams {
@@ -203,23 +225,12 @@ struct InterpParams {
     FieldsDev fields[OVS_MAX_GRIDS];
 };
 
-// The sets of a call whose first donor grid has a network of one width, cut into chunks of kGuessChunk points
-// (a chunk never crosses a set): chunk b is chunk b - chunk_begin[w] of set set[w].
-constexpr int kGuessChunk = 256;
-constexpr int kGuessBlocksPerSM = 8;  // k_guess: 128 threads at up to 64 registers
-struct GuessWork {
-    int32_t nsets;
-    int32_t set[OVS_MAX_SETS];
-    int64_t chunk_begin[OVS_MAX_SETS + 1];
-};
-
 // Everything a step's kernels read, in one block of device memory written by one host-to-device copy per step
 // (so that a captured step graph stays valid from one step to the next): the assembly's and the interpolation's
-// parameters and the learned guess's work lists for hidden widths 32, 64 and 128.
+// parameters.
 struct StepParams {
     AsmParams a;
     InterpParams i;
-    GuessWork w[3];
 };
 
 // error bits of the device status word
@@ -407,11 +418,12 @@ __device__ __forceinline__ void rec_box(const CellRec& r, double lo[3], double h
 
 // FP32 Newton on the monomial form.  Returns true if the last step was below tolerance.
 __device__ __forceinline__ bool newton32(const CellRec& r, float dx, float dy, float dz, float& u, float& v,
-                                         float& w, int maxit = kNewtonMaxIt32) {
+                                         float& w, int maxit = kNewtonMaxIt32, int* iters = nullptr) {
     const float* a = r.a;
     bool conv = false;
 #pragma unroll 1
     for (int it = 0; it < maxit; ++it) {
+        if (iters) ++*iters;
         float uv = u * v, vw = v * w, uw = u * w, uvw = uv * w;
         float F[3], Ju[3], Jv[3], Jw[3];
 #pragma unroll
@@ -656,11 +668,10 @@ cudaError_t launch_bin_fill(const GridDev& g, const int32_t* start, uint32_t* cu
                             cudaStream_t st);
 size_t scan_scratch_elems(int64_t n);
 // ev: 3 optional events (before the fast kernel, after it, after the slow kernels); 2 for interpolation.
-// side/fork/join: a second stream and two events for running the two slow-path kernels concurrently (null:
-// everything on st).
-// asm_bps / slow_bps: blocks per SM of the persistent assembly grid and of each half of the slow-path grid
-// (0: defaults)
-cudaError_t launch_assemble(const AsmParams* dP, uint32_t* queue_count, const GridDev* dgrids, int nsm,
+// interp: 0 assembly only; 1 / 2: the kernels also interpolate FP32 / FP64 fields (dS->i) for every point they
+// decide.  asm_bps / slow_bps: blocks per SM of the persistent assembly grid and of each half of the slow-path
+// grid (0: defaults)
+cudaError_t launch_assemble(const StepParams* dS, int interp, uint32_t* queue_count, const GridDev* dgrids, int nsm,
                             int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev);
 // blocks of k_interp resident per SM (occupancy calculator), or a negative CUDA error
 int interp_default_blocks_per_sm(bool f64);

@@ -58,6 +58,7 @@ EXPORTS = [
     "ovs_hole_cut_many",
     "ovs_get_donors",
     "ovs_set_donors",
+    "ovs_autotune_guess",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -101,7 +102,8 @@ class ovs_tuning(ctypes.Structure):
 
 class ovs_stats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("refined", ctypes.c_int64),
-                ("fallback", ctypes.c_int64), ("guess_used", ctypes.c_int64)]
+                ("fallback", ctypes.c_int64), ("guess_used", ctypes.c_int64), ("newton_iterations", ctypes.c_int64),
+                ("warp_walk_steps", ctypes.c_int64), ("near_face", ctypes.c_int64), ("stuck", ctypes.c_int64)]
 
 
 class ovs_train_desc(ctypes.Structure):
@@ -173,6 +175,9 @@ def load(path: Optional[str] = None):
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_autotune": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors), ctypes.POINTER(ovs_fields),
                          I32, ctypes.POINTER(ovs_fields_out), I32, ctypes.POINTER(ovs_tuning)],
+        "ovs_autotune_guess": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors),
+                               ctypes.POINTER(ovs_fields), I32, ctypes.POINTER(ovs_fields_out), I32, V, V, I32, V,
+                               ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -326,6 +331,24 @@ def ovs_autotune(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int
     _check(ctx, load().ovs_autotune(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
                                     ctypes.byref(out) if out is not None else None, int(reps), ctypes.byref(best)))
     return best
+
+
+def ovs_autotune_guess(ctx, sets, nsets: int, donors: ovs_donors, fields, nfields: int, out, hidden, params,
+                       reps: int):
+    """hidden: candidate widths (0 = no networks); params: per candidate a list over grids of device parameter
+    pointers (int, 0 for none).  Returns (best index, [(cold ms, warm ms) per candidate])."""
+    nc = len(hidden)
+    ng = len(params[0]) if params else 0
+    h = (ctypes.c_int32 * nc)(*[int(x) for x in hidden])
+    flat = [int(p) for cand in params for p in cand]
+    parr = (ctypes.c_void_p * max(1, len(flat)))(*[p or None for p in flat]) if flat else None
+    ms = (ctypes.c_float * (2 * nc))()
+    best = I32()
+    assert not flat or len(flat) == nc * ng
+    _check(ctx, load().ovs_autotune_guess(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
+                                          ctypes.byref(out) if out is not None else None, nc, h, parr, int(reps), ms,
+                                          ctypes.byref(best)))
+    return best.value, [(ms[2 * k], ms[2 * k + 1]) for k in range(nc)]
 
 
 def ovs_assemble_noalloc(ctx, sets, nsets: int, donors: ovs_donors):
@@ -583,6 +606,21 @@ class Context:
         else:
             best = ovs_autotune(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), None, 0, None, reps)
         return {k: getattr(best, k) for k, _ in ovs_tuning._fields_}
+
+    def autotune_guess(self, sets, fields, hidden, params, donors=None, out=None, reps: int = 3,
+                       xi_dtype: int = OVS_F32):
+        """ovs_autotune_guess on this call: hidden = candidate widths (0 = no networks), params[k][g] = a device
+        FP32 parameter tensor of grid g for candidate k (or None).  Returns (chosen index, [(cold ms, warm ms)])."""
+        n = sum(int(s[1].numel()) for s in sets)
+        if donors is None:
+            donors = self.alloc_donors(n, xi_dtype)
+        ptrs = [[(p.data_ptr() if p is not None else 0) for p in cand] for cand in params]
+        if fields is not None:
+            farr, o, out = self._fields_structs(fields, n, out)
+            return ovs_autotune_guess(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), farr,
+                                      len(self.grids), o, hidden, ptrs, reps)
+        return ovs_autotune_guess(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), None, 0, None,
+                                  hidden, ptrs, reps)
 
     def add_surface(self, body_gid: int, V, T) -> int:
         """ovs_create_surface of a closed triangulated body surface (host V (nv, 3), T (nt, 3)) fixed in grid

@@ -193,3 +193,46 @@ def test_trained_guess_gains_on_cold_start(torch_cuda):
           sb["guess_used"])
     assert sb["guess_used"] > 600_000
     assert sb["walk_steps"] < sa["walk_steps"]
+
+
+def test_school_learned_guess_in_the_fused_call(torch_cuda):
+    """Eight fish with networks of two widths (32 on even fish, 128 on odd ones, so one call runs both tile codes
+    and a warp can meet two networks at a set boundary): the learned start, cold (network for every point that
+    has no previous donor) and warm, gives the plain start's donors bit for bit and its fields to within the
+    parity tolerance (a different start can leave the FP32 local coordinates different in their last bits)."""
+    from harness import F_TOL, W_TOL, weights
+
+    sc = gen.config(3)
+    m0 = sc.motion(4)
+    f0 = sc.fringe_sets(4, m0)
+    n = sum(len(s.node_ids) for s in f0) + 1024
+    plain = GpuScene(sc, max_points=n)
+    learned = GpuScene(sc, max_points=n)
+    rng = np.random.default_rng(3)
+    bodies = [gi for gi, g in enumerate(sc.grids) if g.role == 1]
+    for gi in bodies:
+        H = 32 if gi % 2 == 0 else 128
+        cells, xi = gen.mlp_training_samples(3, sc.grids[gi], 200_000)
+        learned.ctx.train_guess(gi, cells, xi.astype(np.float32), flat(random_params(rng, H)).astype(np.float32),
+                                hidden=H, epochs=6, batch=8192, lr=3e-3)
+    plain.ctx.set_options(guess=ovs.OVS_GUESS_HINT)
+    learned.ctx.set_options(guess=ovs.OVS_GUESS_MLP, collect_stats=1)
+
+    def fused(scene, m, fs):
+        scene.set_motion(m)
+        d, out = scene.ctx.assemble_interpolate(scene.upload_sets(fs), scene.fields)
+        scene.ctx.sync()
+        return GpuScene.to_numpy(d, out)
+
+    used = 0
+    for step in (4, 5, 6):  # cold, then warm twice
+        m, fs = sc.motion(step), sc.fringe_sets(step)
+        a, b = fused(plain, m, fs), fused(learned, m, fs)
+        assert np.array_equal(a["grid"], b["grid"]) and np.array_equal(a["cell"], b["cell"]), step
+        assert np.array_equal(a["status"] & 15, b["status"] & 15), step
+        found = (a["status"] & 15) == 0
+        assert np.abs(weights(a["xi"][found]) - weights(b["xi"][found])).max() <= W_TOL[ovs.OVS_F32]
+        scale = np.maximum(np.abs(a["q"]), 1.0)
+        assert (np.abs(a["q"] - b["q"]) / scale).max() <= 10 * F_TOL[np.float32], step
+        used += learned.ctx.stats(reset=True)["guess_used"]
+    assert used > 50_000

@@ -30,10 +30,15 @@ def sampled(fsets, frac, seed):
             for s in fsets]
 
 
-def check_step(sc, scene, ref, step, frac, seed, label):
+def check_step(sc, scene, ref, step, frac, seed, label, fused=False):
     m = sc.motion(step)
     fsets = sc.fringe_sets(step, m)
-    _, d, out = scene.step(m, fsets)
+    if fused:  # ovs_assemble_interpolate: one pass per point
+        scene.set_motion(m)
+        d, out = scene.ctx.assemble_interpolate(scene.upload_sets(fsets), scene.fields, xi_dtype=scene.xi_dtype)
+        scene.ctx.sync()
+    else:
+        _, d, out = scene.step(m, fsets)
     res = GpuScene.to_numpy(d, out)
     parts = split(res, [len(s.node_ids) for s in fsets])
     sample = sampled(fsets, frac, seed)
@@ -70,13 +75,28 @@ def test_school_of_8(torch_cuda):
     assert checked > 200_000
 
 
+def test_school_of_8_fused_call(torch_cuda):
+    """The step as the bench runs it: donors and fields from ovs_assemble_interpolate, cold then warm."""
+    sc = gen.config(3)
+    n = max(sum(len(s.node_ids) for s in sc.fringe_sets(t)) for t in (2, 3))
+    scene = GpuScene(sc, max_points=n + 1024)
+    ref = OracleScene(sc)
+    checked = 0
+    for step in (2, 3):
+        fsets, parts, total = check_step(sc, scene, ref, step, 0.1, 200 + step, f"school8 fused step {step}",
+                                         fused=True)
+        checked += total
+        assert body_to_body_found_in_body(fsets, parts) > 0
+    assert checked > 100_000
+
+
 @pytest.mark.slow
 def test_school_of_16_sampled(torch_cuda):
     sc = gen.config(4)
     m = sc.motion(0)
     n = sum(len(s.node_ids) for s in sc.fringe_sets(0, m))
     scene = GpuScene(sc, max_points=n + 1024)
-    fsets, parts, total = check_step(sc, scene, OracleScene(sc), 0, 0.01, 7, "school16 step 0")
+    fsets, parts, total = check_step(sc, scene, OracleScene(sc), 0, 0.01, 7, "school16 step 0", fused=True)
     assert len(fsets) > 32
     assert total > 20_000
     assert body_to_body_found_in_body(fsets, parts) > 0
