@@ -288,6 +288,27 @@ def body_surface(g: Grid):
 # ----------------------------------------------------------------------------
 # fringe-set construction (input selection)
 # ----------------------------------------------------------------------------
+def index_box_surface(dims: Sequence[int], periodic: Sequence[bool], lo: Sequence[int], hi: Sequence[int]):
+    """The closed surface of the index box of nodes lo[m] .. hi[m] (cells lo[m] .. hi[m]-1) as faces (id = 3 * base
+    node + d: the face of constant index along d spanned by the axes d+1, d+2 mod 3) with signs +1 on the box's
+    upper-index faces and -1 on its lower ones (outward on a right-handed grid).  An axis given as lo = 0,
+    hi = n on a periodic axis wraps around: it has no end faces.  Returns (faces int64, signs int8)."""
+    n = list(dims)
+    faces, signs = [], []
+    for d in range(3):
+        a, b = (d + 1) % 3, (d + 2) % 3
+        if periodic[d] and lo[d] == 0 and hi[d] == n[d]:
+            continue
+        for side, sgn in ((lo[d], -1), (hi[d], 1)):
+            for ib in range(lo[b], hi[b]):
+                for ia in range(lo[a], hi[a]):
+                    q = [0, 0, 0]
+                    q[d], q[a], q[b] = side, ia, ib
+                    faces.append(3 * (q[0] + n[0] * (q[1] + n[1] * q[2])) + d)
+                    signs.append(sgn)
+    return np.array(faces, dtype=np.int64), np.array(signs, dtype=np.int8)
+
+
 def outer_layers(g: Grid, layers: int, axes: Sequence[int]) -> np.ndarray:
     """Node ids within ``layers`` nodes of the low/high boundary on any of ``axes``
     (periodic axes have no boundary and are skipped)."""

@@ -19,6 +19,8 @@ Parts (each cites the passage it follows):
   frame velocity = translation + Omega x X); ABSOLUTE u_r = R_r^T R_d u_d
   (Sec. 2.3.1 eq. "velocity_non", with Q = R^T).  Pressure passes unchanged.
 * ``mlp_*`` -- forward/backward of the 3-64-64-3 SiLU guess network in FP64.
+* ``face_fluxes``, ``mass_correct`` -- contravariant fluxes U = u . S through receiver faces (Sec. 2.1
+  eq. "flux") and the mass-conservation correction over closed interfaces (Sec. 2.4 "Mass conservation").
 
 Parity pins live in ``tests/test_oracle_pins.py``.  The config-level donor
 results have no printed values in the paper: "parity unpinned" beyond the
@@ -349,3 +351,67 @@ def adam_step(params: dict, grads: dict, m: dict, v: dict, t: int, lr: float, b1
         mh = m[k] / (1 - b1 ** t)
         vh = v[k] / (1 - b2 ** t)
         params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+# ----------------------------------------------------------------------------- fluxes at the receivers
+# Sec. 2.1 eq. "flux": the contravariant flux U^r = u_q xi^r_q / J through a face of constant xi^r, where
+# xi^r_q / J is that face's area vector (per unit of the other two curvilinear coordinates).  On a structured grid
+# a face is a quadrilateral of four nodes; its area vector is half the cross product of its diagonals (the
+# vector area of the bilinear face), and the velocity on it is the mean of its four corners (Sec. 2.3.1, last
+# sentence: the flux of each recipient face from the interpolated velocities).
+# Sec. 2.4 "Mass conservation": the fluxes through a closed interface must sum to zero; the imbalance of the
+# reconstructed fluxes is removed by a correction.  Reading (the paper defers the details to its earlier work):
+# the net outward flux is subtracted from the faces in proportion to their areas.
+def face_nodes(dims, periodic, face_id: int):
+    """Face id = 3 * (node id of its base corner) + d: the face of constant index along axis d spanned by the
+    two axes a = d+1, b = d+2 (mod 3).  Its corners in order: base, base + e_a, base + e_a + e_b, base + e_b (node
+    ids, wrapped on periodic axes).  Returns None if the face leaves the grid."""
+    n = list(dims)
+    node, d = divmod(int(face_id), 3)
+    ijk = [node % n[0], (node // n[0]) % n[1], node // (n[0] * n[1])]
+    a, b = (d + 1) % 3, (d + 2) % 3
+    out = []
+    for da, db in ((0, 0), (1, 0), (1, 1), (0, 1)):
+        q = list(ijk)
+        q[a] += da
+        q[b] += db
+        for m in range(3):
+            if q[m] == n[m]:
+                if not periodic[m]:
+                    return None
+                q[m] = 0
+        out.append(q[0] + n[0] * (q[1] + n[1] * q[2]))
+    return out
+
+
+def face_area_vector(xyz: np.ndarray, corners) -> np.ndarray:
+    """Half the cross product of the diagonals (corner 2 - corner 0) x (corner 3 - corner 1)."""
+    x0, x1, x2, x3 = (xyz[c] for c in corners)
+    return 0.5 * np.cross(x2 - x0, x3 - x1)
+
+
+def face_fluxes(dims, periodic, xyz: np.ndarray, vel: np.ndarray, faces) -> np.ndarray:
+    """U_f = (mean of the corner velocities) . S_f for each face id (vel: (n_nodes, 3) in the grid's frame)."""
+    out = np.zeros(len(faces))
+    for k, f in enumerate(faces):
+        c = face_nodes(dims, periodic, f)
+        out[k] = np.dot(vel[c].mean(axis=0), face_area_vector(xyz, c))
+    return out
+
+
+def mass_correct(dims, periodic, xyz: np.ndarray, flux: np.ndarray, faces, signs, surf_start):
+    """For each closed surface s (faces surf_start[s] .. surf_start[s+1]-1, sign +1 where the face's area vector
+    points out of the enclosed region): net = sum of sign * U, A = sum of |S|; each face's flux becomes
+    U - sign * net * |S| / A, so that the corrected net flux is zero.  Returns (corrected fluxes, nets, areas)."""
+    flux = np.array(flux, dtype=np.float64)
+    nets, areas = [], []
+    for s in range(len(surf_start) - 1):
+        sl = slice(surf_start[s], surf_start[s + 1])
+        mag = np.array([np.linalg.norm(face_area_vector(xyz, face_nodes(dims, periodic, f))) for f in faces[sl]])
+        sg = np.asarray(signs[sl], dtype=np.float64)
+        net = float(np.sum(sg * flux[sl]))
+        A = float(np.sum(mag))
+        flux[sl] = flux[sl] - sg * net * mag / A
+        nets.append(net)
+        areas.append(A)
+    return flux, np.array(nets), np.array(areas)
