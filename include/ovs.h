@@ -193,6 +193,21 @@ int ovs_grid_workspace_size(const ovs_grid_desc* desc, size_t* bytes);
  * stream.  Grid ids are 0, 1, 2, ... in creation order.  Motion starts as the identity. */
 int ovs_create_grid(ovs_ctx* ctx, const ovs_grid_desc* desc, void* dworkspace, size_t bytes, int32_t* grid_id);
 
+/* Cells that overlap one another.  The fast path takes a point's donor from the walk as soon as the point lies
+ * clear (by more than the FP32 error bound) of every face of a cell, and near a face it tests only the cells
+ * sharing that face: this is the lowest-id rule only if no other cell of the grid holds the point, i.e. if the
+ * grid's cells do not overlap.  ovs_create_grid classifies every cell by the Jacobian determinants of its
+ * trilinear map at its 8 corners (FP64): all positive, all negative, or mixed / zero (folded or degenerate); a
+ * grid with folded cells or with cells of both signs may overlap itself and is searched exhaustively: every
+ * point the walk finds in it goes to the lowest-id search of its control cell (slower, same rule).
+ * ovs_grid_check: the three counts (cells[3]: positive, negative, folded) and whether the grid is searched
+ * exhaustively (*overlap; either pointer may be NULL).  ovs_set_grid_overlap: the caller's statement for grids
+ * that overlap without folding (e.g. a periodic seam whose end cells overlap, a C-grid wake cut): 1 = search
+ * exhaustively, 0 = the cells do not overlap (refused, OVS_ERR_ARG, for a grid with folded cells).
+ * Synchronises the stream.  Errors: OVS_ERR_ARG (unknown grid, flag not 0 or 1). */
+int ovs_grid_check(const ovs_ctx* ctx, int32_t grid_id, int64_t cells[3], int32_t* overlap);
+int ovs_set_grid_overlap(ovs_ctx* ctx, int32_t grid_id, int32_t overlap);
+
 /* Set a grid's rigid frame (Sec. 2.1, Fig. "non-inertial"): R (row-major 3x3, body -> inertial, must be
  * orthogonal with det +1 to 1e-12), origin c, translational velocity V and angular velocity omega (inertial
  * components).  Host arrays; takes effect for later calls. */
@@ -364,6 +379,29 @@ int ovs_get_tuning(const ovs_ctx* ctx, ovs_tuning* t);
 int ovs_autotune(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const ovs_donors* out,
                  const ovs_fields* fields, int32_t nfields, const ovs_fields_out* fout, int32_t reps,
                  ovs_tuning* best);
+
+/* Fluxes at the receivers and mass conservation over closed interfaces (Sec. 2.1 eq. "flux": the contravariant
+ * flux U^r = u_q xi^r_q / J through a face of constant xi^r; Sec. 2.3.1: fluxes of the recipient faces from the
+ * interpolated, frame-transformed velocities; Sec. 2.4 "Mass conservation": the fluxes through a closed interface
+ * must sum to zero, so their imbalance is removed by a correction).
+ *   Face id = 3 * (node id of its base corner) + d: the face of constant index along axis d spanned by the axes
+ *   a = d+1 and b = d+2 (mod 3); corners base, base + e_a, base + e_a + e_b, base + e_b (wrapped on periodic
+ *   axes).  Its area vector S = (corner 2 - corner 0) x (corner 3 - corner 1) / 2 (FP64, from the grid's own
+ *   coordinates; it points toward increasing index d on a right-handed grid); the velocity on it is the mean of its
+ *   corners' values; its flux U = u . S, in the grid's own frame.
+ * faces: device int64 [nfaces]; signs: device int8 [nfaces], +1 where S points out of the region a surface encloses,
+ * -1 where it points in (NULL: all +1); vel: the grid's node velocities u, v, w (p unused; FP32 or FP64, stride as
+ * in ovs_fields; for a receiver grid, its fringe nodes hold the interpolated values); flux: device [nfaces] of vel's
+ * dtype, the faces' fluxes U (not multiplied by the sign).  Closed surfaces: surface s is faces surf_start[s] ..
+ * surf_start[s+1]-1 (host int64 [nsurf + 1], nondecreasing, within [0, nfaces]; faces outside every surface only
+ * get their flux), at most 64; net: device FP64 [2 nsurf]: the net outward flux sum(sign U) before any correction
+ * and the total area sum |S|, summed in a fixed order (reproducible).  correct = 1: each face of surface s then
+ * gets U - sign * net * |S| / area (the imbalance taken out in proportion to face area), after which the surface's
+ * net flux is zero.  Enqueued on the context stream; a face id that leaves the grid is reported by ovs_sync (its
+ * flux 0).  Errors: OVS_ERR_ARG (unknown grid, NULL arrays, bad surf_start, correct without surfaces). */
+int ovs_interface_flux(ovs_ctx* ctx, int32_t grid_id, int64_t nfaces, const int64_t* faces, const int8_t* signs,
+                       int32_t nsurf, const int64_t* surf_start, const ovs_fields* vel, void* flux, double* net,
+                       int32_t correct);
 
 /* Autotuner of the learned guess (its network width, or none): ncand candidates, candidate k = networks of width
  * hidden[k] (32, 64 or 128; 0 = no networks, the plain start from hints and control cells), with the device FP32

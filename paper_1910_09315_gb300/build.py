@@ -13,7 +13,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libovs.so")
-SOURCES = ["ovs_api.cu", "ovs_grid.cu", "ovs_assemble.cu", "ovs_interp.cu", "ovs_guess.cu", "ovs_matrix.cu", "ovs_hole.cu"]
+SOURCES = ["ovs_api.cu", "ovs_grid.cu", "ovs_assemble.cu", "ovs_interp.cu", "ovs_guess.cu", "ovs_matrix.cu", "ovs_hole.cu",
+           "ovs_flux.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

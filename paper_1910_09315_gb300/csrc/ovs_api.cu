@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "ovs_flux.cuh"
 #include "ovs_guess.cuh"
 #include "ovs_hole.cuh"
 #include "ovs_matrix.cuh"
@@ -31,6 +32,7 @@ struct GridHost {
     size_t ws_bytes;
     int64_t nbins;
     int64_t nreg;
+    int64_t orient[3];  // cells right-handed, left-handed, folded or degenerate (corner Jacobians at creation)
 };
 
 }  // namespace
@@ -144,7 +146,7 @@ GridLayout grid_layout(const ovs_grid_desc& d) {
     L.scan = off;
     off = align_up(off + scan_scratch_elems(L.nbins_max) * 4);
     L.out9 = off;
-    off = align_up(off + 9 * sizeof(double));
+    off = align_up(off + 9 * sizeof(double) + 3 * sizeof(unsigned long long));
     L.total = off;
     return L;
 }
@@ -410,12 +412,17 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
     g.xff = (const float*)(base + L.xff);
     g.mlp = base + L.mlp;
     double* out9 = (double*)(base + L.out9);
+    unsigned long long* orient = (unsigned long long*)(out9 + 9);
     int nblk = (int)std::min<int64_t>(kReduceBlocks, (L.ncells + 255) / 256);
     OVS_CUDA(c, launch_build_records(g, (CellRec*)(base + L.rec), (float*)(base + L.xff),
-                                     (double*)(base + L.partials), nblk, out9, c->stream));
+                                     (double*)(base + L.partials), nblk, out9, orient, c->stream));
     double h9[9];
+    unsigned long long ho[3];
     OVS_CUDA(c, cudaMemcpyAsync(h9, out9, sizeof h9, cudaMemcpyDeviceToHost, c->stream));
+    OVS_CUDA(c, cudaMemcpyAsync(ho, orient, sizeof ho, cudaMemcpyDeviceToHost, c->stream));
     OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+    // cells of both handednesses, or folded ones: the grid may overlap itself
+    g.overlap = (ho[2] > 0 || (ho[0] > 0 && ho[1] > 0)) ? 1 : 0;
     double ext_max = 0;
     for (int a = 0; a < 3; ++a) {
         if (!isfinite(h9[a]) || !isfinite(h9[3 + a]))
@@ -475,12 +482,35 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
     c->gh[id].ws = dws;
     c->gh[id].ws_bytes = bytes;
     c->gh[id].nreg = nreg;
+    for (int q = 0; q < 3; ++q) c->gh[id].orient[q] = (int64_t)ho[q];
     identity_motion(c->motion[id]);
     OVS_CUDA(c, cudaMemcpyAsync(c->d_grids + id, &c->grids[id], sizeof(GridDev), cudaMemcpyHostToDevice, c->stream));
     OVS_CUDA(c, cudaStreamSynchronize(c->stream));
     OVS_CUDA(c, cudaGetLastError());
     c->ngrids = id + 1;
     *grid_id = id;
+    return OVS_OK;
+}
+
+int ovs_grid_check(const ovs_ctx* c, int32_t gid, int64_t cells[3], int32_t* overlap) {
+    if (!c || gid < 0 || gid >= c->ngrids) return OVS_ERR_ARG;
+    if (cells)
+        for (int q = 0; q < 3; ++q) cells[q] = c->gh[gid].orient[q];
+    if (overlap) *overlap = c->grids[gid].overlap;
+    return OVS_OK;
+}
+
+int ovs_set_grid_overlap(ovs_ctx* c, int32_t gid, int32_t overlap) {
+    if (!c) return OVS_ERR_ARG;
+    if (gid < 0 || gid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", gid);
+    if (overlap != 0 && overlap != 1) return fail(c, OVS_ERR_ARG, "overlap must be 0 or 1");
+    const int64_t* o = c->gh[gid].orient;
+    if (!overlap && (o[2] > 0 || (o[0] > 0 && o[1] > 0)))
+        return fail(c, OVS_ERR_ARG, "grid %d has folded cells: its cells may overlap", gid);
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    c->grids[gid].overlap = overlap;
+    OVS_CUDA(c, cudaMemcpyAsync(c->d_grids + gid, &c->grids[gid], sizeof(GridDev), cudaMemcpyHostToDevice, c->stream));
+    OVS_CUDA(c, cudaStreamSynchronize(c->stream));
     return OVS_OK;
 }
 
@@ -1315,6 +1345,44 @@ int ovs_autotune(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const ov
         *best = cur;
         best->launch = launch;
     }
+    return OVS_OK;
+}
+
+int ovs_interface_flux(ovs_ctx* c, int32_t gid, int64_t nfaces, const int64_t* faces, const int8_t* signs,
+                       int32_t nsurf, const int64_t* surf_start, const ovs_fields* vel, void* flux, double* net,
+                       int32_t correct) {
+    if (!c) return OVS_ERR_ARG;
+    if (!c->ws) return fail(c, OVS_ERR_STATE, "no workspace attached");
+    if (gid < 0 || gid >= c->ngrids) return fail(c, OVS_ERR_ARG, "grid %d does not exist", gid);
+    if (nfaces < 0 || (nfaces > 0 && (!faces || !flux))) return fail(c, OVS_ERR_ARG, "faces / flux");
+    if (!vel || !vel->u || !vel->v || !vel->w) return fail(c, OVS_ERR_ARG, "velocity arrays");
+    if (vel->dtype != OVS_F32 && vel->dtype != OVS_F64) return fail(c, OVS_ERR_ARG, "velocity dtype");
+    if (vel->stride < 0) return fail(c, OVS_ERR_ARG, "velocity stride %d", vel->stride);
+    if (nsurf < 0 || nsurf > kMaxFluxSurfaces) return fail(c, OVS_ERR_ARG, "nsurf = %d (0..%d)", nsurf, kMaxFluxSurfaces);
+    if (nsurf > 0 && (!surf_start || !net)) return fail(c, OVS_ERR_ARG, "surf_start / net");
+    if (correct && nsurf == 0) return fail(c, OVS_ERR_ARG, "a correction needs at least one closed surface");
+    FluxParams P;
+    memset(&P, 0, sizeof P);
+    for (int s = 0; s < nsurf; ++s)
+        if (surf_start[s] < 0 || surf_start[s + 1] < surf_start[s] || surf_start[s + 1] > nfaces)
+            return fail(c, OVS_ERR_ARG, "surf_start must be nondecreasing within [0, nfaces]");
+    for (int s = 0; nsurf > 0 && s <= nsurf; ++s) P.surf_start[s] = surf_start[s];
+    P.grid = gid;
+    P.nsurf = nsurf;
+    P.nfaces = nfaces;
+    P.faces = faces;
+    P.signs = signs;
+    P.vel.f[0] = vel->u;
+    P.vel.f[1] = vel->v;
+    P.vel.f[2] = vel->w;
+    P.vel.f[3] = vel->u;
+    P.vel.stride = vel->stride > 1 ? vel->stride : 1;
+    P.flux = flux;
+    P.net = net;
+    P.err = c->d_err;
+    if (nfaces == 0 && nsurf == 0) return OVS_OK;
+    OVS_CUDA(c, cudaSetDevice(c->device));
+    OVS_CUDA(c, launch_flux(P, vel->dtype == OVS_F64, c->d_grids, c->nsm, correct != 0, c->stream));
     return OVS_OK;
 }
 

@@ -195,7 +195,7 @@ __device__ __forceinline__ void guess_tiles(const GuessDev& gn, const GridDev& g
 // Learned initial guess for the lanes with `want` (warp-collective: every lane calls it).  The lanes are grouped by
 // their donor grid's network (a warp's 32 points are consecutive in the call, so they usually share one set); each
 // group's inputs go to the warp's shared rows, 16 to a tensor-core tile.  Returns the guessed cell, or -1.
-__device__ __forceinline__ int64_t learned_guess(const AsmParams& P, const GridDev* __restrict__ G, GuessStage& st,
+__device__ __noinline__ int64_t learned_guess(const AsmParams& P, const GridDev* __restrict__ G, GuessStage& st,
                                                  bool want, int gd0, const float xn[3]) {
     const unsigned lane = lane_id();
     int64_t cell = -1;
@@ -239,8 +239,17 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
     int32_t node = -1;
     bool node_ok = false;
     ff xd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    // the set of point t: lane 0 searches the set table for the warp's first point, the other lanes step forward
+    // from there (a work item of 32 consecutive points rarely crosses a set boundary)
+    {
+        const int64_t t0 = __shfl_sync(0xffffffffu, t, 0);
+        int s0 = 0;
+        if (lane_id() == 0) s0 = find_set(P.s, P.nsets, t0 < P.total ? t0 : P.total - 1);
+        si = __shfl_sync(0xffffffffu, s0, 0);
+        if (active)
+            while (si + 1 < P.nsets && P.s[si + 1].begin <= t) ++si;
+    }
     if (active) {
-        si = find_set(P.s, P.nsets, t);
         const SetDev& s = P.s[si];
         node = __ldg(s.node_ids + (t - s.begin));
         const GridDev& gr = G[s.receiver];
@@ -359,7 +368,13 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
             }
             e.t = (int32_t)t;
             e.di = di;
-            if (r == kWalkFound) {
+            if (r == kWalkFound && g.overlap) {
+                // cells of this grid may overlap: a lower cell elsewhere may hold the point too, so the
+                // exhaustive lowest-id search of the control cell decides
+                slow = true;
+                e.cell = -1;
+                e.xi[0] = e.xi[1] = e.xi[2] = 0.5f;
+            } else if (r == kWalkFound) {
                 const int mask = near_mask(u, v, w, tau);
                 // clear of every face: the only cell of this grid holding the point; blanked -> next donor grid
                 if (mask == 0 && !P.xi_f64 && blocked) continue;
@@ -535,7 +550,7 @@ constexpr int kSlowWarps = kSlowThreads / 32;
 // 1e-3 outside [0,1]^3 (the same iteration in FP32 pairs or FP64 from the same start follows it to within
 // rounding, ~1e-5 in local coordinates for the cells accepted here, so it cannot end in the donor window).
 // On pass, xi holds the FP32 iterate, the start of the donor predicate.
-__device__ __forceinline__ bool exhaustive_filter(const GridDev& g, const ff pf[3], uint32_t c, float xi[3]) {
+__device__ __noinline__ bool exhaustive_filter(const GridDev& g, const ff pf[3], uint32_t c, float xi[3]) {
     CellRec rec;
     load_rec(g.rec, c, rec);
     float d[3];

@@ -34,13 +34,21 @@ template <typename T>
 __device__ __forceinline__ void gather8(const GridDev& g, const FieldsDev& F, int64_t cell, T u, T v, T w, T q[4]) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
+    // corner a = node of (i + di, j + dj, k + dk): the cell's first node plus one offset per set bit (an index
+    // that reaches n is on a periodic axis and wraps to 0)
+    const int64_t n0 = g.n[0], n01 = (int64_t)g.n[0] * g.n[1];
+    const int64_t base = (int64_t)i + n0 * ((int64_t)j + (int64_t)g.n[1] * k);
+    const int64_t oi = i + 1 == g.n[0] ? -(int64_t)i : 1;
+    const int64_t oj = j + 1 == g.n[1] ? -(int64_t)j * n0 : n0;
+    const int64_t ok = k + 1 == g.n[2] ? -(int64_t)k * n01 : n01;
+    auto corner = [&](int a) { return base + ((a & 1) ? oi : 0) + ((a & 2) ? oj : 0) + ((a & 4) ? ok : 0); };
     q[0] = q[1] = q[2] = q[3] = (T)0;
     if (F.rec4) {
         // one (u, v, w, p) record per corner: one 16-byte load (FP32) or two (FP64); the sums as below
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             T wa = ((a & 1) ? u : (T)1 - u) * ((a & 2) ? v : (T)1 - v) * ((a & 4) ? w : (T)1 - w);
-            const int64_t nd = corner_node(g, i, j, k, a);
+            const int64_t nd = corner(a);
             T r[4];
             if constexpr (sizeof(T) == 4) {
                 const float4 x = __ldg(reinterpret_cast<const float4*>(F.f[0]) + nd);
@@ -60,7 +68,7 @@ __device__ __forceinline__ void gather8(const GridDev& g, const FieldsDev& F, in
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             T wa = ((a & 1) ? u : (T)1 - u) * ((a & 2) ? v : (T)1 - v) * ((a & 4) ? w : (T)1 - w);
-            const int64_t nd = corner_node(g, i, j, k, a) * st;
+            const int64_t nd = corner(a) * st;
 #pragma unroll
             for (int c = 0; c < 4; ++c) q[c] += wa * __ldg(f[c] + nd);
         }

@@ -41,8 +41,32 @@ __device__ __forceinline__ void split_store(double v, float* hi, float* lo) {
     *lo = (float)(v - (double)h);
 }
 
+// Orientation of a cell from the Jacobian determinants of its trilinear map at its 8 corners (FP64): +1 all
+// positive, -1 all negative, 0 mixed or zero (a folded or degenerate cell).
+__device__ __forceinline__ int cell_orientation(const double X[8][3]) {
+    int pos = 0, neg = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        double e[3][3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const int b = a ^ (1 << m);
+            const double s = (a >> m) & 1 ? -1.0 : 1.0;  // the edge leaving corner a toward +index m
+#pragma unroll
+            for (int c = 0; c < 3; ++c) e[m][c] = s * (X[b][c] - X[a][c]);
+        }
+        const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                           e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        pos += det > 0.0;
+        neg += det < 0.0;
+    }
+    return pos == 8 ? 1 : (neg == 8 ? -1 : 0);
+}
+
+// orient: 3 counters (cells with all corner Jacobians positive, all negative, mixed or zero)
 __global__ void __launch_bounds__(kBuildThreads) k_build_records(GridDev g, CellRec* rec, float* xff,
-                                                                 double* partials) {
+                                                                 double* partials, unsigned long long* orient) {
     // node coordinates as FP32 pairs, SoA [xh | xl | yh | yl | zh | zl]
     for (int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nd < g.nnodes;
          nd += (int64_t)gridDim.x * blockDim.x) {
@@ -89,6 +113,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_records(GridDev g, Cell
 #pragma unroll
         for (int q = 0; q < 5; ++q) r.pad[q] = 0.f;
         rec[cell] = r;
+        const int o = cell_orientation(X);
+        atomicAdd(orient + (o > 0 ? 0 : (o < 0 ? 1 : 2)), 1ull);
     }
     block_reduce9(v, partials + 9 * blockIdx.x);
 }
@@ -226,8 +252,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t* out, int64_t
 }  // namespace
 
 cudaError_t launch_build_records(const GridDev& g, CellRec* rec, float* xff, double* partials, int nblocks,
-                                 double* out9, cudaStream_t st) {
-    k_build_records<<<nblocks, kBuildThreads, 0, st>>>(g, rec, xff, partials);
+                                 double* out9, unsigned long long* orient, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(orient, 0, 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_build_records<<<nblocks, kBuildThreads, 0, st>>>(g, rec, xff, partials, orient);
     k_reduce_partials<<<1, kBuildThreads, 0, st>>>(partials, nblocks, out9);
     return cudaGetLastError();
 }

@@ -65,7 +65,8 @@ struct GridDev {
     int32_t nb[3];
     int32_t mlp_hidden;
     int32_t blanked;  // 1 once ovs_set_iblank gave the grid a mask (cell records then carry blocked flags)
-    int32_t pad;
+    int32_t overlap;  // 1: cells may overlap one another (folded cells found, or said by the caller): no point is
+                      // final from the walk alone; each goes to the exhaustive lowest-id search of its control cell
 };
 
 struct MotionDev {
@@ -460,7 +461,7 @@ __device__ __forceinline__ bool newton32(const CellRec& r, float dx, float dy, f
 
 // FP64 Newton on the exact node coordinates (the donor rule's decision).  Starts at (u,v,w).
 // Returns true iff converged (last step <= 1e-13 within 50 steps) and the result lies in the window.
-__device__ __forceinline__ bool newton64_contains(const GridDev& g, int64_t cell, double3 p, double& u, double& v,
+static __device__ __noinline__ bool newton64_contains(const GridDev& g, int64_t cell, double3 p, double& u, double& v,
                                                   double& w) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
@@ -530,7 +531,7 @@ __device__ __forceinline__ bool newton64_contains(const GridDev& g, int64_t cell
 // (> 1e-11) that the FP64 definition, 2^8 times less noisy, might itself not reach its 1e-13 tolerance; or a
 // local coordinate within the band of a window bound, where only the FP64 predicate may decide).  Away from
 // that band the FP64 definition gives the same answer, because the two iterations agree to within the band.
-__device__ __forceinline__ int newton_ff(const GridDev& g, int64_t cell, const ff p[3], float u0, float v0, float w0,
+static __device__ __noinline__ int newton_ff(const GridDev& g, int64_t cell, const ff p[3], float u0, float v0, float w0,
                                          double& u, double& v, double& w) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
@@ -655,8 +656,9 @@ __device__ __forceinline__ bool contains_exact(const GridDev& g, int64_t cell, c
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // host-side launchers (defined in the .cu files)
+// orient: 3 device counters (cells right-handed, left-handed, folded or degenerate), zeroed here
 cudaError_t launch_build_records(const GridDev& g, CellRec* rec, float* xff, double* partials, int nblocks,
-                                 double* out9, cudaStream_t st);
+                                 double* out9, unsigned long long* orient, cudaStream_t st);
 cudaError_t launch_bin_count(const GridDev& g, uint32_t* counts, cudaStream_t st);
 // exclusive scan of n counts into start[0..n] (start[n] = total); block_sums: one entry per tile of
 // kScanTileElems counts

@@ -59,6 +59,9 @@ EXPORTS = [
     "ovs_get_donors",
     "ovs_set_donors",
     "ovs_autotune_guess",
+    "ovs_interface_flux",
+    "ovs_grid_check",
+    "ovs_set_grid_overlap",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -175,6 +178,9 @@ def load(path: Optional[str] = None):
         "ovs_get_tuning": [V, ctypes.POINTER(ovs_tuning)],
         "ovs_autotune": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors), ctypes.POINTER(ovs_fields),
                          I32, ctypes.POINTER(ovs_fields_out), I32, ctypes.POINTER(ovs_tuning)],
+        "ovs_grid_check": [V, I32, V, ctypes.POINTER(I32)],
+        "ovs_set_grid_overlap": [V, I32, I32],
+        "ovs_interface_flux": [V, I32, I64, V, V, I32, V, ctypes.POINTER(ovs_fields), V, V, I32],
         "ovs_autotune_guess": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors),
                                ctypes.POINTER(ovs_fields), I32, ctypes.POINTER(ovs_fields_out), I32, V, V, I32, V,
                                ctypes.POINTER(I32)],
@@ -343,12 +349,34 @@ def ovs_autotune_guess(ctx, sets, nsets: int, donors: ovs_donors, fields, nfield
     flat = [int(p) for cand in params for p in cand]
     parr = (ctypes.c_void_p * max(1, len(flat)))(*[p or None for p in flat]) if flat else None
     ms = (ctypes.c_float * (2 * nc))()
-    best = I32()
+    best = ctypes.c_int32()
     assert not flat or len(flat) == nc * ng
     _check(ctx, load().ovs_autotune_guess(ctx, sets, int(nsets), ctypes.byref(donors), fields, int(nfields),
                                           ctypes.byref(out) if out is not None else None, nc, h, parr, int(reps), ms,
                                           ctypes.byref(best)))
     return best.value, [(ms[2 * k], ms[2 * k + 1]) for k in range(nc)]
+
+
+def ovs_interface_flux(ctx, grid_id: int, nfaces: int, faces: int, signs: int, nsurf: int, surf_start, vel: ovs_fields,
+                       flux: int, net: int, correct: bool):
+    """Pointers as ints (device), surf_start a host sequence of nsurf + 1 offsets."""
+    ss = (ctypes.c_int64 * max(1, nsurf + 1))(*[int(x) for x in (surf_start if nsurf else [0])])
+    _check(ctx, load().ovs_interface_flux(ctx, int(grid_id), int(nfaces), ctypes.c_void_p(faces or None),
+                                          ctypes.c_void_p(signs or None), int(nsurf), ss if nsurf else None,
+                                          ctypes.byref(vel), ctypes.c_void_p(flux or None),
+                                          ctypes.c_void_p(net or None), int(bool(correct))))
+
+
+def ovs_grid_check(ctx, grid_id: int):
+    """(cells right-handed, left-handed, folded or degenerate), and whether the grid is searched exhaustively."""
+    cells = (ctypes.c_int64 * 3)()
+    ov = ctypes.c_int32()
+    _check(ctx, load().ovs_grid_check(ctx, int(grid_id), cells, ctypes.byref(ov)))
+    return tuple(int(x) for x in cells), bool(ov.value)
+
+
+def ovs_set_grid_overlap(ctx, grid_id: int, overlap: bool):
+    _check(ctx, load().ovs_set_grid_overlap(ctx, int(grid_id), int(bool(overlap))))
 
 
 def ovs_assemble_noalloc(ctx, sets, nsets: int, donors: ovs_donors):
@@ -621,6 +649,23 @@ class Context:
                                       len(self.grids), o, hidden, ptrs, reps)
         return ovs_autotune_guess(self.ctx, make_sets(sets), len(sets), self.donors_struct(donors), None, 0, None,
                                   hidden, ptrs, reps)
+
+    def interface_flux(self, gid: int, faces, vel, signs=None, surf_start=None, correct: bool = False):
+        """ovs_interface_flux: faces device int64 tensor, vel = (u, v, w) device tensors over grid gid's nodes,
+        signs device int8 tensor or None, surf_start host list (nsurf + 1) or None.  Returns (flux, net) where net
+        is a device FP64 tensor [2 nsurf] (net flux before the correction, total area) or None."""
+        t = self.torch
+        nsurf = 0 if surf_start is None else len(surf_start) - 1
+        flux = t.empty(int(faces.numel()), dtype=vel[0].dtype, device=self.device)
+        net = t.empty(max(1, 2 * nsurf), dtype=t.float64, device=self.device) if nsurf else None
+        v = ovs_fields()
+        v.u, v.v, v.w, v.p = vel[0].data_ptr(), vel[1].data_ptr(), vel[2].data_ptr(), vel[0].data_ptr()
+        v.dtype = OVS_F64 if vel[0].dtype == t.float64 else OVS_F32
+        v.stride = 1
+        ovs_interface_flux(self.ctx, gid, int(faces.numel()), faces.data_ptr(),
+                           signs.data_ptr() if signs is not None else 0, nsurf, surf_start, v, flux.data_ptr(),
+                           net.data_ptr() if net is not None else 0, correct)
+        return flux, net
 
     def add_surface(self, body_gid: int, V, T) -> int:
         """ovs_create_surface of a closed triangulated body surface (host V (nv, 3), T (nt, 3)) fixed in grid
