@@ -612,7 +612,7 @@ def run_ovs(args, rank, world, local):
                    "distinct_time_steps": n_distinct},
         "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
         "breakdown_ms_per_step": {"k_assemble (with the interpolation of its points)": fast_avg_ms,
-                                  "k_slow (near-face || stuck halves, with the interpolation of their points)":
+                                  "k_slow_near + k_slow_stuck (with the interpolation of their points)":
                                       float(np.mean(slow_ms))},
         "launch_modes_ms_per_step": {"graph": mode_ms["graph"], "direct": mode_ms["direct"],
                                      "direct_traced": float(np.mean(traced_ms)),
@@ -623,7 +623,7 @@ def run_ovs(args, rank, world, local):
                      "traffic": traffic},
         "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                 "d2h_bytes_per_step": d2h // K},
-        "gpu_launches": 2 * K,  # per step: k_assemble and k_slow (both interpolating)
+        "gpu_launches": 3 * K,  # per step: k_assemble, k_slow_near, k_slow_stuck (all interpolating)
         "clocks": ck,
         "walk_stats": stats,
         "plain_unbatched_ms_per_step": unbatched_ms,

@@ -179,7 +179,7 @@ const char* ovs_last_error(const ovs_ctx* ctx);
 int ovs_set_stream(ovs_ctx* ctx, void* cuda_stream);
 
 /* Bytes of the context workspace needed for calls of up to `max_points` query points (slow-path
- * queue, counters, status word). */
+ * queue of two entries per point, counters, status word, step parameters). */
 int ovs_workspace_size(const ovs_ctx* ctx, int64_t max_points, size_t* bytes);
 /* Attach a caller-owned device workspace (256-byte aligned) of at least ovs_workspace_size bytes. */
 int ovs_workspace_attach(ovs_ctx* ctx, void* dptr, size_t bytes, int64_t max_points);
@@ -359,7 +359,8 @@ int ovs_set_donors(ovs_ctx* ctx, int32_t grid_id, const uint32_t* src);
 typedef struct {
     int32_t assemble_blocks_per_sm; /* k_assemble, 256 threads a block: 1..12 */
     int32_t interp_blocks_per_sm;   /* k_interp, 256 threads a block: 1..32 */
-    int32_t slow_blocks_per_sm;     /* k_slow, 256 threads a block, per SM for each of its two halves: 1..8 */
+    int32_t slow_blocks_per_sm;     /* the slow-path kernels (near-face decisions, then exhaustive searches), 256
+                                       threads a block, each: 1..8 */
     int32_t guess_blocks_per_sm;    /* 0..32, accepted and kept but without effect: the learned guess runs inside
                                        the assembly kernel, in its launch shape */
     int32_t launch;                 /* OVS_LAUNCH_GRAPH or OVS_LAUNCH_DIRECT (the option of ovs_set_options);
@@ -420,7 +421,7 @@ int ovs_autotune_guess(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, 
 
 /* Tracing: record caller-created CUDA events (cudaEvent_t, NULL to skip one) on the context's stream at
  * fixed points of later calls: ev[0] before the fast assembly kernel, ev[1] after it, ev[2] after the
- * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it; ev[5] and ev[6]
+ * slow-path kernels (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it; ev[5] and ev[6]
  * are not recorded (the learned guess runs inside the fast assembly kernel, between ev[0] and ev[1]).  In
  * ovs_assemble_interpolate the two assembly kernels interpolate each point as they decide its donor (there is
  * no interpolation kernel): ev[3] and ev[4] are then both recorded after the slow-path kernel.
@@ -440,9 +441,9 @@ int ovs_set_trace_events(ovs_ctx* ctx, void* const* ev, int32_t n);
  * always as direct kernel launches, never as a captured CUDA graph (the launch option is ignored).
  *
  *  - Limit: at most OVS_NOALLOC_MAX_POINTS points per call (sum over the sets); larger calls return
- *    OVS_ERR_WORKSPACE without launching anything.  The array is 24 MiB of device memory
- *    (OVS_NOALLOC_MAX_POINTS x 24 bytes + 256), held by every GPU on which the library's kernels are
- *    loaded until the process exits.
+ *    OVS_ERR_WORKSPACE without launching anything.  The array is 48 MiB of device memory
+ *    (two slow-path entries of 24 bytes per point: OVS_NOALLOC_MAX_POINTS x 48 bytes + 256), held by every
+ *    GPU on which the library's kernels are loaded until the process exits.
  *  - Allocates nothing: no cudaMalloc/cudaFree and no allocating library routine, host or device.  It
  *    still needs a context with a workspace attached and grids created (set-up time objects): the grid
  *    table, the device status word and the statistics counters live there.

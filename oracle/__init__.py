@@ -212,15 +212,26 @@ def frame_of(m) -> Frame:
 
 
 def to_inertial(f: Frame, x: np.ndarray) -> np.ndarray:
-    """x_in = R x + c (Sec. 2.1, Fig. "non-inertial")."""
+    """x_in = R x + c (Sec. 2.1, Fig. "non-inertial"), evaluated in a fixed order, each product and sum rounded
+    once: x_in_i = ((R_i0 x_0 + R_i1 x_1) + R_i2 x_2) + c_i.  The order defines the FP64 point every donor and
+    hole-cut decision is taken on (the reading of "the point in the donor frame" down to the last bit)."""
+    x = np.asarray(x, dtype=np.float64)
+    shape, x = x.shape, x.reshape(-1, 3)
+    R, c = f.R, f.c
     with np.errstate(invalid="ignore", over="ignore"):
-        return x @ f.R.T + f.c
+        cols = [((R[i, 0] * x[:, 0] + R[i, 1] * x[:, 1]) + R[i, 2] * x[:, 2]) + c[i] for i in range(3)]
+    return np.stack(cols, axis=1).reshape(shape)
 
 
 def to_frame(f: Frame, x_in: np.ndarray) -> np.ndarray:
-    """x_body = R^T (x_in - c)."""
+    """x_body = R^T (x_in - c), in the fixed order x_body_i = (R_0i d_0 + R_1i d_1) + R_2i d_2, d = x_in - c."""
+    x_in = np.asarray(x_in, dtype=np.float64)
+    shape, x_in = x_in.shape, x_in.reshape(-1, 3)
+    R, c = f.R, f.c
     with np.errstate(invalid="ignore", over="ignore"):
-        return (x_in - f.c) @ f.R
+        d = [x_in[:, k] - c[k] for k in range(3)]
+        cols = [(R[0, i] * d[0] + R[1, i] * d[1]) + R[2, i] * d[2] for i in range(3)]
+    return np.stack(cols, axis=1).reshape(shape)
 
 
 def frame_map(f_r: Frame, f_d: Frame, x_r: np.ndarray):

@@ -235,6 +235,51 @@ void fill_xforms(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, Xf
     }
 }
 
+// Per set: the velocity transform from its first donor's frame to the receiver's as one affine map (FP64 here,
+// FP32 on the device): u_r = A u_d + B x_r + b (see VelAffine).
+void fill_vel_affine(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, int mode, VelAffine* out) {
+    for (int s = 0; s < nsets; ++s) {
+        const MotionDev& r = c->motion[sets[s].receiver];
+        const MotionDev& d = c->motion[sets[s].donors[0]];
+        VelAffine& V = out[s];
+        memset(&V, 0, sizeof V);
+        double A[9], B[9] = {0}, b[3] = {0};
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double m = 0;
+                for (int j = 0; j < 3; ++j) m += r.R[3 * j + i] * d.R[3 * j + k];  // (R_r^T R_d)_ik
+                A[3 * i + k] = mode == OVS_VEL_NONE ? (i == k ? 1.0 : 0.0) : m;
+            }
+        if (mode == OVS_VEL_RELATIVE) {
+            const double w[3] = {d.w[0] - r.w[0], d.w[1] - r.w[1], d.w[2] - r.w[2]};
+            const double W[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};  // [w]x
+            double WR[9];
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    double m = 0;
+                    for (int j = 0; j < 3; ++j) m += W[3 * i + j] * r.R[3 * j + k];
+                    WR[3 * i + k] = m;
+                }
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    double m = 0;
+                    for (int j = 0; j < 3; ++j) m += r.R[3 * j + i] * WR[3 * j + k];
+                    B[3 * i + k] = m;
+                }
+            const double dc[3] = {r.c[0] - d.c[0], r.c[1] - d.c[1], r.c[2] - d.c[2]};
+            const double e[3] = {d.V[0] - r.V[0] + d.w[1] * dc[2] - d.w[2] * dc[1],
+                                 d.V[1] - r.V[1] + d.w[2] * dc[0] - d.w[0] * dc[2],
+                                 d.V[2] - r.V[2] + d.w[0] * dc[1] - d.w[1] * dc[0]};
+            for (int i = 0; i < 3; ++i) b[i] = r.R[i] * e[0] + r.R[3 + i] * e[1] + r.R[6 + i] * e[2];
+        }
+        for (int q = 0; q < 9; ++q) {
+            V.A[q] = (float)A[q];
+            V.B[q] = (float)B[q];
+        }
+        for (int q = 0; q < 3; ++q) V.b[q] = (float)b[q];
+    }
+}
+
 // FP32 copies of the motions for the FP32 velocity transform
 void fill_motion_f32(const ovs_ctx* c, MotionF* out) {
     for (int g = 0; g < OVS_MAX_GRIDS; ++g) {
@@ -330,7 +375,9 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     size_t off = align_up(sizeof(GridDev) * OVS_MAX_GRIDS);
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     off = align_up(off + 4 * sizeof(int32_t));
-    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    // the slow-path queue: two entries per point (a near-face point the neighbourhood test cannot place is queued
+    // again for the exhaustive search)
+    off = align_up(off + (size_t)std::max<int64_t>(1, 2 * max_points) * sizeof(SlowEntry));
     off = align_up(off + sizeof(StepParams));
     *bytes = off;
     return OVS_OK;
@@ -356,7 +403,7 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // near-face queue, stuck queue, work counter
     off = align_up(off + 4 * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
-    off = align_up(off + (size_t)std::max<int64_t>(1, max_points) * sizeof(SlowEntry));
+    off = align_up(off + (size_t)std::max<int64_t>(1, 2 * max_points) * sizeof(SlowEntry));
     c->d_step = (StepParams*)(base + off);
     off = align_up(off + sizeof(StepParams));
     c->ws = dptr;
@@ -735,6 +782,7 @@ void fill_interp(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
     fill_sets(sets, nsets, P->s);
     memcpy(P->m, c->motion, sizeof P->m);
     fill_motion_f32(c, P->mf);
+    fill_vel_affine(c, sets, nsets, P->mode, P->va);
     for (int g = 0; g < c->ngrids; ++g) {
         FieldsDev& F = P->fields[g];
         F.f[0] = fields[g].u;
@@ -893,7 +941,7 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     P->guess = mlp ? OVS_GUESS_HINT : c->opts.guess;
     P->stats = c->opts.collect_stats;
     P->total = total;
-    P->queue_cap = c->max_points;
+    P->queue_cap = 2 * c->max_points;
     P->out_grid = out->grid;
     P->out_cell = out->cell;
     P->out_xi = out->xi;
@@ -1472,12 +1520,12 @@ int ovs_autotune_guess(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
 // ovs_assemble_noalloc: the slow-path queue of k_assemble in a fixed device array instead of the context
 // workspace (see include/ovs.h for who needs this and its limits).
 //
-// Layout of the array: [queue counter, padded to 256 bytes][OVS_NOALLOC_MAX_POINTS slow-path entries].
+// Layout of the array: [queue counters, padded to 256 bytes][2 x OVS_NOALLOC_MAX_POINTS slow-path entries].
 // In host code `ovs_noalloc_scratch` is only a host-side stand-in for the symbol; the device address comes
 // from cudaGetSymbolAddress, looked up once per device with that device current.
 namespace {
 constexpr size_t kNoAllocHead = 256;
-constexpr size_t kNoAllocBytes = kNoAllocHead + (size_t)OVS_NOALLOC_MAX_POINTS * sizeof(SlowEntry);
+constexpr size_t kNoAllocBytes = kNoAllocHead + 2 * (size_t)OVS_NOALLOC_MAX_POINTS * sizeof(SlowEntry);
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
@@ -1545,7 +1593,7 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     P.guess = mlp ? OVS_GUESS_HINT : c->opts.guess;
     P.stats = c->opts.collect_stats;
     P.total = total;
-    P.queue_cap = OVS_NOALLOC_MAX_POINTS;
+    P.queue_cap = 2 * (int64_t)OVS_NOALLOC_MAX_POINTS;
     P.out_grid = out->grid;
     P.out_cell = out->cell;
     P.out_xi = out->xi;

@@ -8,12 +8,14 @@
 //                    ballot + one atomic per warp) into the slow queue.
 //   k_slow_near      one warp per point near a face: the donor predicate (FP32-pair Newton on the node
 //                    coordinates, FP64 where that cannot decide) over the cells sharing the near faces /
-//                    edges / corner, one lane each, lowest linear id first.
-//   k_slow_stuck     one block per stuck walk: the exhaustive search of the point's control cell of
-//                    Sec. 2.2.5 (the paper's brute-force fallback); all threads filter the list, warp 0 decides.
-//   Both continue with the later grids of the set's priority list (Sec. 2.4 item 1).
+//                    edges / corner, one lane each, lowest linear id first; a point none of them holds is
+//                    appended to the stuck queue.
+//   k_slow_stuck     then, one block per stuck entry: the exhaustive search of the point's control cell of
+//                    Sec. 2.2.5 (the paper's brute-force fallback); all threads filter the list, the exact test
+//                    runs on every survivor at once; it continues with the later grids of the set's priority
+//                    list (Sec. 2.4 item 1).
 //
-// In a call that also interpolates (ovs_assemble_interpolate) both kernels go on, for every point whose donor
+// In a call that also interpolates (ovs_assemble_interpolate) the kernels go on, for every point whose donor
 // they decide, to the trilinear interpolation of u, v, w, p and the frame velocity transform (Sec. 2.2.6,
 // Sec. 2.1; ovs_fields.cuh) while donor, local coordinates and receiver node are at hand: one pass per point,
 // no separate interpolation kernel re-reading the donor records.
@@ -239,6 +241,7 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
     int32_t node = -1;
     bool node_ok = false;
     ff xd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    uint32_t h0 = kNoHint;  // the receiver node's donor at the previous call, loaded with its coordinates
     // the set of point t: lane 0 searches the set table for the warp's first point, the other lanes step forward
     // from there (a work item of 32 consecutive points rarely crosses a set boundary)
     {
@@ -261,6 +264,7 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
             const float* xf = gr.xff;
 #pragma unroll
             for (int c = 0; c < 3; ++c) x[c] = {__ldg(xf + 2 * c * nn + node), __ldg(xf + (2 * c + 1) * nn + node)};
+            if (P.guess == OVS_GUESS_HINT) h0 = gr.hint[node];
         }
         xf_apply(P.xf[si], x, xd);
     }
@@ -279,11 +283,9 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
             const GuessDev& gn = P.gn[gd0];
             if (gn.hidden) {
                 bool valid = false;
-                if (!P.guess_always) {
-                    const uint32_t h = G[s.receiver].hint[node];
-                    valid = h != kNoHint && (int)(h >> kCellBits) == gd0 &&
-                            (int64_t)(h & ((1u << kCellBits) - 1)) < G[gd0].ncells;
-                }
+                if (!P.guess_always)
+                    valid = h0 != kNoHint && (int)(h0 >> kCellBits) == gd0 &&
+                            (int64_t)(h0 & ((1u << kCellBits) - 1)) < G[gd0].ncells;
                 if (!valid) {
                     bool inside = true;
 #pragma unroll
@@ -336,8 +338,7 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
             }
             int64_t cell = di == 0 ? gcell : -1;
             if (cell < 0 && P.guess == OVS_GUESS_HINT) {
-                uint32_t h = gr.hint[node];
-                if (h != kNoHint && (int)(h >> kCellBits) == gd) cell = h & ((1u << kCellBits) - 1);
+                if (h0 != kNoHint && (int)(h0 >> kCellBits) == gd) cell = h0 & ((1u << kCellBits) - 1);
                 if (cell >= g.ncells) cell = -1;
             }
             const bool from_hint = cell >= 0;
@@ -385,7 +386,8 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
                     if (IM) {
                         const InterpParams& I = S.i;
                         interp_point<T>(g, gr, I.fields[gd], I.mode, I.mf[gd], I.mf[s.receiver], I.m[gd],
-                                        I.m[s.receiver], node, cell, (T)u, (T)v, (T)w, I.out, t);
+                                        I.m[s.receiver], node, cell, (T)u, (T)v, (T)w, I.out, t,
+                                        di == 0 ? I.va + si : nullptr);
                     }
                 } else {
                     // near a face (FP64 decision among the neighbours), or FP64 precision (FP64 refinement)
@@ -706,7 +708,7 @@ __device__ __forceinline__ void finish(const StepParams& S, const GridDev* G, co
                 c = P.xi_f64 ? (T)w : (T)(float)w;
         const InterpParams& I = S.i;
         interp_point<T>(G[gd], G[r], I.fields[gd], I.mode, I.mf[gd], I.mf[r], I.m[gd], I.m[r], sp.node, cell, a, b, c,
-                        I.out, sp.t);
+                        I.out, sp.t, gd == P.s[sp.si].donors[0] ? I.va + sp.si : nullptr);
     }
 }
 
@@ -716,56 +718,47 @@ __device__ __forceinline__ void finish_none(const StepParams& S, int64_t t) {
     if (IM) zero_point<typename FieldT<IM>::T>(S.i.out, t);
 }
 
-// Points near a face: one warp each, one lane per candidate cell.  A point whose candidates all fail (or a
-// later donor of its list) gets the warp-level exhaustive search.
+// Points near a face: one warp each, one lane per candidate cell (the cells sharing the near faces / edges /
+// corner, lowest id first).  A point none of them holds goes on to the stuck queue, where the exhaustive search
+// of its control cell (and the later grids of its list) runs a block wide: a warp alone would walk a crowded
+// control cell in a long chain of dependent loads.
 template <int IM>
 __device__ __forceinline__ void slow_near_body(const StepParams& S, const GridDev* __restrict__ G, unsigned bid,
                                                unsigned nblk) {
     const AsmParams& P = S.a;
-    uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
+    const uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
-    unsigned nref = 0, nfb = 0;
+    unsigned nref = 0;
     for (uint32_t q = bid * kSlowWarps + (threadIdx.x >> 5); q < count; q += nblk * kSlowWarps) {
         const SlowEntry e = P.queue[q];
         const SlowPoint sp = slow_point(P, e);
-        const SetDev& s = P.s[sp.si];
-        bool done = false;
-        for (int di = sp.di0; di < s.ndonor && !done; ++di) {
-            const int gd = s.donors[di];
-            const GridDev& g = G[gd];
-            auto p64 = [&]() { return point64(P, G, sp, gd); };
-            ff pf[3];
-            const bool pf_ok = point_ff(P, G, sp, di, pf);
-            int64_t cell = -1;
-            double u = 0, v = 0, w = 0;
-            uint8_t st = OVS_STATUS_FOUND | OVS_STATUS_REFINED;
-            bool ok = false;
-            if (di == sp.di0 && pf_ok) ok = neighbourhood_warp(g, pf, p64, e.cell, sp.mask0, e.xi, cell, u, v, w);
-            if (!ok) {
-                const double3 p = p64();
-                const int64_t b = point_bin(g, p);
-                if (b < 0) continue;
-                if (!pf_ok) {
-                    pf[0] = split_double(p.x);
-                    pf[1] = split_double(p.y);
-                    pf[2] = split_double(p.z);
-                }
-                st |= OVS_STATUS_FALLBACK;
-                ++nfb;
-                ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
-            }
-            if (ok) {
-                if (lane == 0) finish<IM>(S, G, sp, gd, cell, u, v, w, st);
-                done = true;
-                ++nref;
+        const int gd = P.s[sp.si].donors[sp.di0];
+        const GridDev& g = G[gd];
+        auto p64 = [&]() { return point64(P, G, sp, gd); };
+        ff pf[3];
+        const bool pf_ok = point_ff(P, G, sp, sp.di0, pf);
+        int64_t cell = -1;
+        double u = 0, v = 0, w = 0;
+        bool ok = false;
+        if (pf_ok) ok = neighbourhood_warp(g, pf, p64, e.cell, sp.mask0, e.xi, cell, u, v, w);
+        if (ok) {
+            if (lane == 0) finish<IM>(S, G, sp, gd, cell, u, v, w, OVS_STATUS_FOUND | OVS_STATUS_REFINED);
+            ++nref;
+        } else if (lane == 0) {
+            // to the back of the queue, below the near-face entries (which this kernel is still reading)
+            const uint32_t idx = atomicAdd(P.queue_count + 1, 1u);
+            if ((int64_t)idx < P.queue_cap - (int64_t)count) {
+                SlowEntry r = e;
+                r.di = sp.di0;
+                r.cell = -1;
+                r.xi[0] = r.xi[1] = r.xi[2] = 0.5f;
+                P.queue[P.queue_cap - 1 - idx] = r;
+            } else {
+                atomicOr(P.err, kErrQueueOverflow);
             }
         }
-        if (!done && lane == 0) finish_none<IM>(S, sp.t);
     }
-    if (P.stats && lane == 0) {
-        if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
-        if (nfb) atomicAdd(P.counters + kCtrFallback, (unsigned long long)nfb);
-    }
+    if (P.stats && lane == 0 && nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
 }
 
 constexpr int kMaxCand = 128;
@@ -878,16 +871,19 @@ __device__ __forceinline__ void slow_stuck_body(const StepParams& S, const GridD
     }
 }
 
-// The two slow paths in one launch, side by side: odd blocks take the stuck walks (a block per entry), even
-// blocks the near-face points (a warp per entry).  Interleaved, the first wave of blocks holds both kinds, so
-// the long stuck walks do not keep the near-face points waiting; one kernel keeps them concurrent without a
-// second stream (or a fork in the step graph).
+// The slow paths, one after the other on the stream: the near-face decisions (a warp per entry), then the
+// exhaustive searches (a block per entry) of the stuck walks and of the near-face points none of whose
+// neighbouring cells holds them.
 template <int IM>
-__global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restrict__ Sp,
-                                                       const GridDev* __restrict__ G) {
-    const unsigned half = gridDim.x >> 1;
-    if (blockIdx.x & 1) slow_stuck_body<IM>(*Sp, G, blockIdx.x >> 1, half);
-    else slow_near_body<IM>(*Sp, G, blockIdx.x >> 1, half);
+__global__ void __launch_bounds__(kSlowThreads) k_slow_near(const StepParams* __restrict__ Sp,
+                                                            const GridDev* __restrict__ G) {
+    slow_near_body<IM>(*Sp, G, blockIdx.x, gridDim.x);
+}
+
+template <int IM>
+__global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const StepParams* __restrict__ Sp,
+                                                             const GridDev* __restrict__ G) {
+    slow_stuck_body<IM>(*Sp, G, blockIdx.x, gridDim.x);
 }
 
 }  // namespace
@@ -906,9 +902,14 @@ cudaError_t launch_assemble(const StepParams* dS, int interp, uint32_t* queue_co
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    if (interp == 1) k_slow<1><<<2 * sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    else if (interp == 2) k_slow<2><<<2 * sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    else k_slow<0><<<2 * sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    if (interp == 1) k_slow_near<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else if (interp == 2) k_slow_near<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else k_slow_near<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if (interp == 1) k_slow_stuck<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else if (interp == 2) k_slow_stuck<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else k_slow_stuck<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

@@ -166,14 +166,33 @@ __device__ __forceinline__ void vel_transform_f64(int mode, const MotionDev& md,
 }
 
 // Interpolated and transformed (u, v, w, p) of one point at donor (gd, cell, xi), written to out[*][t].
-// T = field type.  Receiver position: FP32 pair (T = float) or FP64 (T = double) of node `node`.
+// T = field type.  Receiver position: FP32 pair (T = float) or FP64 (T = double) of node `node`.  va: the set's
+// affine velocity map when gd is the set's first donor and the fields are FP32 (else NULL: the two transforms).
 template <typename T>
 __device__ __forceinline__ void interp_point(const GridDev& g, const GridDev& gr, const FieldsDev& F, int mode,
                                              const MotionF& mfd, const MotionF& mfr, const MotionDev& md,
                                              const MotionDev& mr, int32_t node, int64_t cell, T u, T v, T w,
-                                             void* const out[4], int64_t t) {
+                                             void* const out[4], int64_t t, const VelAffine* va = nullptr) {
     T q[4];
     gather8<T>(g, F, cell, u, v, w, q);
+    if constexpr (sizeof(T) == 4) {
+        if (va) {
+            const float ud[3] = {q[0], q[1], q[2]};
+            float x[3] = {0.f, 0.f, 0.f};
+            if (mode == OVS_VEL_RELATIVE) {
+                const int64_t nn = gr.nnodes;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) x[c] = __ldg(gr.xff + 2 * c * nn + node) + __ldg(gr.xff + (2 * c + 1) * nn + node);
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                q[r] = fmaf(va->A[3 * r], ud[0], fmaf(va->A[3 * r + 1], ud[1], fmaf(va->A[3 * r + 2], ud[2],
+                       fmaf(va->B[3 * r], x[0], fmaf(va->B[3 * r + 1], x[1], fmaf(va->B[3 * r + 2], x[2], va->b[r]))))));
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ((T*)out[c])[t] = q[c];
+            return;
+        }
+    }
     if (mode != OVS_VEL_NONE) {
         T ud[3] = {q[0], q[1], q[2]};
         if constexpr (sizeof(T) == 4) {

@@ -131,9 +131,33 @@ struct SurfHot {
     int ar, au, aw;
 };
 
-// The point (pr along the ray; pu, pw in the plane; FP32 pairs) against registration e: the FP32 decision, else
-// the FP64 test at the point hi + lo.
-__device__ __forceinline__ int crosses(const SurfHot& H, int32_t e, ff pr, ff pu, ff pw) {
+// The candidate node in the body frame in FP64, by the frame maps' fixed order of operations (to_inertial of the
+// target grid's motion, then to_body of the body's): the point every FP64 test decides on, computed on first use.
+struct Exact64 {
+    const GridDev* tg;
+    const MotionDev* mt;
+    const MotionDev* mb;
+    int64_t node;
+    int ar, au, aw;
+    bool have;
+    double p[3];
+    __device__ __forceinline__ const double* get() {
+        if (!have) {
+            const double3 x = make_double3(__ldg(tg->x + node), __ldg(tg->y + node), __ldg(tg->z + node));
+            const double3 b = to_body(*mb, to_inertial(*mt, x));
+            const double q[3] = {b.x, b.y, b.z};
+            p[0] = q[ar];
+            p[1] = q[au];
+            p[2] = q[aw];
+            have = true;
+        }
+        return p;
+    }
+};
+
+// The point (pr along the ray; pu, pw in the plane; FP32 pairs) against registration e: the FP32 decision (its
+// bound covers the pairs' distance to the FP64 point, about 1e-14 relative), else the FP64 test at the FP64 point.
+__device__ __forceinline__ int crosses(const SurfHot& H, int32_t e, ff pr, ff pu, ff pw, Exact64& x64) {
     const float4 g0 = __ldg(H.rec + 2 * (int64_t)e), g1 = __ldg(H.rec + 2 * (int64_t)e + 1);
     const int sc = screen(g0, g1, H.tri_r, pu.hi, pw.hi, pr.hi, H.mag);
     if (sc != kUnsure) return sc;
@@ -142,8 +166,8 @@ __device__ __forceinline__ int crosses(const SurfHot& H, int32_t e, ff pr, ff pu
     const double A[3] = {__ldg(H.v + 3 * i0 + H.ar), __ldg(H.v + 3 * i0 + H.au), __ldg(H.v + 3 * i0 + H.aw)};
     const double B[3] = {__ldg(H.v + 3 * i1 + H.ar), __ldg(H.v + 3 * i1 + H.au), __ldg(H.v + 3 * i1 + H.aw)};
     const double C[3] = {__ldg(H.v + 3 * i2 + H.ar), __ldg(H.v + 3 * i2 + H.au), __ldg(H.v + 3 * i2 + H.aw)};
-    return ray_crosses(A, B, C, (double)pr.hi + (double)pr.lo, (double)pu.hi + (double)pu.lo,
-                       (double)pw.hi + (double)pw.lo);
+    const double* p = x64.get();
+    return ray_crosses(A, B, C, p[0], p[1], p[2]);
 }
 
 constexpr int kHoleThreads = 256;
@@ -160,6 +184,8 @@ struct HoleBatch {
     const int32_t* nodes[OVS_MAX_GRIDS];
     SurfaceDev S[OVS_MAX_GRIDS];
     HoleXf F[OVS_MAX_GRIDS];
+    MotionDev mt;                 // the target grid's motion
+    MotionDev mb[OVS_MAX_GRIDS];  // each surface's body motion
 };
 static_assert(sizeof(HoleBatch) + sizeof(GridDev) + 16 <= 32764, "kernel parameters exceed the 32764-byte limit");
 
@@ -226,8 +252,9 @@ __global__ void __launch_bounds__(kHoleThreads) k_hole_cut(const __grid_constant
         if (!__any_sync(0xffffffffu, work)) continue;  // (warp-uniform)
         const SurfHot H = {S.bin_rec, S.tri_r, S.tri, S.v, S.mag, ar, au, aw};
         if (work && !heavy) {
+            Exact64 x64 = {&tg, &P.mt, &P.mb[si], node, ar, au, aw, false, {0.0, 0.0, 0.0}};
 #pragma unroll 4
-            for (int32_t e = e0; e < e1; ++e) odd ^= crosses(H, e, pr, pu, pw);
+            for (int32_t e = e0; e < e1; ++e) odd ^= crosses(H, e, pr, pu, pw, x64);
         }
         // the heavy points of this warp, one after another, each over all lanes
         for (unsigned hm = __ballot_sync(0xffffffffu, heavy); hm; hm &= hm - 1) {
@@ -236,8 +263,10 @@ __global__ void __launch_bounds__(kHoleThreads) k_hole_cut(const __grid_constant
             const ff hr = {__shfl_sync(0xffffffffu, pr.hi, l), __shfl_sync(0xffffffffu, pr.lo, l)};
             const ff hu = {__shfl_sync(0xffffffffu, pu.hi, l), __shfl_sync(0xffffffffu, pu.lo, l)};
             const ff hw = {__shfl_sync(0xffffffffu, pw.hi, l), __shfl_sync(0xffffffffu, pw.lo, l)};
+            Exact64 x64 = {&tg, &P.mt, &P.mb[si], (int64_t)__shfl_sync(0xffffffffu, (long long)node, l), ar, au, aw,
+                           false, {0.0, 0.0, 0.0}};
             int par = 0;
-            for (int32_t e = h0 + lane; e < h1; e += 32) par ^= crosses(H, e, hr, hu, hw);
+            for (int32_t e = h0 + lane; e < h1; e += 32) par ^= crosses(H, e, hr, hu, hw, x64);
             const unsigned bits = __ballot_sync(0xffffffffu, par != 0);
             if (lane == l) odd = __popc(bits) & 1;
         }
@@ -307,8 +336,10 @@ cudaError_t launch_hole_cut(const HoleJob* jobs, int njobs, const GridDev& targe
         P.nodes[k] = jobs[j].nodes;
         P.S[k] = *jobs[j].S;
         P.F[k] = hole_map(*jobs[j].S, target, mt, *jobs[j].mb);
+        P.mb[k] = *jobs[j].mb;
     }
     P.group_begin[P.nsurf] = g;
+    P.mt = mt;
     if (g == 0) return cudaSuccess;
     // one resident wave; the groups are dealt round-robin to its warps
     static int occ = 0;

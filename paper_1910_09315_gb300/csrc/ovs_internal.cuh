@@ -141,7 +141,7 @@ __device__ __forceinline__ float near_tau(const CellRec& r, float u, float v, fl
     float det = Ju[0] * (Jv[1] * Jw[2] - Jv[2] * Jw[1]) + Ju[1] * (Jv[2] * Jw[0] - Jv[0] * Jw[2]) +
                 Ju[2] * (Jv[0] * Jw[1] - Jv[1] * Jw[0]);
     float mx = fmaxf(nu, fmaxf(nv, nw)), mn = fminf(nu, fminf(nv, nw));
-    float t = 1e-5f + 4e-6f * (mx / mn) * (nu * nv * nw / fabsf(det));
+    float t = 1e-5f + 4e-6f * mx * (nu * nv * nw) * __frcp_rn(mn * fabsf(det));
     return t < 0.25f ? t : 0.25f;  // also catches NaN (degenerate cell): everything counts as near
 }
 
@@ -206,6 +206,16 @@ struct AsmParams {
     GuessDev gn[OVS_MAX_GRIDS];
 };
 
+// The velocity transform of a set's points taken from its first donor grid, as one affine map of the donor
+// velocity u_d and the receiver node's position x_r (receiver frame), composed in FP64 on the host:
+//   RELATIVE  u_r = A u_d + B x_r + b,  A = R_r^T R_d,  B = R_r^T [Omega_d - Omega_r]x R_r,
+//             b = R_r^T (V_d - V_r + Omega_d x (c_r - c_d))  (the two frame maps of Sec. 2.1 with x_in = R_r x_r + c_r)
+//   ABSOLUTE  A = R_r^T R_d, B = 0, b = 0  (Sec. 2.3.1 eq. "velocity_non");  NONE  A = I, B = 0, b = 0
+struct VelAffine {
+    float A[9], B[9], b[3];
+    int32_t pad;
+};
+
 struct InterpParams {
     int32_t nsets;
     int32_t xi_f64;
@@ -224,6 +234,7 @@ struct InterpParams {
     MotionDev m[OVS_MAX_GRIDS];
     MotionF mf[OVS_MAX_GRIDS];
     FieldsDev fields[OVS_MAX_GRIDS];
+    VelAffine va[OVS_MAX_SETS];  // per set, for its first donor grid (FP32 fields)
 };
 
 // Everything a step's kernels read, in one block of device memory written by one host-to-device copy per step
@@ -321,19 +332,28 @@ __device__ __forceinline__ int find_set(const SetDev* s, int nsets, int64_t t) {
     return lo;
 }
 
+// The frame maps in FP64 with a fixed order of operations, each product and sum rounded once (no fused
+// multiply-add), so that the FP64 point a decision is taken on is defined bit for bit:
+//   x_in_i = ((R_i0 x_0 + R_i1 x_1) + R_i2 x_2) + c_i              (Sec. 2.1: x_in = R x + c)
+//   x_b_i  = (R_0i d_0 + R_1i d_1) + R_2i d_2,  d = x_in - c        (its inverse, R^T (x_in - c))
+// An identity motion returns its input unchanged (which is also what these sums give).
 __device__ __forceinline__ double3 to_inertial(const MotionDev& m, double3 x) {
     if (m.identity) return x;
-    return make_double3(fma(m.R[0], x.x, fma(m.R[1], x.y, fma(m.R[2], x.z, m.c[0]))),
-                        fma(m.R[3], x.x, fma(m.R[4], x.y, fma(m.R[5], x.z, m.c[1]))),
-                        fma(m.R[6], x.x, fma(m.R[7], x.y, fma(m.R[8], x.z, m.c[2]))));
+    auto row = [&](int i, double c) {
+        return __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(m.R[3 * i], x.x), __dmul_rn(m.R[3 * i + 1], x.y)),
+                                   __dmul_rn(m.R[3 * i + 2], x.z)),
+                         c);
+    };
+    return make_double3(row(0, m.c[0]), row(1, m.c[1]), row(2, m.c[2]));
 }
 
 __device__ __forceinline__ double3 to_body(const MotionDev& m, double3 xin) {
     if (m.identity) return xin;
-    double dx = xin.x - m.c[0], dy = xin.y - m.c[1], dz = xin.z - m.c[2];
-    return make_double3(fma(m.R[0], dx, fma(m.R[3], dy, m.R[6] * dz)),
-                        fma(m.R[1], dx, fma(m.R[4], dy, m.R[7] * dz)),
-                        fma(m.R[2], dx, fma(m.R[5], dy, m.R[8] * dz)));
+    const double dx = __dsub_rn(xin.x, m.c[0]), dy = __dsub_rn(xin.y, m.c[1]), dz = __dsub_rn(xin.z, m.c[2]);
+    auto col = [&](int i) {
+        return __dadd_rn(__dadd_rn(__dmul_rn(m.R[i], dx), __dmul_rn(m.R[3 + i], dy)), __dmul_rn(m.R[6 + i], dz));
+    };
+    return make_double3(col(0), col(1), col(2));
 }
 
 __device__ __forceinline__ bool finite3(double3 p) {
@@ -442,7 +462,7 @@ __device__ __forceinline__ bool newton32(const CellRec& r, float dx, float dy, f
         float cwu[3] = {Jw[1] * Ju[2] - Jw[2] * Ju[1], Jw[2] * Ju[0] - Jw[0] * Ju[2], Jw[0] * Ju[1] - Jw[1] * Ju[0]};
         float cuv[3] = {Ju[1] * Jv[2] - Ju[2] * Jv[1], Ju[2] * Jv[0] - Ju[0] * Jv[2], Ju[0] * Jv[1] - Ju[1] * Jv[0]};
         float det = Ju[0] * cvw[0] + Ju[1] * cvw[1] + Ju[2] * cvw[2];
-        float inv = -1.0f / det;
+        float inv = -__frcp_rn(det);  // the correctly rounded reciprocal, as 1.0f / det
         float du = (F[0] * cvw[0] + F[1] * cvw[1] + F[2] * cvw[2]) * inv;
         float dv = (F[0] * cwu[0] + F[1] * cwu[1] + F[2] * cwu[2]) * inv;
         float dw = (F[0] * cuv[0] + F[1] * cuv[1] + F[2] * cuv[2]) * inv;

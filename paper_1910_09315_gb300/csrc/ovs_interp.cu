@@ -46,8 +46,9 @@ __device__ __forceinline__ void interp_one(const InterpParams& P, const GridDev*
         zero_point<T>(P.out, t);
         return;
     }
+    const int si = (int)(&s - P.s);
     interp_point<T>(G[gd], gr, P.fields[gd], P.mode, P.mf[gd], P.mf[s.receiver], P.m[gd], P.m[s.receiver], node,
-                    cell, u, v, w, P.out, t);
+                    cell, u, v, w, P.out, t, gd == s.donors[0] ? P.va + si : nullptr);
 }
 
 // Persistent grid (a multiple of the SM count), grid-stride over the call's points.

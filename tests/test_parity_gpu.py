@@ -157,6 +157,32 @@ def test_ties_on_nodes_and_faces(torch_cuda, xi_dtype):
     assert np.array_equal(cell, expect)
 
 
+@pytest.mark.parametrize("xi_dtype", [ovs.OVS_F64, ovs.OVS_F32])
+def test_ties_under_a_quarter_turn(torch_cuda, xi_dtype):
+    """A moving donor: a Cartesian grid of spacing 1/8 turned a quarter about z and shifted by dyadic offsets, so
+    that its frame map is exact in floating point; the receiver's nodes (a lattice of spacing 1/16 over the donor's
+    inertial box) land on the donor's nodes, edges, faces and cell centres.  The lowest linear id wins (closed form
+    in the donor frame), and the oracle agrees point for point."""
+    donor = cart("d9", 9, 0.0, 1.0, role=1)
+    R = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])  # body -> inertial: (x, y, z) -> (-y, x, z)
+    c = np.array([0.5, 0.25, 0.125])
+    rec = gen.cartesian_grid("r17", (17, 17, 17), (-0.5, 0.25, 0.125), (0.5, 1.25, 1.125), role=0)
+    ids = np.arange(rec.n_nodes, dtype=np.int32)
+    motions = [gen.Motion(R, c, np.array([0.1, 0.0, 0.0]), np.array([0.0, 0.0, 0.7])), gen.Motion.identity()]
+    sc = mini_scenario([donor, rec], [gen.FringeSet(1, ids, [0], "ties")], motions,
+                       dtype=np.float64 if xi_dtype == ovs.OVS_F64 else np.float32)
+    _, _, n = run_and_compare(sc, 0, xi_dtype, label="quarter-turn ties")
+    assert n == rec.n_nodes
+    scene = GpuScene(sc, max_points=rec.n_nodes, xi_dtype=xi_dtype)
+    _, d, _ = scene.step(motions, sc.fringe_sets(0), interpolate=False)
+    cell = d["cell"].cpu().numpy()
+    xb = np.stack([rec.y - 0.25, 0.5 - rec.x, rec.z - 0.125], axis=1)  # R^T (x - c), exact on these lattices
+    t = xb * 8
+    ijk = np.clip(np.maximum(0, np.ceil(t - 1 - 1e-10)), 0, 7).astype(np.int64)
+    expect = ijk[:, 0] + 8 * (ijk[:, 1] + 8 * ijk[:, 2])
+    assert np.array_equal(cell, expect)
+
+
 def test_ragged_empty_sets_orphans_priority(torch_cuda):
     """Several sets of ragged sizes (0, 1, 31, 33, 257, ...) in one call, an empty set between others, a priority
     list of two donors with fall-through, and points outside every donor (orphans)."""
