@@ -484,8 +484,10 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
         ext[a] = g.hi[a] - g.lo[a];
         mean[a] = std::max(h9[6 + a] / (double)L.ncells, 1e-12 * ext_max + 1e-300);
     }
-    // bins about two mean cell extents wide, at most one bin per cell
-    double scale = 2.0;
+    // bins about 0.6 mean cell extents wide, at most one bin per cell (retried coarser if that exceeds the bin or
+    // registration capacity): fine enough that the control cells of crowded regions (an O-grid's polar axis, thin
+    // near-wall cells) list few cells, which bounds the exhaustive search and makes cold starts close
+    double scale = 0.6;
     int64_t nreg = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
         int64_t nb_tot = 1;

@@ -27,7 +27,7 @@ namespace ovs {
 namespace {
 
 constexpr int kAsmThreads = 256;
-constexpr int kAsmMinBlocks = 3;
+constexpr int kAsmMinBlocks = 2;  // 128 registers a thread: no spills (3 blocks spill about 0.6 KB a thread)
 
 enum WalkResult { kWalkFound = 0, kWalkStuck = 1 };
 
@@ -298,7 +298,8 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
                 }
             }
         }
-        gcell = learned_guess(P, G, gs, want, gd0, xn);
+        // the network only for warps that have a point needing it (the call saves the warp's registers)
+        if (__ballot_sync(0xffffffffu, want)) gcell = learned_guess(P, G, gs, want, gd0, xn);
         if (P.guess_used) warp_add(P.guess_used, gcell >= 0 ? 1u : 0u);
     }
     if (active) {
@@ -777,6 +778,9 @@ __device__ __forceinline__ void slow_stuck_body(const StepParams& S, const GridD
     __shared__ int found;
     __shared__ long long fcell;
     __shared__ double fuvw[3];
+    __shared__ double3 sp64;   // the point in the donor's frame: FP64 (the decision's), and as FP32 pairs
+    __shared__ ff spf[3];
+    __shared__ long long sbin;
     const uint32_t count = min(P.queue_count[1], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
     const int warp = threadIdx.x >> 5;
@@ -789,15 +793,27 @@ __device__ __forceinline__ void slow_stuck_body(const StepParams& S, const GridD
         for (int di = sp.di0; di < s.ndonor && !done; ++di) {
             const int gd = s.donors[di];
             const GridDev& g = G[gd];
-            const double3 p = point64(P, G, sp, gd);
-            const int64_t b = point_bin(g, p);
-            if (b < 0) continue;  // outside the bins' box: no cell of this grid holds the point
-            ff pf[3];
-            if (!point_ff(P, G, sp, di, pf)) {
-                pf[0] = split_double(p.x);
-                pf[1] = split_double(p.y);
-                pf[2] = split_double(p.z);
+            // the point and its control cell, by one thread (FP64 is slow here) for the whole block
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const double3 p0 = point64(P, G, sp, gd);
+                sbin = point_bin(g, p0);
+                ff q[3];
+                if (!point_ff(P, G, sp, di, q)) {
+                    q[0] = split_double(p0.x);
+                    q[1] = split_double(p0.y);
+                    q[2] = split_double(p0.z);
+                }
+                sp64 = p0;
+                spf[0] = q[0];
+                spf[1] = q[1];
+                spf[2] = q[2];
             }
+            __syncthreads();
+            const double3 p = sp64;
+            const int64_t b = sbin;
+            if (b < 0) continue;  // outside the bins' box: no cell of this grid holds the point
+            const ff pf[3] = {spf[0], spf[1], spf[2]};
             if (threadIdx.x == 0) {
                 ncand = 0;
                 found = 0;

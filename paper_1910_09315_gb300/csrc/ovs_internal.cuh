@@ -544,104 +544,117 @@ static __device__ __noinline__ bool newton64_contains(const GridDev& g, int64_t 
 }
 
 // The donor predicate in FP32-pair arithmetic (~44 significant bits) on the node coordinates' FP32 pairs,
-// started at (u,v,w): the same Newton iteration as newton64_contains, converged when a step is <= 1e-12, or when
-// the steps stop shrinking quadratically below 1e-9 (they have reached the pair arithmetic's rounding noise,
-// which in thin or badly scaled cells lies above 1e-12: the iterate is then accurate to about that step).
-// Returns 1 (the cell holds the point), 0 (it does not) or -1 (undecided: not converged; the noise so large
-// (> 1e-11) that the FP64 definition, 2^8 times less noisy, might itself not reach its 1e-13 tolerance; or a
-// local coordinate within the band of a window bound, where only the FP64 predicate may decide).  Away from
-// that band the FP64 definition gives the same answer, because the two iterations agree to within the band.
+// started at (u,v,w): Newton's iteration for the trilinear map with the residual F(xi) = x(xi) - p formed in
+// FP32 pairs (the map as the weights N_a(xi) of the corners' offsets X_a - X_0) and the step solved with the
+// Jacobian in FP32 (iterative refinement: an FP32 Jacobian changes only how fast the steps shrink, by a factor of
+// about 1e-7 times its condition number per step, not where they lead).  Converged when a step is <= 1e-12, or
+// when the steps stop shrinking geometrically below 1e-9 (they have reached the pair arithmetic's rounding noise).
+// Returns 1 (the cell holds the point), 0 (it does not) or -1 (undecided: not converged; the steps shrinking by
+// less than a factor 0.9; the noise so large (> 1e-11) that the FP64 definition might itself not reach its 1e-13
+// tolerance; or a local coordinate within the band of a window bound, where only the FP64 predicate may decide).
+// Away from that band the FP64 definition gives the same answer, because both iterations approach the same root
+// to within the band.
 static __device__ __noinline__ int newton_ff(const GridDev& g, int64_t cell, const ff p[3], float u0, float v0, float w0,
-                                         double& u, double& v, double& w) {
+                                             double& u, double& v, double& w) {
     int i, j, k;
     cell_ijk(g, cell, i, j, k);
     const int64_t nn = g.nnodes;
-    ff X0[3], A[7][3], d[3];
-    ff E[8][3];
+    ff X0[3], E[7][3], d[3];
+    float A[7][3];  // FP32 monomial coefficients of the map (for the Jacobian)
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        int64_t nd = corner_node(g, i, j, k, a);
+    for (int c = 0; c < 3; ++c) {
+        const int64_t n0 = corner_node(g, i, j, k, 0);
+        X0[c] = {__ldg(g.xff + 2 * c * nn + n0), __ldg(g.xff + (2 * c + 1) * nn + n0)};
+    }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) E[a][c] = {__ldg(g.xff + 2 * c * nn + nd), __ldg(g.xff + (2 * c + 1) * nn + nd)};
+    for (int a = 1; a < 8; ++a) {
+        const int64_t nd = corner_node(g, i, j, k, a);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            E[a - 1][c] = ff_sub({__ldg(g.xff + 2 * c * nn + nd), __ldg(g.xff + (2 * c + 1) * nn + nd)}, X0[c]);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        X0[c] = E[0][c];
-        ff e1 = ff_sub(E[1][c], X0[c]), e2 = ff_sub(E[2][c], X0[c]), e3 = ff_sub(E[3][c], X0[c]),
-           e4 = ff_sub(E[4][c], X0[c]), e5 = ff_sub(E[5][c], X0[c]), e6 = ff_sub(E[6][c], X0[c]),
-           e7 = ff_sub(E[7][c], X0[c]);
+        const float e1 = E[0][c].hi, e2 = E[1][c].hi, e3 = E[2][c].hi, e4 = E[3][c].hi, e5 = E[4][c].hi,
+                    e6 = E[5][c].hi, e7 = E[6][c].hi;
         A[0][c] = e1;
         A[1][c] = e2;
         A[2][c] = e4;
-        A[3][c] = ff_sub(ff_sub(e3, e1), e2);
-        A[4][c] = ff_sub(ff_sub(e6, e2), e4);
-        A[5][c] = ff_sub(ff_sub(e5, e1), e4);
-        A[6][c] = ff_add(ff_add(ff_add(ff_sub(ff_sub(ff_sub(e7, e3), e5), e6), e1), e2), e4);
+        A[3][c] = e3 - e1 - e2;
+        A[4][c] = e6 - e2 - e4;
+        A[5][c] = e5 - e1 - e4;
+        A[6][c] = e7 - e3 - e5 - e6 + e1 + e2 + e4;
         d[c] = ff_sub(p[c], X0[c]);
     }
     ff U = {u0, 0.f}, V = {v0, 0.f}, W = {w0, 0.f};
     bool conv = false;
-    float m_prev = 3.4e38f, m_noise = 0.f;
+    float m_prev = 3.4e38f, m_noise = 0.f, rho = 0.f;
 #pragma unroll 1
     for (int it = 0; it < kNewtonMaxIt64; ++it) {
-        ff uv = ff_mul(U, V), vw = ff_mul(V, W), uw = ff_mul(U, W), uvw = ff_mul(uv, W);
-        ff F[3], Ju[3], Jv[3], Jw[3];
+        // residual: sum over corners a = 1..7 of N_a(xi) (X_a - X_0), minus (p - X_0)
+        const ff one = {1.f, 0.f};
+        const ff mu = ff_sub(one, U), mv = ff_sub(one, V), mw = ff_sub(one, W);
+        const ff b00 = ff_mul(mu, mv), b10 = ff_mul(U, mv), b01 = ff_mul(mu, V), b11 = ff_mul(U, V);
+        const ff N[7] = {ff_mul(b10, mw), ff_mul(b01, mw), ff_mul(b11, mw), ff_mul(b00, W),
+                         ff_mul(b10, W),  ff_mul(b01, W),  ff_mul(b11, W)};
+        float F[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ff f = ff_sub(ff_mul(A[0][c], U), d[c]);
-            f = ff_add(f, ff_mul(A[1][c], V));
-            f = ff_add(f, ff_mul(A[2][c], W));
-            f = ff_add(f, ff_mul(A[3][c], uv));
-            f = ff_add(f, ff_mul(A[4][c], vw));
-            f = ff_add(f, ff_mul(A[5][c], uw));
-            F[c] = ff_add(f, ff_mul(A[6][c], uvw));
-            Ju[c] = ff_add(ff_add(ff_add(A[0][c], ff_mul(A[3][c], V)), ff_mul(A[5][c], W)), ff_mul(A[6][c], vw));
-            Jv[c] = ff_add(ff_add(ff_add(A[1][c], ff_mul(A[3][c], U)), ff_mul(A[4][c], W)), ff_mul(A[6][c], uw));
-            Jw[c] = ff_add(ff_add(ff_add(A[2][c], ff_mul(A[4][c], V)), ff_mul(A[5][c], U)), ff_mul(A[6][c], uv));
+            ff f = ff_neg(d[c]);
+#pragma unroll
+            for (int a = 0; a < 7; ++a) f = ff_add(f, ff_mul(N[a], E[a][c]));
+            F[c] = __fadd_rn(f.hi, f.lo);
         }
-        ff cvw[3], cwu[3], cuv[3];
+        // step with the FP32 Jacobian at the FP32 iterate
+        const float fu = U.hi, fv = V.hi, fw = W.hi;
+        float Ju[3], Jv[3], Jw[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-            cvw[c] = ff_sub(ff_mul(Jv[c1], Jw[c2]), ff_mul(Jv[c2], Jw[c1]));
-            cwu[c] = ff_sub(ff_mul(Jw[c1], Ju[c2]), ff_mul(Jw[c2], Ju[c1]));
-            cuv[c] = ff_sub(ff_mul(Ju[c1], Jv[c2]), ff_mul(Ju[c2], Jv[c1]));
+            Ju[c] = fmaf(A[3][c], fv, fmaf(A[5][c], fw, fmaf(A[6][c], fv * fw, A[0][c])));
+            Jv[c] = fmaf(A[3][c], fu, fmaf(A[4][c], fw, fmaf(A[6][c], fu * fw, A[1][c])));
+            Jw[c] = fmaf(A[4][c], fv, fmaf(A[5][c], fu, fmaf(A[6][c], fu * fv, A[2][c])));
         }
-        ff det = ff_add(ff_add(ff_mul(Ju[0], cvw[0]), ff_mul(Ju[1], cvw[1])), ff_mul(Ju[2], cvw[2]));
-        if (!(fabsf(det.hi) > 0.f)) return 0;
-        ff nu = ff_add(ff_add(ff_mul(F[0], cvw[0]), ff_mul(F[1], cvw[1])), ff_mul(F[2], cvw[2]));
-        ff nv = ff_add(ff_add(ff_mul(F[0], cwu[0]), ff_mul(F[1], cwu[1])), ff_mul(F[2], cwu[2]));
-        ff nw = ff_add(ff_add(ff_mul(F[0], cuv[0]), ff_mul(F[1], cuv[1])), ff_mul(F[2], cuv[2]));
-        ff du = ff_neg(ff_div(nu, det)), dv = ff_neg(ff_div(nv, det)), dw = ff_neg(ff_div(nw, det));
-        U = ff_add(U, du);
-        V = ff_add(V, dv);
-        W = ff_add(W, dw);
-        float m = fmaxf(ff_abs_f(du), fmaxf(ff_abs_f(dv), ff_abs_f(dw)));
+        const float cvw[3] = {Jv[1] * Jw[2] - Jv[2] * Jw[1], Jv[2] * Jw[0] - Jv[0] * Jw[2], Jv[0] * Jw[1] - Jv[1] * Jw[0]};
+        const float cwu[3] = {Jw[1] * Ju[2] - Jw[2] * Ju[1], Jw[2] * Ju[0] - Jw[0] * Ju[2], Jw[0] * Ju[1] - Jw[1] * Ju[0]};
+        const float cuv[3] = {Ju[1] * Jv[2] - Ju[2] * Jv[1], Ju[2] * Jv[0] - Ju[0] * Jv[2], Ju[0] * Jv[1] - Ju[1] * Jv[0]};
+        const float det = Ju[0] * cvw[0] + Ju[1] * cvw[1] + Ju[2] * cvw[2];
+        if (!(fabsf(det) > 0.f)) return -1;
+        const float inv = -__frcp_rn(det);
+        const float du = (F[0] * cvw[0] + F[1] * cvw[1] + F[2] * cvw[2]) * inv;
+        const float dv = (F[0] * cwu[0] + F[1] * cwu[1] + F[2] * cwu[2]) * inv;
+        const float dw = (F[0] * cuv[0] + F[1] * cuv[1] + F[2] * cuv[2]) * inv;
+        U = ff_add(U, {du, 0.f});
+        V = ff_add(V, {dv, 0.f});
+        W = ff_add(W, {dw, 0.f});
+        const float m = fmaxf(fabsf(du), fmaxf(fabsf(dv), fabsf(dw)));
         if (!(m < 1e30f) || !ff_finite(U) || !ff_finite(V) || !ff_finite(W)) return 0;
         if (m <= 1e-12f) {
             conv = true;
+            rho = m_prev < 3e38f ? m / m_prev : 0.f;
             break;
         }
-        if (m < 1e-9f && m > 0.5f * m_prev) {  // no longer quadratic: at the rounding noise
+        if (m < 1e-9f && m > 0.5f * m_prev) {  // no longer shrinking fast: at the rounding noise (or contracting slowly)
             conv = true;
             m_noise = m;
+            rho = m / m_prev;
             break;
         }
         m_prev = m;
     }
-    if (!conv || m_noise > 1e-11f) return -1;
+    // a slow contraction (a nearly singular FP32 Jacobian) leaves the iterate up to m rho / (1 - rho) away
+    if (!conv || m_noise > 1e-11f || rho >= 0.9f) return -1;
     // undecided band: 1e-12 plus the FP32-pair error of the point and corners (~4e-14 of the coordinates'
-    // magnitude) measured in local-coordinate units of the cell's shortest edge; at least 8 times the last step
-    // when the iteration stopped at its rounding noise
+    // magnitude) measured in local-coordinate units of the cell's shortest edge; at least 8 times the distance the
+    // remaining steps can still move the iterate when the iteration stopped at its rounding noise
     float pm = fmaxf(fabsf(p[0].hi), fmaxf(fabsf(p[1].hi), fabsf(p[2].hi))) +
                fmaxf(fabsf(X0[0].hi), fmaxf(fabsf(X0[1].hi), fabsf(X0[2].hi)));
     float hmin = 3.4e38f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        float n2 = A[q][0].hi * A[q][0].hi + A[q][1].hi * A[q][1].hi + A[q][2].hi * A[q][2].hi;
+        float n2 = A[q][0] * A[q][0] + A[q][1] * A[q][1] + A[q][2] * A[q][2];
         hmin = fminf(hmin, sqrtf(n2));
     }
-    const float band = fmaxf(1e-12f + 4e-14f * pm / hmin, 8.f * m_noise);
+    const float band = fmaxf(1e-12f + 4e-14f * pm / hmin, 8.f * m_noise / (1.f - rho));
     ff q[3] = {U, V, W};
     bool in = true, amb = false;
 #pragma unroll
