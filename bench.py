@@ -44,7 +44,7 @@ BYTES_POINT = BYTES_ASSEMBLE + BYTES_INTERP
 BYTES_FUSED = BYTES_ASSEMBLE + 128 + 16
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_assemble_cfg4.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1910_09315_gb300", "csrc", f) for f in
-                  ("ovs_assemble.cu", "ovs_internal.cuh", "ovs_fields.cuh")]
+                  ("ovs_assemble.cu", "ovs_internal.cuh", "ovs_fields.cuh", "ovs_mlp.cuh")]
 WORKLOADS = {
     "cfg1": "moving ellipsoid: stretched curvilinear bg 128^3 + O-grid 96x64x64, 100 steps dt=1e-3, FP32 fields",
     "cfg0": "tiny: Cartesian bg 64^3 + rotated perturbed box 32^3, FP64 fields",
@@ -100,6 +100,13 @@ def rank0_choice(world: int, flag: bool, device="cpu") -> bool:
     t = torch.tensor([1 if flag else 0], dtype=torch.int32, device=device)
     torch.distributed.broadcast(t, 0)
     return bool(t.item())
+
+
+def _gen_surface(dims, periodic):
+    """The closed shell between a body O-grid's two outer radial layers (all azimuths, all polar rings)."""
+    import gen
+
+    return gen.index_box_surface(dims, periodic, (0, 0, dims[2] - 2), (dims[0], dims[1] - 1, dims[2] - 1))
 
 
 def guess_label(choice) -> str:
@@ -565,6 +572,40 @@ def run_ovs(args, rank, world, local):
                  "ms_per_step_one_call_per_body": ev_h[2].elapsed_time(ev_h[3]) / reps,
                  "note": "one ovs_hole_cut_many launch for all bodies (mask fill included)"}
         ovs.ovs_set_iblank(ctx.ctx, gids[0], None)
+    # fluxes at the receivers (paper Sec. 2.1 eq. flux, Sec. 2.4 mass conservation): after one step, every body
+    # grid's interpolated fringe velocities are placed in its node arrays (outside the timing) and the flux through
+    # the closed shell between its two fringe layers is reconstructed and corrected, one call per body grid
+    fluxes = None
+    shells = []
+    for q, g in enumerate(sc.grids):
+        if g.role != 1 or g.meta.get("kind") not in ("ogrid", "fish"):
+            continue
+        n = g.dims
+        faces_np, signs_np = _gen_surface(n, g.periodic)
+        shells.append((q, torch.as_tensor(faces_np).to(dev), torch.as_tensor(signs_np).to(dev)))
+    if shells:
+        nW = one_step(W, dev_sets[W])
+        vel = {q: [torch.zeros(sc.grids[q].n_nodes, dtype=fdt, device=dev) for _ in range(3)] for q, _, _ in shells}
+        b = 0
+        for r, ids, _ in dev_sets[W]:
+            k = int(ids.numel())
+            if r in vel:
+                for c in range(3):
+                    vel[r][c].index_copy_(0, ids.long(), outs[c][b:b + k])
+            b += k
+        ev_f = events(2)
+        reps = 10
+        nfaces = sum(int(f.numel()) for _, f, _ in shells)
+        for r in range(reps + 1):
+            if r == 1:
+                ev_f[0].record(stream)
+            for q, f, sg in shells:
+                ctx.interface_flux(gids[q], f, tuple(vel[q]), signs=sg, surf_start=[0, int(f.numel())], correct=True)
+        ev_f[1].record(stream)
+        torch.cuda.synchronize()
+        fluxes = {"grids": len(shells), "faces": nfaces, "ms_per_step": ev_f[0].elapsed_time(ev_f[1]) / reps,
+                  "note": "each body grid's closed shell between its two fringe layers: face fluxes, net flux, "
+                          "correction in proportion to area (one ovs_interface_flux per grid)"}
     learned = None if args.no_learned else learned_vs_plain(guess_choice, ctx, dev_sets, one_step, timed, stream,
                                                             flush, K, W, ovs, torch)
     # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
@@ -633,6 +674,7 @@ def run_ovs(args, rank, world, local):
         "batched_over_unbatched": unbatched_ms / (total_ms / K),
         "learned_vs_plain": learned,
         "interp_matrix": matrix,
+        "interface_flux": fluxes,
         "hole_cut": holes,
         "interleaved_fields": interleaved,
     }

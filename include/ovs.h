@@ -179,7 +179,8 @@ const char* ovs_last_error(const ovs_ctx* ctx);
 int ovs_set_stream(ovs_ctx* ctx, void* cuda_stream);
 
 /* Bytes of the context workspace needed for calls of up to `max_points` query points (slow-path
- * queue of two entries per point, counters, status word, step parameters). */
+ * queue of two entries per point, counters, status word, step parameters, and 64 KiB of partial sums for
+ * ovs_interface_flux). */
 int ovs_workspace_size(const ovs_ctx* ctx, int64_t max_points, size_t* bytes);
 /* Attach a caller-owned device workspace (256-byte aligned) of at least ovs_workspace_size bytes. */
 int ovs_workspace_attach(ovs_ctx* ctx, void* dptr, size_t bytes, int64_t max_points);
@@ -387,8 +388,8 @@ int ovs_autotune(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const 
  * must sum to zero, so their imbalance is removed by a correction).
  *   Face id = 3 * (node id of its base corner) + d: the face of constant index along axis d spanned by the axes
  *   a = d+1 and b = d+2 (mod 3); corners base, base + e_a, base + e_a + e_b, base + e_b (wrapped on periodic
- *   axes).  Its area vector S = (corner 2 - corner 0) x (corner 3 - corner 1) / 2 (FP64, from the grid's own
- *   coordinates; it points toward increasing index d on a right-handed grid); the velocity on it is the mean of its
+ *   axes).  Its area vector S = (corner 2 - corner 0) x (corner 3 - corner 1) / 2 (in the precision stated at the
+ *   end; it points toward increasing index d on a right-handed grid); the velocity on it is the mean of its
  *   corners' values; its flux U = u . S, in the grid's own frame.
  * faces: device int64 [nfaces]; signs: device int8 [nfaces], +1 where S points out of the region a surface encloses,
  * -1 where it points in (NULL: all +1); vel: the grid's node velocities u, v, w (p unused; FP32 or FP64, stride as
@@ -396,10 +397,13 @@ int ovs_autotune(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, const 
  * dtype, the faces' fluxes U (not multiplied by the sign).  Closed surfaces: surface s is faces surf_start[s] ..
  * surf_start[s+1]-1 (host int64 [nsurf + 1], nondecreasing, within [0, nfaces]; faces outside every surface only
  * get their flux), at most 64; net: device FP64 [2 nsurf]: the net outward flux sum(sign U) before any correction
- * and the total area sum |S|, summed in a fixed order (reproducible).  correct = 1: each face of surface s then
- * gets U - sign * net * |S| / area (the imbalance taken out in proportion to face area), after which the surface's
- * net flux is zero.  Enqueued on the context stream; a face id that leaves the grid is reported by ovs_sync (its
- * flux 0).  Errors: OVS_ERR_ARG (unknown grid, NULL arrays, bad surf_start, correct without surfaces). */
+ * and the total area sum |S|, summed in a fixed order that depends only on nfaces, nsurf and surf_start
+ * (reproducible: blocks sum chunks of consecutive faces, then one block per surface sums its chunks).
+ * correct = 1: each face of surface s then gets U - sign * net * |S| / area (the imbalance taken out in
+ * proportion to face area), after which the surface's net flux is zero.  Enqueued on the context stream; a face id that leaves the grid is reported by ovs_sync (its
+ * flux 0).  The face areas are formed in FP64 from the grid's coordinates for FP64 velocities and in FP32 from
+ * their FP32 pairs for FP32 velocities.  Errors: OVS_ERR_ARG (unknown grid, NULL arrays, bad surf_start, correct
+ * without surfaces). */
 int ovs_interface_flux(ovs_ctx* ctx, int32_t grid_id, int64_t nfaces, const int64_t* faces, const int8_t* signs,
                        int32_t nsurf, const int64_t* surf_start, const ovs_fields* vel, void* flux, double* net,
                        int32_t correct);

@@ -51,6 +51,7 @@ struct ovs_ctx {
     int32_t* d_err = nullptr;
     uint32_t* d_qcount = nullptr;
     SlowEntry* d_queue = nullptr;
+    double* d_flux_part = nullptr;  // chunk sums of ovs_interface_flux
     // grids
     int ngrids = 0;
     GridDev grids[OVS_MAX_GRIDS];
@@ -379,6 +380,7 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     // again for the exhaustive search)
     off = align_up(off + (size_t)std::max<int64_t>(1, 2 * max_points) * sizeof(SlowEntry));
     off = align_up(off + sizeof(StepParams));
+    off = align_up(off + 2 * sizeof(double) * kFluxChunks);
     *bytes = off;
     return OVS_OK;
 }
@@ -406,6 +408,8 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     off = align_up(off + (size_t)std::max<int64_t>(1, 2 * max_points) * sizeof(SlowEntry));
     c->d_step = (StepParams*)(base + off);
     off = align_up(off + sizeof(StepParams));
+    c->d_flux_part = (double*)(base + off);
+    off = align_up(off + 2 * sizeof(double) * kFluxChunks);
     c->ws = dptr;
     c->ws_bytes = bytes;
     c->max_points = max_points;
@@ -801,7 +805,7 @@ void fill_interp(const ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
 }
 
 // Kinds of call (bit set): which kernels a call launches.
-constexpr uint32_t kStepAssemble = 1, kStepInterp = 2, kStepInterpF64 = 4, kStepNoAlloc = 8;
+constexpr uint32_t kStepAssemble = 1, kStepInterp = 2, kStepInterpF64 = 4, kStepNoAlloc = 8, kStepMlp = 16;
 
 // The learned guess of a call: with OVS_GUESS_MLP / OVS_GUESS_MLP_ONLY, every grid's network (width, box, input
 // normalisation as in its header, region) for the assembly kernel, which evaluates it for the points that have no
@@ -849,8 +853,9 @@ cudaError_t enqueue_step(ovs_ctx* c, int b, uint32_t kind, uint32_t* qcount, cud
     if (kind & kStepAssemble) {
         // with fields, the assembly kernels interpolate every point as they decide its donor (one pass)
         const int im = (kind & kStepInterp) ? ((kind & kStepInterpF64) ? 2 : 1) : 0;
-        e = launch_assemble(c->d_step, im, qcount, c->d_grids, c->nsm, c->tune.assemble_blocks_per_sm,
-                            c->tune.slow_blocks_per_sm, st, trace ? c->trace : nullptr);
+        e = launch_assemble(c->d_step, im, (kind & kStepMlp) != 0, qcount, c->d_grids, c->nsm,
+                            c->tune.assemble_blocks_per_sm, c->tune.slow_blocks_per_sm, st,
+                            trace ? c->trace : nullptr);
         if (e != cudaSuccess || !im) return e;
         if (trace && c->trace[3]) cudaEventRecord(c->trace[3], st);
         if (trace && c->trace[4]) cudaEventRecord(c->trace[4], st);
@@ -955,8 +960,7 @@ int assemble_impl(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, const o
     fill_sets(sets, nsets, P->s);
     fill_xforms(c, sets, nsets, P->xf);
     memcpy(P->m, c->motion, sizeof P->m);
-    fill_guess(c, P);
-    uint32_t kind = kStepAssemble;
+    uint32_t kind = kStepAssemble | (fill_guess(c, P) ? kStepMlp : 0u);
     if (fout) {
         memset(&S.i, 0, offsetof(InterpParams, s));
         fill_interp(c, sets, nsets, out, fields, fout, total, &S.i);
@@ -1417,6 +1421,19 @@ int ovs_interface_flux(ovs_ctx* c, int32_t gid, int64_t nfaces, const int64_t* f
         if (surf_start[s] < 0 || surf_start[s + 1] < surf_start[s] || surf_start[s + 1] > nfaces)
             return fail(c, OVS_ERR_ARG, "surf_start must be nondecreasing within [0, nfaces]");
     for (int s = 0; nsurf > 0 && s <= nsurf; ++s) P.surf_start[s] = surf_start[s];
+    // chunks of consecutive faces of one surface, each summed by one block: at least 1024 faces, and few enough
+    // that every surface's chunks fit the kFluxChunks partial sums
+    if (nsurf > 0) {
+        const int64_t in_surf = surf_start[nsurf] - surf_start[0];
+        int64_t L = std::max<int64_t>(1024, (in_surf + (kFluxChunks - nsurf) - 1) / (kFluxChunks - nsurf));
+        L = (L + 255) / 256 * 256;
+        if (L > INT32_MAX / 2) return fail(c, OVS_ERR_ARG, "%lld faces on the surfaces", (long long)in_surf);
+        P.chunk = (int32_t)L;
+        P.chunk_start[0] = 0;
+        for (int s = 0; s < nsurf; ++s)
+            P.chunk_start[s + 1] = P.chunk_start[s] + (int32_t)((surf_start[s + 1] - surf_start[s] + L - 1) / L);
+    }
+    P.part = c->d_flux_part;
     P.grid = gid;
     P.nsurf = nsurf;
     P.nfaces = nfaces;
@@ -1607,8 +1624,8 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     fill_sets(sets, nsets, P.s);
     fill_xforms(c, sets, nsets, P.xf);
     memcpy(P.m, c->motion, sizeof P.m);
-    fill_guess(c, &P);
-    cudaError_t e = run_step(c, b, kStepAssemble | kStepNoAlloc, (uint32_t*)base, false);
+    const uint32_t mk = fill_guess(c, &P) ? kStepMlp : 0u;
+    cudaError_t e = run_step(c, b, kStepAssemble | kStepNoAlloc | mk, (uint32_t*)base, false);
     if (e != cudaSuccess) return cuda_fail(c, e, "assemble (no-alloc) launch");
     return OVS_OK;
 }

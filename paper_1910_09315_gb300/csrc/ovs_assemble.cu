@@ -34,8 +34,8 @@ enum WalkResult { kWalkFound = 0, kWalkStuck = 1 };
 // FP32 walk from `cell` toward the donor-frame point xd (FP32 pairs).  On kWalkFound, cell/u/v/w hold a cell
 // whose FP32 local coordinates lie within kAccept32 of [0,1]^3.
 __device__ __forceinline__ int walk32(const GridDev& g, const ff xd[3], int64_t& cell, float& u, float& v, float& w,
-                                      float& tau, int max_walk, int& steps, int& iters, bool& blocked) {
-    int i, j, k;
+                                      float& tau, int max_walk, int& steps, int& iters, bool& blocked, int& i, int& j,
+                                      int& k) {
     cell_ijk(g, cell, i, j, k);
     u = v = w = 0.5f;
 #pragma unroll 1
@@ -227,7 +227,7 @@ __device__ __noinline__ int64_t learned_guess(const AsmParams& P, const GridDev*
 
 // One query point per thread (t may lie past the end: the lane then only takes part in the warp's collective
 // steps).  All lanes of a warp call it together.
-template <int IM>
+template <int IM, bool MLP>
 __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDev* __restrict__ G, GuessStage& gs,
                                                const int64_t t) {
     using T = typename FieldT<IM>::T;
@@ -242,6 +242,7 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
     bool node_ok = false;
     ff xd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     uint32_t h0 = kNoHint;  // the receiver node's donor at the previous call, loaded with its coordinates
+    float xr32[3] = {0.f, 0.f, 0.f};  // the receiver node's position in its own frame, FP32
     // the set of point t: lane 0 searches the set table for the warp's first point, the other lanes step forward
     // from there (a work item of 32 consecutive points rarely crosses a set boundary)
     {
@@ -262,18 +263,22 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
         ff x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         if (node_ok) {
             const float* xf = gr.xff;
+            // (xr32 below keeps the position in FP32 for the velocity transform of the interpolation)
 #pragma unroll
             for (int c = 0; c < 3; ++c) x[c] = {__ldg(xf + 2 * c * nn + node), __ldg(xf + (2 * c + 1) * nn + node)};
             if (P.guess == OVS_GUESS_HINT) h0 = gr.hint[node];
         }
         xf_apply(P.xf[si], x, xd);
+        xr32[0] = __fadd_rn(x[0].hi, x[0].lo);
+        xr32[1] = __fadd_rn(x[1].hi, x[1].lo);
+        xr32[2] = __fadd_rn(x[2].hi, x[2].lo);
     }
     const bool fast_ok = ff_finite(xd[0]) && ff_finite(xd[1]) && ff_finite(xd[2]);
     // learned guess (not in the paper): points whose first donor grid has a network and that have no usable hint
     // start where the network says.  Its input needs no more than FP32: the point in the donor frame, inside the
     // grid's padded box, normalised as in training.
     int64_t gcell = -1;
-    if (P.guess_mlp) {  // uniform over the call
+    if (MLP && P.guess_mlp) {  // uniform over the call
         bool want = false;
         int gd0 = -1;
         float xn[3] = {0.f, 0.f, 0.f};
@@ -359,14 +364,15 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
             }
             float u, v, w, tau = 0.25f;
             bool blocked = false;
+            int ci, cj, ck;
             int r = walk32(g, xd, cell, u, v, w, tau, from_hint ? min(P.max_walk, kHintWalk) : P.max_walk, steps,
-                           iters, blocked);
+                           iters, blocked, ci, cj, ck);
             if (r != kWalkFound && from_hint) {
                 // a walk from the previous donor or the learned guess that got stuck (on the grid's boundary, or
                 // after kHintWalk steps) starts again from the control cell before the exhaustive search
                 cell = control_cell();
                 if (cell < 0) continue;
-                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps, iters, blocked);
+                r = walk32(g, xd, cell, u, v, w, tau, P.max_walk, steps, iters, blocked, ci, cj, ck);
             }
             e.t = (int32_t)t;
             e.di = di;
@@ -386,9 +392,10 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
                     done = true;
                     if (IM) {
                         const InterpParams& I = S.i;
+                        const int ijk[3] = {ci, cj, ck};
                         interp_point<T>(g, gr, I.fields[gd], I.mode, I.mf[gd], I.mf[s.receiver], I.m[gd],
                                         I.m[s.receiver], node, cell, (T)u, (T)v, (T)w, I.out, t,
-                                        di == 0 ? I.va + si : nullptr);
+                                        di == 0 ? I.va + si : nullptr, ijk, xr32);
                     }
                 } else {
                     // near a face (FP64 decision among the neighbours), or FP64 precision (FP64 refinement)
@@ -442,7 +449,7 @@ __device__ __forceinline__ void assemble_point(const StepParams& S, const GridDe
 // Persistent: a fixed grid (a multiple of the SM count, so that a captured step graph fits every call) whose
 // warps take work items of 32 consecutive points of the call (all sets of all grids in one index space) from a
 // counter, so that uneven walks balance across the GPU.
-template <int IM>
+template <int IM, bool MLP>
 __global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const StepParams* __restrict__ Sp,
                                                                          const GridDev* __restrict__ G) {
     const AsmParams& P = Sp->a;
@@ -455,7 +462,7 @@ __global__ void __launch_bounds__(kAsmThreads, kAsmMinBlocks) k_assemble(const S
         if (lane == 0) base = atomicAdd(P.queue_count + 2, 32u);
         base = __shfl_sync(0xffffffffu, base, 0);
         if ((int64_t)base >= total) break;
-        assemble_point<IM>(*Sp, G, gs, (int64_t)base + lane);
+        assemble_point<IM, MLP>(*Sp, G, gs, (int64_t)base + lane);
     }
 }
 
@@ -904,17 +911,25 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const StepParams* _
 
 }  // namespace
 
-cudaError_t launch_assemble(const StepParams* dS, int interp, uint32_t* queue_count, const GridDev* dgrids, int nsm,
-                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev) {
+cudaError_t launch_assemble(const StepParams* dS, int interp, bool mlp, uint32_t* queue_count, const GridDev* dgrids,
+                            int nsm, int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev) {
     const unsigned ab = (unsigned)(nsm * (asm_bps > 0 ? asm_bps : kAsmMinBlocks));
     const unsigned sb = (unsigned)(nsm * (slow_bps > 0 ? slow_bps : 1));
     // the two queue counters and the work counter
     cudaError_t err = cudaMemsetAsync(queue_count, 0, 3 * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    if (interp == 1) k_assemble<1><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
-    else if (interp == 2) k_assemble<2><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
-    else k_assemble<0><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+    // the learned guess in its own instantiation: without it the kernel holds no call site whose saved
+    // registers would weigh on the plain path
+    if (mlp) {
+        if (interp == 1) k_assemble<1, true><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+        else if (interp == 2) k_assemble<2, true><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+        else k_assemble<0, true><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+    } else {
+        if (interp == 1) k_assemble<1, false><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+        else if (interp == 2) k_assemble<2, false><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+        else k_assemble<0, false><<<ab, kAsmThreads, 0, st>>>(dS, dgrids);
+    }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);

@@ -31,9 +31,8 @@ __device__ __forceinline__ void cross_add(const M w[3], const T r[3], T acc[3], 
 
 // q[0..3] = trilinear interpolation of u, v, w, p at local coordinates (u, v, w) of `cell`
 template <typename T>
-__device__ __forceinline__ void gather8(const GridDev& g, const FieldsDev& F, int64_t cell, T u, T v, T w, T q[4]) {
-    int i, j, k;
-    cell_ijk(g, cell, i, j, k);
+__device__ __forceinline__ void gather8_ijk(const GridDev& g, const FieldsDev& F, int i, int j, int k, T u, T v, T w,
+                                            T q[4]) {
     // corner a = node of (i + di, j + dj, k + dk): the cell's first node plus one offset per set bit (an index
     // that reaches n is on a periodic axis and wraps to 0)
     const int64_t n0 = g.n[0], n01 = (int64_t)g.n[0] * g.n[1];
@@ -77,6 +76,13 @@ __device__ __forceinline__ void gather8(const GridDev& g, const FieldsDev& F, in
         sum(1);  // four contiguous arrays (the multiply folds away)
     else
         sum(F.stride);
+}
+
+template <typename T>
+__device__ __forceinline__ void gather8(const GridDev& g, const FieldsDev& F, int64_t cell, T u, T v, T w, T q[4]) {
+    int i, j, k;
+    cell_ijk(g, cell, i, j, k);
+    gather8_ijk<T>(g, F, i, j, k, u, v, w, q);
 }
 
 // FP32 velocity transform.  The receiver node's position is its FP32 pair (xh + xl) in the receiver frame;
@@ -168,13 +174,17 @@ __device__ __forceinline__ void vel_transform_f64(int mode, const MotionDev& md,
 // Interpolated and transformed (u, v, w, p) of one point at donor (gd, cell, xi), written to out[*][t].
 // T = field type.  Receiver position: FP32 pair (T = float) or FP64 (T = double) of node `node`.  va: the set's
 // affine velocity map when gd is the set's first donor and the fields are FP32 (else NULL: the two transforms).
+// ijk (may be NULL): the cell's indices, when the caller has them; xr (may be NULL): the receiver node's position
+// in its frame in FP32 (hi + lo of its pair), when the caller has it.
 template <typename T>
 __device__ __forceinline__ void interp_point(const GridDev& g, const GridDev& gr, const FieldsDev& F, int mode,
                                              const MotionF& mfd, const MotionF& mfr, const MotionDev& md,
                                              const MotionDev& mr, int32_t node, int64_t cell, T u, T v, T w,
-                                             void* const out[4], int64_t t, const VelAffine* va = nullptr) {
+                                             void* const out[4], int64_t t, const VelAffine* va = nullptr,
+                                             const int* ijk = nullptr, const float* xr = nullptr) {
     T q[4];
-    gather8<T>(g, F, cell, u, v, w, q);
+    if (ijk) gather8_ijk<T>(g, F, ijk[0], ijk[1], ijk[2], u, v, w, q);
+    else gather8<T>(g, F, cell, u, v, w, q);
     if constexpr (sizeof(T) == 4) {
         if (va) {
             const float ud[3] = {q[0], q[1], q[2]};
@@ -182,7 +192,8 @@ __device__ __forceinline__ void interp_point(const GridDev& g, const GridDev& gr
             if (mode == OVS_VEL_RELATIVE) {
                 const int64_t nn = gr.nnodes;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) x[c] = __ldg(gr.xff + 2 * c * nn + node) + __ldg(gr.xff + (2 * c + 1) * nn + node);
+                for (int c = 0; c < 3; ++c)
+                    x[c] = xr ? xr[c] : __ldg(gr.xff + 2 * c * nn + node) + __ldg(gr.xff + (2 * c + 1) * nn + node);
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r)

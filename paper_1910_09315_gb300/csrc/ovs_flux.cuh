@@ -7,6 +7,9 @@
 namespace ovs {
 
 constexpr int kMaxFluxSurfaces = 64;
+// partial sums of a call: at most this many chunks of consecutive surface faces (the context workspace holds
+// their (net, area) pairs)
+constexpr int kFluxChunks = 4096;
 
 struct FluxParams {
     int32_t grid;
@@ -17,9 +20,11 @@ struct FluxParams {
     FieldsDev vel;         // node velocities u, v, w of the grid
     void* flux;            // [nfaces], the fields' type
     double* net;           // [2 nsurf]: net signed flux before the correction, total face area
+    double* part;          // [2 kFluxChunks]: (net, area) of each chunk (context workspace)
     int32_t* err;
-    int32_t pad;
+    int32_t chunk;                              // faces per chunk (a multiple of 256)
     int64_t surf_start[kMaxFluxSurfaces + 1];
+    int32_t chunk_start[kMaxFluxSurfaces + 1];  // surface s owns chunks chunk_start[s] .. chunk_start[s+1]-1
 };
 
 cudaError_t launch_flux(const FluxParams& P, bool f64, const GridDev* dgrids, int nsm, bool correct, cudaStream_t st);

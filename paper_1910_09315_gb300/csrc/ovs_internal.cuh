@@ -706,8 +706,8 @@ size_t scan_scratch_elems(int64_t n);
 // interp: 0 assembly only; 1 / 2: the kernels also interpolate FP32 / FP64 fields (dS->i) for every point they
 // decide.  asm_bps / slow_bps: blocks per SM of the persistent assembly grid and of each half of the slow-path
 // grid (0: defaults)
-cudaError_t launch_assemble(const StepParams* dS, int interp, uint32_t* queue_count, const GridDev* dgrids, int nsm,
-                            int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev);
+cudaError_t launch_assemble(const StepParams* dS, int interp, bool mlp, uint32_t* queue_count, const GridDev* dgrids,
+                            int nsm, int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev);
 // blocks of k_interp resident per SM (occupancy calculator), or a negative CUDA error
 int interp_default_blocks_per_sm(bool f64);
 // bps: blocks per SM of the persistent grid (0: the occupancy calculator's figure)

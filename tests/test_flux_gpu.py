@@ -2,12 +2,14 @@
 
 * face fluxes U = u . S (S = half the cross product of the face diagonals, u = the corners' mean) on a stretched
   curvilinear grid and on the O-grid, whose closed shell surface wraps around its periodic axis; FP64 and FP32
-  velocities; several closed surfaces in one call with loose faces beside them; nets, areas and corrected fluxes;
+  velocities; several closed surfaces in one call (one of them empty, the others summed in several chunks) with
+  loose faces beside them; nets, areas and corrected fluxes;
 * the chain of one time step: the O-grid's fringe velocities interpolated from the background (GPU: the fused
   call; oracle: its own interpolation), then the flux through the O-grid's interface shell and its correction;
 * a face id that leaves the grid is reported by ovs_sync.
-Tolerances: fluxes |U - U_ref| <= tol * (|u|max |S| of the face), tol = 1e-12 (FP64) / 1e-5 (FP32); nets and
-areas relative 1e-12 (FP64 velocities) / 1e-5 (FP32, to the sum of |U|); corrected net flux zero to the same.
+Tolerances: fluxes |U - U_ref| <= tol * (|u|max |S| of the face), tol = 1e-12 (FP64) / 1e-5 (FP32: the face areas
+are formed in FP32 from the coordinates' FP32 pairs); nets to tol of the sum of |U|, areas to tol relative;
+corrected net flux zero to the same.
 """
 import numpy as np
 import pytest
@@ -51,7 +53,7 @@ def compare(g, faces, signs, starts, vel, got, nets, got_c, tol):
         sl = slice(starts[s], starts[s + 1])
         scale = np.sum(np.abs(U[sl]))
         assert abs(nets[2 * s] - nref[s]) <= tol * scale
-        assert abs(nets[2 * s + 1] - aref[s]) <= 1e-12 * aref[s]
+        assert abs(nets[2 * s + 1] - aref[s]) <= tol * aref[s]  # areas: FP64 for FP64 velocities, else FP32
         assert np.all(np.abs(got_c[sl] - Uc[sl]) <= tol * umax * S[sl] + tol * scale * S[sl] / aref[s])
         assert abs(np.sum(signs[sl] * got_c[sl])) <= 4 * tol * scale
     loose = np.ones(len(faces), bool)
@@ -77,7 +79,8 @@ def test_face_fluxes_and_correction_match_oracle(torch_cuda, dtype):
         extra = (3 * (ijk[0] + n[0] * (ijk[1] + n[1] * ijk[2])) + rng.integers(0, 3, 500)).astype(np.int64)
         faces = np.concatenate([parts[0][0], parts[1][0], extra])
         signs = np.concatenate([parts[0][1], parts[1][1], np.ones(len(extra), np.int8)]).astype(np.int8)
-        starts = [0, len(parts[0][0]), len(parts[0][0]) + len(parts[1][0])]
+        # the second surface is empty (no faces): its net and area are 0 and nothing is corrected
+        starts = [0, len(parts[0][0]), len(parts[0][0]), len(parts[0][0]) + len(parts[1][0])]
         xyz = g.xyz()
         vel = (np.sin(3 * xyz) + rng.uniform(-0.5, 0.5, xyz.shape)).astype(dtype)
         got, nets = run_flux(scene, gid, faces, signs, starts, vel, correct=False)
