@@ -608,24 +608,9 @@ def run_ovs(args, rank, world, local):
                           "correction in proportion to area (one ovs_interface_flux per grid)"}
     learned = None if args.no_learned else learned_vs_plain(guess_choice, ctx, dev_sets, one_step, timed, stream,
                                                             flush, K, W, ovs, torch)
-    # end-to-end through the public API: host (pinned) node ids in, host fields out, copies inside the timing
-    host_out = [torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)]
-    host_status = torch.empty(max_pts, dtype=torch.uint8).pin_memory()
-    e2e_ms, h2d, d2h = [], 0, 0
-    for s in range(W, W + K):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sets = [(r, ids.to(dev, non_blocking=True), dn) for r, ids, dn in host_sets[s]]
-        n = one_step(s, sets)
-        for o, h in zip(outs, host_out):
-            h[:n].copy_(o[:n], non_blocking=True)
-        host_status[:n].copy_(donors["status"][:n], non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        h2d += 4 * n
-        d2h += n * (4 * outs[0].element_size() + 1)
-    total_ms, e2e_total, pts_all = combine_ranks(world, total_ms, float(np.sum(e2e_ms)), float(pts), dev)
+    e2e_ms, h2d, d2h, e2e_ref = end_to_end(ctx, lib, inputs, host_sets, dev_sets, prep, layout, max_pts, xi_dtype,
+                                           fdt, W, K, flush, stream, dev, ovs, torch)
+    total_ms, e2e_total, pts_all = combine_ranks(world, total_ms, e2e_ms, float(pts), dev)
     stats = None
     if rank == 0:
         ctx.set_options(collect_stats=1)
@@ -666,7 +651,13 @@ def run_ovs(args, rank, world, local):
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)", "bytes_per_point": BYTES_FUSED,
                      "traffic": traffic},
         "e2e": {"value": pts_all / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // K,
-                "d2h_bytes_per_step": d2h // K},
+                "d2h_bytes_per_step": d2h // K,
+                "how": "a time loop through the C ABI: per step one H2D copy of its node ids (pinned), "
+                       "ovs_set_motion per grid + ovs_assemble_interpolate, D2H of u, v, w, p and status (pinned); "
+                       "copies on two copy streams, two device buffer sets alternating, so that step s+1's "
+                       "copy-in and step s-1's copy-out overlap step s's kernels; host wall clock over the K "
+                       "steps, L2 flushed once before",
+                "serial_ms_per_step": e2e_ref},
         "gpu_launches": 3 * K,  # per step: k_assemble, k_slow_near, k_slow_stuck (all interpolating)
         "clocks": ck,
         "walk_stats": stats,
@@ -681,6 +672,113 @@ def run_ovs(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, inputs[W], args.cpu_sample)
     return line
+
+
+def end_to_end(ctx, lib, inputs, host_sets, dev_sets, prep, layout, max_pts, xi_dtype, fdt, W, K, flush, stream,
+               dev, ovs, torch):
+    """End to end: steps W .. W+K-1 from pinned host node ids to pinned host outputs.  The headline drives the
+    C ABI as a C caller's time loop would (structs marshalled once; one H2D copy of the step's node ids on a copy
+    stream; the library's calls on its stream after that copy; the D2H copies of u, v, w, p and status on a
+    second copy stream after the call; two device buffer sets alternating, so that copies of neighbouring steps
+    overlap a step's kernels), timed by the host wall clock over the K steps.  For reference, per-step
+    synchronous figures (ms per step): the same C-ABI calls with each step's copies and kernels in sequence, and
+    the Python binding (one copy per set, the binding's marshalling on every call).  Returns (total ms,
+    H2D bytes, D2H bytes, references)."""
+    ctypes_ = __import__("ctypes")
+    host_ids = [torch.cat([ids for _, ids, _ in host_sets[s]]).pin_memory() for s in range(W + K)]
+    nb = 2
+    dstage = [torch.empty(max_pts, dtype=torch.int32, device=dev) for _ in range(nb)]
+    ddon = [ctx.alloc_donors(max_pts, xi_dtype) for _ in range(nb)]
+    douts = [[torch.empty(max_pts, dtype=fdt, device=dev) for _ in range(4)] for _ in range(nb)]
+    hout = [[torch.empty(max_pts, dtype=fdt).pin_memory() for _ in range(4)] for _ in range(nb)]
+    hstat = [torch.empty(max_pts, dtype=torch.uint8).pin_memory() for _ in range(nb)]
+    # each step's structs, marshalled before timing as a C caller holds them
+    call_args = []
+    for k in range(K):
+        s, b = W + k, k % nb
+        views, off = [], 0
+        for r, ids, dn in dev_sets[s]:
+            m = int(ids.numel())
+            views.append((r, dstage[b][off:off + m], dn))
+            off += m
+        n = off
+        dview = {"grid": ddon[b]["grid"][:n], "cell": ddon[b]["cell"][:n], "xi": ddon[b]["xi"][:3 * n],
+                 "status": ddon[b]["status"][:n], "xi_dtype": xi_dtype, "n": n}
+        farr, ostruct, _ = ctx._fields_structs(layout[0], n, [o[:n] for o in douts[b]])
+        call_args.append((s, b, n, ovs.make_sets(views), len(views), ovs.Context.donors_struct(dview), farr, ostruct,
+                          dview))
+
+    def check(rc):
+        if rc != ovs.OVS_OK:
+            raise ovs.OvsError(rc, ovs.ovs_last_error(ctx.ctx))
+
+    def c_call(k):
+        s, b, n, sarr, ns, dstruct, farr, ostruct, _ = call_args[k]
+        for gid, _, ptrs in prep[s][0]:
+            check(lib.ovs_set_motion(ctx.ctx, gid, *ptrs))
+        check(lib.ovs_assemble_interpolate(ctx.ctx, sarr, ns, ctypes_.byref(dstruct), farr, len(farr),
+                                           ctypes_.byref(ostruct)))
+
+    def copy_out(k):
+        s, b, n = call_args[k][:3]
+        for c in range(4):
+            hout[b][c][:n].copy_(douts[b][c][:n], non_blocking=True)
+        hstat[b][:n].copy_(ddon[b]["status"][:n], non_blocking=True)
+
+    h2d_st, d2h_st = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event() for _ in range(K)]
+    ev_call = [torch.cuda.Event() for _ in range(K)]
+    ev_out = [torch.cuda.Event() for _ in range(K)]
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        s, b, n = call_args[k][:3]
+        with torch.cuda.stream(h2d_st):
+            if k >= nb:
+                h2d_st.wait_event(ev_call[k - nb])  # the call that read this staging buffer has run
+            dstage[b][:n].copy_(host_ids[s], non_blocking=True)
+            ev_in[k].record(h2d_st)
+        stream.wait_event(ev_in[k])
+        if k >= nb:
+            stream.wait_event(ev_out[k - nb])  # this buffer set's outputs of step k-2 are copied out
+        c_call(k)
+        ev_call[k].record(stream)
+        with torch.cuda.stream(d2h_st):
+            d2h_st.wait_event(ev_call[k])
+            copy_out(k)
+            ev_out[k].record(d2h_st)
+    torch.cuda.synchronize()
+    total = (time.perf_counter() - t0) * 1e3
+    h2d = sum(4 * call_args[k][2] for k in range(K))
+    d2h = sum(call_args[k][2] * (4 * douts[0][0].element_size() + 1) for k in range(K))
+    # per-step synchronous references
+    serial, binding = [], []
+    for k in range(K):
+        s, b, n = call_args[k][:3]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        dstage[b][:n].copy_(host_ids[s], non_blocking=True)
+        c_call(k)
+        copy_out(k)
+        torch.cuda.synchronize()
+        serial.append((time.perf_counter() - t) * 1e3)
+    for k in range(K):
+        s, b, n = call_args[k][:3]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sets = [(r, ids.to(dev, non_blocking=True), dn) for r, ids, dn in host_sets[s]]
+        for gid, mo in enumerate(inputs[s][0]):
+            ctx.set_motion(gid, mo.R, mo.c, mo.V, mo.omega)
+        ctx.assemble_interpolate(sets, layout[0], donors=call_args[k][8], out=[o[:n] for o in douts[b]])
+        copy_out(k)
+        torch.cuda.synchronize()
+        binding.append((time.perf_counter() - t) * 1e3)
+    ref = {"c_abi_synchronous": float(np.median(serial)), "python_binding_synchronous": float(np.median(binding)),
+           "note": "medians; each step's H2D copy, calls and D2H copies in sequence, then a synchronisation"}
+    return total, h2d, d2h, ref
 
 
 GUESS_WIDTHS = (32, 64)
