@@ -375,7 +375,7 @@ int ovs_workspace_size(const ovs_ctx* c, int64_t max_points, size_t* bytes) {
     if (!c || !bytes || max_points < 0) return OVS_ERR_ARG;
     size_t off = align_up(sizeof(GridDev) * OVS_MAX_GRIDS);
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
-    off = align_up(off + 4 * sizeof(int32_t));
+    off = align_up(off + (1 + kQueueCounters) * sizeof(int32_t));
     // the slow-path queue: two entries per point (a near-face point the neighbourhood test cannot place is queued
     // again for the exhaustive search)
     off = align_up(off + (size_t)std::max<int64_t>(1, 2 * max_points) * sizeof(SlowEntry));
@@ -402,8 +402,8 @@ int ovs_workspace_attach(ovs_ctx* c, void* dptr, size_t bytes, int64_t max_point
     c->d_counters = (unsigned long long*)(base + off);
     off = align_up(off + sizeof(unsigned long long) * kNumCounters);
     c->d_err = (int32_t*)(base + off);
-    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // near-face queue, stuck queue, work counter
-    off = align_up(off + 4 * sizeof(int32_t));
+    c->d_qcount = (uint32_t*)(base + off + sizeof(int32_t));  // the slow-path queue's counters
+    off = align_up(off + (1 + kQueueCounters) * sizeof(int32_t));
     c->d_queue = (SlowEntry*)(base + off);
     off = align_up(off + (size_t)std::max<int64_t>(1, 2 * max_points) * sizeof(SlowEntry));
     c->d_step = (StepParams*)(base + off);
@@ -1544,6 +1544,7 @@ int ovs_autotune_guess(ovs_ctx* c, const ovs_fringe_set* sets, int32_t nsets, co
 // from cudaGetSymbolAddress, looked up once per device with that device current.
 namespace {
 constexpr size_t kNoAllocHead = 256;
+static_assert(kQueueCounters * sizeof(uint32_t) <= kNoAllocHead, "queue counters fit the head");
 constexpr size_t kNoAllocBytes = kNoAllocHead + 2 * (size_t)OVS_NOALLOC_MAX_POINTS * sizeof(SlowEntry);
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -1617,7 +1618,7 @@ extern "C" int ovs_assemble_noalloc(ovs_ctx* c, const ovs_fringe_set* sets, int3
     P.out_cell = out->cell;
     P.out_xi = out->xi;
     P.out_status = out->status;
-    P.queue_count = (uint32_t*)base;  // three counters, zeroed on the stream by launch_assemble before the kernels
+    P.queue_count = (uint32_t*)base;  // the queue's counters, zeroed on the stream by launch_assemble first
     P.queue = (SlowEntry*)((char*)base + kNoAllocHead);
     P.counters = c->d_counters;
     P.err = c->d_err;

@@ -6,14 +6,13 @@
 //                    strictly inside a cell (every local coordinate at least 1e-4 from a face) are final.
 //                    Points near a face, points in FP64 precision mode and stuck walks are compacted (warp
 //                    ballot + one atomic per warp) into the slow queue.
-//   k_slow_near      one warp per point near a face: the donor predicate (FP32-pair Newton on the node
-//                    coordinates, FP64 where that cannot decide) over the cells sharing the near faces /
-//                    edges / corner, one lane each, lowest linear id first; a point none of them holds is
-//                    appended to the stuck queue.
-//   k_slow_stuck     then, one block per stuck entry: the exhaustive search of the point's control cell of
-//                    Sec. 2.2.5 (the paper's brute-force fallback); all threads filter the list, the exact test
-//                    runs on every survivor at once; it continues with the later grids of the set's priority
-//                    list (Sec. 2.4 item 1).
+//   k_slow           then, in one persistent kernel whose blocks take units from a counter: the stuck entries,
+//                    one block each (the exhaustive search of the point's control cell of Sec. 2.2.5, the paper's
+//                    brute-force fallback: all threads filter the list, the exact test runs on every survivor at
+//                    once; then the later grids of the set's priority list, Sec. 2.4 item 1), and the points near
+//                    a face, one warp each (the donor predicate, FP32-pair Newton on the node coordinates and FP64
+//                    where that cannot decide, over the cells sharing the near faces / edges / corner, one lane
+//                    each, lowest linear id first; a point none of them holds joins the stuck entries).
 //
 // In a call that also interpolates (ovs_assemble_interpolate) the kernels go on, for every point whose donor
 // they decide, to the trilinear interpolation of u, v, w, p and the frame velocity transform (Sec. 2.2.6,
@@ -726,187 +725,230 @@ __device__ __forceinline__ void finish_none(const StepParams& S, int64_t t) {
     if (IM) zero_point<typename FieldT<IM>::T>(S.i.out, t);
 }
 
-// Points near a face: one warp each, one lane per candidate cell (the cells sharing the near faces / edges /
-// corner, lowest id first).  A point none of them holds goes on to the stuck queue, where the exhaustive search
-// of its control cell (and the later grids of its list) runs a block wide: a warp alone would walk a crowded
-// control cell in a long chain of dependent loads.
+// The slow-path queue entry at index q (near-face entries from the front, stuck entries from the back), read
+// past L1: entries appended during the kernel may share a line that this SM has cached before they were written.
+__device__ __forceinline__ SlowEntry load_entry(const SlowEntry* e) {
+    const int* w = reinterpret_cast<const int*>(e);
+    SlowEntry r;
+    r.t = __ldcg(w);
+    r.di = __ldcg(w + 1);
+    r.cell = __ldcg(w + 2);
+    r.xi[0] = __int_as_float(__ldcg(w + 3));
+    r.xi[1] = __int_as_float(__ldcg(w + 4));
+    r.xi[2] = __int_as_float(__ldcg(w + 5));
+    return r;
+}
+
+// A point near a face, by one warp: one lane per candidate cell (the cells sharing the near faces / edges /
+// corner, lowest id first).  A point none of them holds is appended to the stuck entries (lane 0), for the
+// exhaustive search of its control cell (and the later grids of its list), which runs a block wide: a warp alone
+// would walk a crowded control cell in a long chain of dependent loads.  Returns true if decided here.
 template <int IM>
-__device__ __forceinline__ void slow_near_body(const StepParams& S, const GridDev* __restrict__ G, unsigned bid,
-                                               unsigned nblk) {
+__device__ __forceinline__ bool near_entry(const StepParams& S, const GridDev* __restrict__ G, uint32_t q,
+                                           uint32_t n_near, uint32_t n_stuck0) {
     const AsmParams& P = S.a;
-    const uint32_t count = min(P.queue_count[0], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
-    unsigned nref = 0;
-    for (uint32_t q = bid * kSlowWarps + (threadIdx.x >> 5); q < count; q += nblk * kSlowWarps) {
-        const SlowEntry e = P.queue[q];
-        const SlowPoint sp = slow_point(P, e);
-        const int gd = P.s[sp.si].donors[sp.di0];
-        const GridDev& g = G[gd];
-        auto p64 = [&]() { return point64(P, G, sp, gd); };
-        ff pf[3];
-        const bool pf_ok = point_ff(P, G, sp, sp.di0, pf);
-        int64_t cell = -1;
-        double u = 0, v = 0, w = 0;
-        bool ok = false;
-        if (pf_ok) ok = neighbourhood_warp(g, pf, p64, e.cell, sp.mask0, e.xi, cell, u, v, w);
-        if (ok) {
-            if (lane == 0) finish<IM>(S, G, sp, gd, cell, u, v, w, OVS_STATUS_FOUND | OVS_STATUS_REFINED);
-            ++nref;
-        } else if (lane == 0) {
-            // to the back of the queue, below the near-face entries (which this kernel is still reading)
-            const uint32_t idx = atomicAdd(P.queue_count + 1, 1u);
-            if ((int64_t)idx < P.queue_cap - (int64_t)count) {
-                SlowEntry r = e;
-                r.di = sp.di0;
-                r.cell = -1;
-                r.xi[0] = r.xi[1] = r.xi[2] = 0.5f;
-                P.queue[P.queue_cap - 1 - idx] = r;
-            } else {
-                atomicOr(P.err, kErrQueueOverflow);
-            }
+    const SlowEntry e = P.queue[q];
+    const SlowPoint sp = slow_point(P, e);
+    const int gd = P.s[sp.si].donors[sp.di0];
+    const GridDev& g = G[gd];
+    auto p64 = [&]() { return point64(P, G, sp, gd); };
+    ff pf[3];
+    const bool pf_ok = point_ff(P, G, sp, sp.di0, pf);
+    int64_t cell = -1;
+    double u = 0, v = 0, w = 0;
+    bool ok = false;
+    if (pf_ok) ok = neighbourhood_warp(g, pf, p64, e.cell, sp.mask0, e.xi, cell, u, v, w);
+    if (ok) {
+        if (lane == 0) finish<IM>(S, G, sp, gd, cell, u, v, w, OVS_STATUS_FOUND | OVS_STATUS_REFINED);
+    } else if (lane == 0) {
+        // behind the stuck entries of the assembly kernel, in the back of the queue (the near-face entries hold
+        // the front)
+        const uint32_t idx = n_stuck0 + atomicAdd(P.queue_count + 5, 1u);
+        if ((int64_t)idx < P.queue_cap - (int64_t)n_near) {
+            SlowEntry r = e;
+            r.di = sp.di0;
+            r.cell = -1;
+            r.xi[0] = r.xi[1] = r.xi[2] = 0.5f;
+            P.queue[P.queue_cap - 1 - idx] = r;
+            __threadfence();  // visible to the block that searches the appended entries
+        } else {
+            atomicOr(P.err, kErrQueueOverflow);
         }
     }
-    if (P.stats && lane == 0 && nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
+    return ok;
 }
 
 constexpr int kMaxCand = 128;
 
-// Stuck walks (points outside the grid, or where the walk gave up): one block each.  All threads filter the
-// control cell's list (box, slabs, FP32 Newton); warp 0 applies the donor predicate to the survivors.
+// Block-shared state of the exhaustive search of one stuck entry.
+struct StuckShared {
+    uint32_t cand[kMaxCand];
+    float cxi[kMaxCand][3];
+    int ncand;
+    int found;
+    long long fcell;
+    double fuvw[3];
+    double3 p64;  // the point in the donor's frame: FP64 (the decision's), and as FP32 pairs
+    ff pf[3];
+    long long bin;
+};
+
+// A stuck walk (a point outside the grid, or where the walk gave up), stuck entry number q, by the whole block:
+// all threads filter the control cell's list (box, slabs, FP32 Newton), then the donor predicate runs on every
+// survivor at once; the later grids of the set's list follow if none holds the point.
 template <int IM>
-__device__ __forceinline__ void slow_stuck_body(const StepParams& S, const GridDev* __restrict__ G, unsigned bid,
-                                                unsigned nblk) {
+__device__ __forceinline__ void stuck_entry(const StepParams& S, const GridDev* __restrict__ G, uint32_t q,
+                                            StuckShared& sh, unsigned& nref, unsigned& nfb) {
     const AsmParams& P = S.a;
     static_assert(kMaxCand <= kSlowThreads, "one thread per candidate");
     constexpr long long kNoCellLL = 0x7FFFFFFFFFFFFFFFll;
-    __shared__ uint32_t cand[kMaxCand];
-    __shared__ float cxi[kMaxCand][3];
-    __shared__ int ncand;
-    __shared__ int found;
-    __shared__ long long fcell;
-    __shared__ double fuvw[3];
-    __shared__ double3 sp64;   // the point in the donor's frame: FP64 (the decision's), and as FP32 pairs
-    __shared__ ff spf[3];
-    __shared__ long long sbin;
-    const uint32_t count = min(P.queue_count[1], (uint32_t)P.queue_cap);
     const int lane = (int)lane_id();
     const int warp = threadIdx.x >> 5;
-    unsigned nref = 0, nfb = 0;
-    for (uint32_t q = bid; q < count; q += nblk) {
-        const SlowEntry e = P.queue[P.queue_cap - 1 - q];
-        const SlowPoint sp = slow_point(P, e);
-        const SetDev& s = P.s[sp.si];
-        bool done = false;
-        for (int di = sp.di0; di < s.ndonor && !done; ++di) {
-            const int gd = s.donors[di];
-            const GridDev& g = G[gd];
-            // the point and its control cell, by one thread (FP64 is slow here) for the whole block
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const double3 p0 = point64(P, G, sp, gd);
-                sbin = point_bin(g, p0);
-                ff q[3];
-                if (!point_ff(P, G, sp, di, q)) {
-                    q[0] = split_double(p0.x);
-                    q[1] = split_double(p0.y);
-                    q[2] = split_double(p0.z);
-                }
-                sp64 = p0;
-                spf[0] = q[0];
-                spf[1] = q[1];
-                spf[2] = q[2];
+    const SlowEntry e = load_entry(P.queue + (P.queue_cap - 1 - q));
+    const SlowPoint sp = slow_point(P, e);
+    const SetDev& s = P.s[sp.si];
+    bool done = false;
+    for (int di = sp.di0; di < s.ndonor && !done; ++di) {
+        const int gd = s.donors[di];
+        const GridDev& g = G[gd];
+        // the point and its control cell, by one thread (FP64 is slow here) for the whole block
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double3 p0 = point64(P, G, sp, gd);
+            sh.bin = point_bin(g, p0);
+            ff pq[3];
+            if (!point_ff(P, G, sp, di, pq)) {
+                pq[0] = split_double(p0.x);
+                pq[1] = split_double(p0.y);
+                pq[2] = split_double(p0.z);
             }
-            __syncthreads();
-            const double3 p = sp64;
-            const int64_t b = sbin;
-            if (b < 0) continue;  // outside the bins' box: no cell of this grid holds the point
-            const ff pf[3] = {spf[0], spf[1], spf[2]};
-            if (threadIdx.x == 0) {
-                ncand = 0;
-                found = 0;
-            }
-            __syncthreads();
-            const int32_t r0 = __ldg(g.bin_start + b), r1 = __ldg(g.bin_start + b + 1);
-            for (int32_t r = r0 + (int32_t)threadIdx.x; r < r1; r += kSlowThreads) {
-                uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
-                float xi[3];
-                if (exhaustive_filter(g, pf, c, xi)) {
-                    int k = atomicAdd(&ncand, 1);
-                    if (k < kMaxCand) {
-                        cand[k] = c;
-                        cxi[k][0] = xi[0];
-                        cxi[k][1] = xi[1];
-                        cxi[k][2] = xi[2];
-                    }
-                }
-            }
-            __syncthreads();
-            const int nc = ncand;
-            if (nc <= kMaxCand) {
-                // the exact test on every survivor at once, a thread per candidate; the lowest containing id wins
-                if (threadIdx.x == 0) fcell = kNoCellLL;
-                __syncthreads();
-                double a = 0, bb = 0, cc = 0;
-                bool hit = false;
-                uint32_t c = 0xFFFFFFFFu;
-                if ((int)threadIdx.x < nc) {
-                    c = cand[threadIdx.x];
-                    hit = contains_exact(g, c, pf, [&]() { return p; }, cxi[threadIdx.x][0], cxi[threadIdx.x][1],
-                                         cxi[threadIdx.x][2], a, bb, cc);
-                    if (hit) atomicMin((unsigned long long*)&fcell, (unsigned long long)c);
-                }
-                __syncthreads();
-                if (hit && (long long)c == fcell) {
-                    found = 1;
-                    fuvw[0] = a;
-                    fuvw[1] = bb;
-                    fuvw[2] = cc;
-                }
-            } else if (warp == 0) {
-                // more survivors than the list holds: the warp-cooperative exhaustive search
-                int64_t cell = -1;
-                double u = 0, v = 0, w = 0;
-                const bool ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
-                if (ok && lane == 0) {
-                    found = 1;
-                    fcell = cell;
-                    fuvw[0] = u;
-                    fuvw[1] = v;
-                    fuvw[2] = w;
-                }
-            }
-            __syncthreads();
-            ++nfb;
-            if (found) {
-                if (threadIdx.x == 0)
-                    finish<IM>(S, G, sp, gd, fcell, fuvw[0], fuvw[1], fuvw[2],
-                               OVS_STATUS_FOUND | OVS_STATUS_REFINED | OVS_STATUS_FALLBACK);
-                done = true;
-                ++nref;
-            }
-            __syncthreads();
+            sh.p64 = p0;
+            sh.pf[0] = pq[0];
+            sh.pf[1] = pq[1];
+            sh.pf[2] = pq[2];
         }
-        if (!done && threadIdx.x == 0) finish_none<IM>(S, sp.t);
+        __syncthreads();
+        const double3 p = sh.p64;
+        const int64_t b = sh.bin;
+        if (b < 0) continue;  // outside the bins' box: no cell of this grid holds the point
+        const ff pf[3] = {sh.pf[0], sh.pf[1], sh.pf[2]};
+        if (threadIdx.x == 0) {
+            sh.ncand = 0;
+            sh.found = 0;
+        }
+        __syncthreads();
+        const int32_t r0 = __ldg(g.bin_start + b), r1 = __ldg(g.bin_start + b + 1);
+        for (int32_t r = r0 + (int32_t)threadIdx.x; r < r1; r += kSlowThreads) {
+            uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
+            float xi[3];
+            if (exhaustive_filter(g, pf, c, xi)) {
+                int k = atomicAdd(&sh.ncand, 1);
+                if (k < kMaxCand) {
+                    sh.cand[k] = c;
+                    sh.cxi[k][0] = xi[0];
+                    sh.cxi[k][1] = xi[1];
+                    sh.cxi[k][2] = xi[2];
+                }
+            }
+        }
+        __syncthreads();
+        const int nc = sh.ncand;
+        if (nc <= kMaxCand) {
+            // the exact test on every survivor at once, a thread per candidate; the lowest containing id wins
+            if (threadIdx.x == 0) sh.fcell = kNoCellLL;
+            __syncthreads();
+            double a = 0, bb = 0, cc = 0;
+            bool hit = false;
+            uint32_t c = 0xFFFFFFFFu;
+            if ((int)threadIdx.x < nc) {
+                c = sh.cand[threadIdx.x];
+                hit = contains_exact(g, c, pf, [&]() { return p; }, sh.cxi[threadIdx.x][0], sh.cxi[threadIdx.x][1],
+                                     sh.cxi[threadIdx.x][2], a, bb, cc);
+                if (hit) atomicMin((unsigned long long*)&sh.fcell, (unsigned long long)c);
+            }
+            __syncthreads();
+            if (hit && (long long)c == sh.fcell) {
+                sh.found = 1;
+                sh.fuvw[0] = a;
+                sh.fuvw[1] = bb;
+                sh.fuvw[2] = cc;
+            }
+        } else if (warp == 0) {
+            // more survivors than the list holds: the warp-cooperative exhaustive search
+            int64_t cell = -1;
+            double u = 0, v = 0, w = 0;
+            const bool ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
+            if (ok && lane == 0) {
+                sh.found = 1;
+                sh.fcell = cell;
+                sh.fuvw[0] = u;
+                sh.fuvw[1] = v;
+                sh.fuvw[2] = w;
+            }
+        }
+        __syncthreads();
+        ++nfb;
+        if (sh.found) {
+            if (threadIdx.x == 0)
+                finish<IM>(S, G, sp, gd, sh.fcell, sh.fuvw[0], sh.fuvw[1], sh.fuvw[2],
+                           OVS_STATUS_FOUND | OVS_STATUS_REFINED | OVS_STATUS_FALLBACK);
+            done = true;
+            ++nref;
+        }
+        __syncthreads();
     }
-    if (P.stats && threadIdx.x == 0) {
-        if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
-        if (nfb) atomicAdd(P.counters + kCtrFallback, (unsigned long long)nfb);
-    }
+    if (!done && threadIdx.x == 0) finish_none<IM>(S, sp.t);
 }
 
-// The slow paths, one after the other on the stream: the near-face decisions (a warp per entry), then the
-// exhaustive searches (a block per entry) of the stuck walks and of the near-face points none of whose
-// neighbouring cells holds them.
+// The slow paths in one persistent kernel, so that the near-face decisions and the exhaustive searches run at
+// the same time.  Blocks take units from a counter: first the stuck entries of the assembly kernel (a block
+// each: they are the long ones), then groups of kSlowWarps near-face entries (a warp each).  A near-face point
+// none of whose neighbouring cells holds it is appended behind the stuck entries; the block that finishes the
+// last group (counted after every appended entry is visible) searches those appended entries itself, so no block
+// ever waits for another.
 template <int IM>
-__global__ void __launch_bounds__(kSlowThreads) k_slow_near(const StepParams* __restrict__ Sp,
-                                                            const GridDev* __restrict__ G) {
-    slow_near_body<IM>(*Sp, G, blockIdx.x, gridDim.x);
-}
-
-template <int IM>
-__global__ void __launch_bounds__(kSlowThreads) k_slow_stuck(const StepParams* __restrict__ Sp,
-                                                             const GridDev* __restrict__ G) {
-    slow_stuck_body<IM>(*Sp, G, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restrict__ Sp,
+                                                       const GridDev* __restrict__ G) {
+    const StepParams& S = *Sp;
+    const AsmParams& P = S.a;
+    __shared__ StuckShared sh;
+    __shared__ uint32_t s_unit;
+    __shared__ int s_last;
+    const uint32_t n_near = min(P.queue_count[0], (uint32_t)P.queue_cap);
+    const uint32_t n_stuck0 = min(P.queue_count[1], (uint32_t)P.queue_cap);  // final: the assembly kernel has ended
+    const uint32_t n_groups = (n_near + kSlowWarps - 1) / kSlowWarps;
+    const uint32_t n_units = n_stuck0 + n_groups;
+    unsigned nref_near = 0, nref = 0, nfb = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(P.queue_count + 3, 1u);
+        __syncthreads();
+        const uint32_t u = s_unit;
+        __syncthreads();
+        if (u >= n_units) break;
+        if (u < n_stuck0) {
+            stuck_entry<IM>(S, G, u, sh, nref, nfb);
+            continue;
+        }
+        const uint32_t q = (u - n_stuck0) * kSlowWarps + (threadIdx.x >> 5);
+        if (q < n_near && near_entry<IM>(S, G, q, n_near, n_stuck0)) ++nref_near;
+        __syncthreads();  // every entry this group appended has been written and fenced
+        if (threadIdx.x == 0) s_last = atomicAdd(P.queue_count + 4, 1u) + 1 == n_groups;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const uint32_t n_app = min(atomicAdd(P.queue_count + 5, 0u), (uint32_t)P.queue_cap);
+            for (uint32_t k = 0; k < n_app && n_stuck0 + k < (uint32_t)P.queue_cap - n_near; ++k)
+                stuck_entry<IM>(S, G, n_stuck0 + k, sh, nref, nfb);
+        }
+    }
+    if (P.stats) {
+        if ((threadIdx.x & 31) == 0 && nref_near) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref_near);
+        if (threadIdx.x == 0) {
+            if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
+            if (nfb) atomicAdd(P.counters + kCtrFallback, (unsigned long long)nfb);
+        }
+    }
 }
 
 }  // namespace
@@ -915,8 +957,9 @@ cudaError_t launch_assemble(const StepParams* dS, int interp, bool mlp, uint32_t
                             int nsm, int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev) {
     const unsigned ab = (unsigned)(nsm * (asm_bps > 0 ? asm_bps : kAsmMinBlocks));
     const unsigned sb = (unsigned)(nsm * (slow_bps > 0 ? slow_bps : 1));
-    // the two queue counters and the work counter
-    cudaError_t err = cudaMemsetAsync(queue_count, 0, 3 * sizeof(uint32_t), st);
+    // the queue counters and the work counters (near-face, stuck, assembly work, slow-path work, near-face groups
+    // done, near-face entries appended to the stuck ones)
+    cudaError_t err = cudaMemsetAsync(queue_count, 0, kQueueCounters * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
     // the learned guess in its own instantiation: without it the kernel holds no call site whose saved
@@ -933,14 +976,9 @@ cudaError_t launch_assemble(const StepParams* dS, int interp, bool mlp, uint32_t
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
-    if (interp == 1) k_slow_near<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    else if (interp == 2) k_slow_near<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    else k_slow_near<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    if (interp == 1) k_slow_stuck<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    else if (interp == 2) k_slow_stuck<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
-    else k_slow_stuck<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    if (interp == 1) k_slow<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else if (interp == 2) k_slow<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else k_slow<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

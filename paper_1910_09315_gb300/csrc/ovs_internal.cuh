@@ -115,6 +115,9 @@ struct FieldsDev {
     int32_t pad;
 };
 
+// the slow-path queue's counters (zeroed before each assembly call)
+constexpr int kQueueCounters = 6;
+
 struct SlowEntry {
     int32_t t;      // point index
     int32_t di;     // bits 0-7: position in the set's donor list to resume at; bits 8-13: near-face mask
@@ -194,7 +197,9 @@ struct AsmParams {
     void* out_xi;
     uint8_t* out_status;
     SlowEntry* queue;
-    uint32_t* queue_count;  // [0] near-face queue, [1] stuck queue, [2] work counter of k_assemble
+    uint32_t* queue_count;  // kQueueCounters: [0] near-face queue, [1] stuck queue (from k_assemble), [2] work
+                            // counter of k_assemble, [3] work counter of k_slow, [4] near-face groups done,
+                            // [5] near-face entries appended to the stuck ones
     unsigned long long* counters;
     int32_t* err;
     unsigned long long* guess_used;  // learned-guess statistics counter, or NULL
@@ -591,20 +596,18 @@ static __device__ __noinline__ int newton_ff(const GridDev& g, int64_t cell, con
     float m_prev = 3.4e38f, m_noise = 0.f, rho = 0.f;
 #pragma unroll 1
     for (int it = 0; it < kNewtonMaxIt64; ++it) {
-        // residual: sum over corners a = 1..7 of N_a(xi) (X_a - X_0), minus (p - X_0)
+        // residual: sum over corners a = 1..7 of N_a(xi) (X_a - X_0), minus (p - X_0), corner by corner
         const ff one = {1.f, 0.f};
         const ff mu = ff_sub(one, U), mv = ff_sub(one, V), mw = ff_sub(one, W);
-        const ff b00 = ff_mul(mu, mv), b10 = ff_mul(U, mv), b01 = ff_mul(mu, V), b11 = ff_mul(U, V);
-        const ff N[7] = {ff_mul(b10, mw), ff_mul(b01, mw), ff_mul(b11, mw), ff_mul(b00, W),
-                         ff_mul(b10, W),  ff_mul(b01, W),  ff_mul(b11, W)};
-        float F[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ff f = ff_neg(d[c]);
-#pragma unroll
-            for (int a = 0; a < 7; ++a) f = ff_add(f, ff_mul(N[a], E[a][c]));
-            F[c] = __fadd_rn(f.hi, f.lo);
+        ff f0 = ff_neg(d[0]), f1 = ff_neg(d[1]), f2 = ff_neg(d[2]);
+#pragma unroll 1
+        for (int a = 1; a < 8; ++a) {
+            const ff N = ff_mul(ff_mul((a & 1) ? U : mu, (a & 2) ? V : mv), (a & 4) ? W : mw);
+            f0 = ff_add(f0, ff_mul(N, E[a - 1][0]));
+            f1 = ff_add(f1, ff_mul(N, E[a - 1][1]));
+            f2 = ff_add(f2, ff_mul(N, E[a - 1][2]));
         }
+        const float F[3] = {__fadd_rn(f0.hi, f0.lo), __fadd_rn(f1.hi, f1.lo), __fadd_rn(f2.hi, f2.lo)};
         // step with the FP32 Jacobian at the FP32 iterate
         const float fu = U.hi, fv = V.hi, fw = W.hi;
         float Ju[3], Jv[3], Jw[3];
