@@ -883,7 +883,9 @@ def oracle_points_per_s(sc, motions, fsets, sample_n: int, rng, grids=None):
     import oracle
 
     if grids is None:
-        grids = [oracle.OracleGrid.from_gen(g) for g in sc.grids]
+        # the oracle's grids and every receiver grid's node coordinates: inputs, formed before any timing
+        grids = ([oracle.OracleGrid.from_gen(g) for g in sc.grids], [g.xyz() for g in sc.grids])
+    ogrids, xyz = grids
     frames = [oracle.frame_of(m) for m in motions]
     sizes = np.array([len(s.node_ids) for s in fsets], dtype=np.int64)
     tot = sizes.sum()
@@ -894,7 +896,7 @@ def oracle_points_per_s(sc, motions, fsets, sample_n: int, rng, grids=None):
         if k == 0:
             continue
         ids = s.node_ids if k >= sz else np.sort(rng.choice(s.node_ids, size=k, replace=False))
-        d = oracle.assemble(grids, frames, sc.grids[s.receiver].xyz(), s.receiver, ids, s.donors)
+        d = oracle.assemble(ogrids, frames, xyz[s.receiver], s.receiver, ids, s.donors)
         oracle.interpolate(d, sc.fields, frames, s.receiver)
         n += len(ids)
     return n, time.perf_counter() - t0, grids
