@@ -936,8 +936,10 @@ def run_reference(args, rank, world):
     K, W = args.steps, args.warmup
     inputs, _ = step_inputs(sc, W + K, DISTINCT_STEPS.get(args.workload, 0), workers=host_workers())
     rng = np.random.default_rng(11)
-    per_step = 20_000
-    grids = None
+    # each step a bounded sample of its fringe points, sized from a first probe step so that the K + W steps take
+    # about 90 s of oracle time in all (at most 20 k points a step)
+    n0, dt0, grids = oracle_points_per_s(sc, inputs[0][0], inputs[0][1], 2_000, rng, None)
+    per_step = int(max(500, min(20_000, 90.0 * (n0 / max(dt0, 1e-9)) / max(1, W + K))))
     for s in range(W):
         _, _, grids = oracle_points_per_s(sc, inputs[s][0], inputs[s][1], per_step, rng, grids)
     tot_n, tot_t = 0, 0.0

@@ -149,3 +149,32 @@ def test_bad_face_is_reported(torch_cuda):
         scene.ctx.interface_flux(0, scene.torch.zeros(1, dtype=scene.torch.int64, device=scene.ctx.device),
                                  tuple(scene.torch.zeros(4, device=scene.ctx.device) for _ in range(3)),
                                  correct=True)  # a correction needs a surface
+
+
+def test_a_surface_of_thousands_of_chunks(torch_cuda):
+    """A closed surface listed 80 times over (4.5 M faces: more than 4096 chunks of 1024 faces, so the chunk length
+    grows) sums to 80 times the net and area of one copy, every copy keeps the single copy's face fluxes bit for
+    bit, and the correction (net over area, the same ratio) matches the oracle's on one copy."""
+    sc = gen.config(1)
+    scene = GpuScene(sc, max_points=16)
+    g = sc.grids[0]
+    faces1, signs1 = gen.index_box_surface(g.dims, g.periodic, (3, 5, 7), (100, 96, 110))
+    R = 80
+    faces = np.tile(faces1, R)
+    signs = np.tile(signs1, R).astype(np.int8)
+    xyz = g.xyz()
+    vel = np.sin(3 * xyz) + 0.2
+    got, nets = run_flux(scene, 0, faces, signs, [0, len(faces)], vel, correct=False)
+    got_c, nets_c = run_flux(scene, 0, faces, signs, [0, len(faces)], vel, correct=True)
+    m = len(faces1)
+    one = got[:m]
+    assert all(np.array_equal(got[r * m:(r + 1) * m], one) for r in range(R))
+    U = oracle.face_fluxes(g.dims, g.periodic, xyz, vel, faces1)
+    Uc, nref, aref = oracle.mass_correct(g.dims, g.periodic, xyz, U, faces1, signs1, [0, m])
+    scale = np.sum(np.abs(U))
+    assert abs(nets[0] - R * nref[0]) <= 1e-9 * R * scale
+    assert abs(nets[1] - R * aref[0]) <= 1e-9 * R * aref[0]
+    assert np.array_equal(nets, nets_c)
+    S = np.array([np.linalg.norm(oracle.face_area_vector(xyz, oracle.face_nodes(g.dims, g.periodic, f))) for f in faces1])
+    tol = 1e-9 * (np.abs(vel).max() * S + scale * S / aref[0])
+    assert all(np.all(np.abs(got_c[r * m:(r + 1) * m] - Uc) <= tol) for r in (0, R // 2, R - 1))
