@@ -883,9 +883,11 @@ def oracle_points_per_s(sc, motions, fsets, sample_n: int, rng, grids=None):
     import oracle
 
     if grids is None:
-        # the oracle's grids and every receiver grid's node coordinates: inputs, formed before any timing
-        grids = ([oracle.OracleGrid.from_gen(g) for g in sc.grids], [g.xyz() for g in sc.grids])
-    ogrids, xyz = grids
+        # the oracle's grids, every receiver grid's node coordinates and the donor fields in FP64 (the oracle's
+        # precision): inputs, formed once before any timing
+        fields64 = [{k: np.asarray(f[k], dtype=np.float64) for k in ("u", "v", "w", "p")} for f in sc.fields]
+        grids = ([oracle.OracleGrid.from_gen(g) for g in sc.grids], [g.xyz() for g in sc.grids], fields64)
+    ogrids, xyz, fields64 = grids
     frames = [oracle.frame_of(m) for m in motions]
     sizes = np.array([len(s.node_ids) for s in fsets], dtype=np.int64)
     tot = sizes.sum()
@@ -897,7 +899,7 @@ def oracle_points_per_s(sc, motions, fsets, sample_n: int, rng, grids=None):
             continue
         ids = s.node_ids if k >= sz else np.sort(rng.choice(s.node_ids, size=k, replace=False))
         d = oracle.assemble(ogrids, frames, xyz[s.receiver], s.receiver, ids, s.donors)
-        oracle.interpolate(d, sc.fields, frames, s.receiver)
+        oracle.interpolate(d, fields64, frames, s.receiver)
         n += len(ids)
     return n, time.perf_counter() - t0, grids
 
