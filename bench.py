@@ -144,16 +144,18 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the kernel's source
-    has not changed since the capture (the summary records the source hash); else None."""
+def profile_traffic(workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the summary covers this
+    workload and the kernel's source has not changed since the capture (the summary records the workload and
+    the source hash); else None."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
-    if not m_hash or not m_tr or m_hash.group(1) != kernel_hash():
+    m_wl = re.search(r"traffic_workload:\s*(\S+)", txt)
+    if not m_hash or not m_tr or not m_wl or m_wl.group(1) != workload or m_hash.group(1) != kernel_hash():
         return None
     return float(m_tr.group(1))
 
@@ -624,7 +626,7 @@ def run_ovs(args, rank, world, local):
     fast_avg_ms = float(np.mean(fast_ms))
     pts_per_step = pts / K
     achieved = BYTES_FUSED * pts_per_step / (fast_avg_ms / 1e3) / 1e9
-    traffic = profile_traffic()
+    traffic = profile_traffic(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
