@@ -643,7 +643,7 @@ def run_ovs(args, rank, world, local):
                    "distinct_time_steps": n_distinct},
         "hbm_frac_model": value / world * BYTES_POINT / (peak * 1e9),
         "breakdown_ms_per_step": {"k_assemble (with the interpolation of its points)": fast_avg_ms,
-                                  "k_slow (with the interpolation of its points)":
+                                  "k_slow + k_slow_tail (with the interpolation of their points)":
                                       float(np.mean(slow_ms))},
         "launch_modes_ms_per_step": {"graph": mode_ms["graph"], "direct": mode_ms["direct"],
                                      "direct_traced": float(np.mean(traced_ms)),
@@ -660,7 +660,7 @@ def run_ovs(args, rank, world, local):
                        "copy-in and step s-1's copy-out overlap step s's kernels; host wall clock over the K "
                        "steps, L2 flushed once before",
                 "serial_ms_per_step": e2e_ref},
-        "gpu_launches": 2 * K,  # per step: k_assemble, k_slow (both interpolating)
+        "gpu_launches": 3 * K,  # per step: k_assemble, k_slow, k_slow_tail (all interpolating)
         "clocks": ck,
         "walk_stats": stats,
         "plain_unbatched_ms_per_step": unbatched_ms,

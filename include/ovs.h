@@ -360,8 +360,9 @@ int ovs_set_donors(ovs_ctx* ctx, int32_t grid_id, const uint32_t* src);
 typedef struct {
     int32_t assemble_blocks_per_sm; /* k_assemble, 256 threads a block: 1..12 */
     int32_t interp_blocks_per_sm;   /* k_interp, 256 threads a block: 1..32 */
-    int32_t slow_blocks_per_sm;     /* the slow-path kernel (near-face decisions and exhaustive searches side
-                                       by side), 256 threads a block: 1..8 */
+    int32_t slow_blocks_per_sm;     /* the slow-path kernels (near-face decisions and exhaustive searches side
+                                       by side, then the searches the decisions hand on), 256 threads a block:
+                                       1..8 */
     int32_t guess_blocks_per_sm;    /* 0..32, accepted and kept but without effect: the learned guess runs inside
                                        the assembly kernel, in its launch shape */
     int32_t launch;                 /* OVS_LAUNCH_GRAPH or OVS_LAUNCH_DIRECT (the option of ovs_set_options);
@@ -425,7 +426,7 @@ int ovs_autotune_guess(ovs_ctx* ctx, const ovs_fringe_set* sets, int32_t nsets, 
 
 /* Tracing: record caller-created CUDA events (cudaEvent_t, NULL to skip one) on the context's stream at
  * fixed points of later calls: ev[0] before the fast assembly kernel, ev[1] after it, ev[2] after the
- * slow-path kernel (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it; ev[5] and ev[6]
+ * slow-path kernels (end of ovs_assemble), ev[3] before the interpolation kernel, ev[4] after it; ev[5] and ev[6]
  * are not recorded (the learned guess runs inside the fast assembly kernel, between ev[0] and ev[1]).  In
  * ovs_assemble_interpolate the two assembly kernels interpolate each point as they decide its donor (there is
  * no interpolation kernel): ev[3] and ev[4] are then both recorded after the slow-path kernel.

@@ -13,6 +13,7 @@
 //                    a face, one warp each (the donor predicate, FP32-pair Newton on the node coordinates and FP64
 //                    where that cannot decide, over the cells sharing the near faces / edges / corner, one lane
 //                    each, lowest linear id first; a point none of them holds joins the stuck entries).
+//   k_slow_tail      the stuck entries k_slow appended, a block each (usually none).
 //
 // In a call that also interpolates (ovs_assemble_interpolate) the kernels go on, for every point whose donor
 // they decide, to the trilinear interpolation of u, v, w, p and the frame velocity transform (Sec. 2.2.6,
@@ -725,8 +726,7 @@ __device__ __forceinline__ void finish_none(const StepParams& S, int64_t t) {
     if (IM) zero_point<typename FieldT<IM>::T>(S.i.out, t);
 }
 
-// The slow-path queue entry at index q (near-face entries from the front, stuck entries from the back), read
-// past L1: entries appended during the kernel may share a line that this SM has cached before they were written.
+// A slow-path queue entry (near-face entries from the front, stuck entries from the back), read once, through L2.
 __device__ __forceinline__ SlowEntry load_entry(const SlowEntry* e) {
     const int* w = reinterpret_cast<const int*>(e);
     SlowEntry r;
@@ -764,14 +764,13 @@ __device__ __forceinline__ bool near_entry(const StepParams& S, const GridDev* _
     } else if (lane == 0) {
         // behind the stuck entries of the assembly kernel, in the back of the queue (the near-face entries hold
         // the front)
-        const uint32_t idx = n_stuck0 + atomicAdd(P.queue_count + 5, 1u);
+        const uint32_t idx = n_stuck0 + atomicAdd(P.queue_count + 4, 1u);
         if ((int64_t)idx < P.queue_cap - (int64_t)n_near) {
             SlowEntry r = e;
             r.di = sp.di0;
             r.cell = -1;
             r.xi[0] = r.xi[1] = r.xi[2] = 0.5f;
             P.queue[P.queue_cap - 1 - idx] = r;
-            __threadfence();  // visible to the block that searches the appended entries
         } else {
             atomicOr(P.err, kErrQueueOverflow);
         }
@@ -904,9 +903,7 @@ __device__ __forceinline__ void stuck_entry(const StepParams& S, const GridDev* 
 // The slow paths in one persistent kernel, so that the near-face decisions and the exhaustive searches run at
 // the same time.  Blocks take units from a counter: first the stuck entries of the assembly kernel (a block
 // each: they are the long ones), then groups of kSlowWarps near-face entries (a warp each).  A near-face point
-// none of whose neighbouring cells holds it is appended behind the stuck entries; the block that finishes the
-// last group (counted after every appended entry is visible) searches those appended entries itself, so no block
-// ever waits for another.
+// none of whose neighbouring cells holds it is appended behind the stuck entries, for k_slow_tail.
 template <int IM>
 __global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restrict__ Sp,
                                                        const GridDev* __restrict__ G) {
@@ -914,7 +911,6 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restr
     const AsmParams& P = S.a;
     __shared__ StuckShared sh;
     __shared__ uint32_t s_unit;
-    __shared__ int s_last;
     const uint32_t n_near = min(P.queue_count[0], (uint32_t)P.queue_cap);
     const uint32_t n_stuck0 = min(P.queue_count[1], (uint32_t)P.queue_cap);  // final: the assembly kernel has ended
     const uint32_t n_groups = (n_near + kSlowWarps - 1) / kSlowWarps;
@@ -932,15 +928,6 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restr
         }
         const uint32_t q = (u - n_stuck0) * kSlowWarps + (threadIdx.x >> 5);
         if (q < n_near && near_entry<IM>(S, G, q, n_near, n_stuck0)) ++nref_near;
-        __syncthreads();  // every entry this group appended has been written and fenced
-        if (threadIdx.x == 0) s_last = atomicAdd(P.queue_count + 4, 1u) + 1 == n_groups;
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            const uint32_t n_app = min(atomicAdd(P.queue_count + 5, 0u), (uint32_t)P.queue_cap);
-            for (uint32_t k = 0; k < n_app && n_stuck0 + k < (uint32_t)P.queue_cap - n_near; ++k)
-                stuck_entry<IM>(S, G, n_stuck0 + k, sh, nref, nfb);
-        }
     }
     if (P.stats) {
         if ((threadIdx.x & 31) == 0 && nref_near) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref_near);
@@ -951,14 +938,35 @@ __global__ void __launch_bounds__(kSlowThreads) k_slow(const StepParams* __restr
     }
 }
 
+// The near-face points k_slow appended to the stuck entries (none of their neighbouring cells holds them): the
+// exhaustive search, a block each.  Usually there are none and the launch ends at once; with many (blanked donor
+// cells, FP64 local coordinates) they are searched side by side rather than by one block.
+template <int IM>
+__global__ void __launch_bounds__(kSlowThreads) k_slow_tail(const StepParams* __restrict__ Sp,
+                                                            const GridDev* __restrict__ G) {
+    const StepParams& S = *Sp;
+    const AsmParams& P = S.a;
+    __shared__ StuckShared sh;
+    const uint32_t n_near = min(P.queue_count[0], (uint32_t)P.queue_cap);
+    const uint32_t n_stuck0 = min(P.queue_count[1], (uint32_t)P.queue_cap);
+    const uint32_t n_app = min(P.queue_count[4], (uint32_t)P.queue_cap);
+    unsigned nref = 0, nfb = 0;
+    for (uint32_t k = blockIdx.x; k < n_app && n_stuck0 + k < (uint32_t)P.queue_cap - n_near; k += gridDim.x)
+        stuck_entry<IM>(S, G, n_stuck0 + k, sh, nref, nfb);
+    if (P.stats && threadIdx.x == 0) {
+        if (nref) atomicAdd(P.counters + kCtrRefined, (unsigned long long)nref);
+        if (nfb) atomicAdd(P.counters + kCtrFallback, (unsigned long long)nfb);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_assemble(const StepParams* dS, int interp, bool mlp, uint32_t* queue_count, const GridDev* dgrids,
                             int nsm, int asm_bps, int slow_bps, cudaStream_t st, cudaEvent_t const* ev) {
     const unsigned ab = (unsigned)(nsm * (asm_bps > 0 ? asm_bps : kAsmMinBlocks));
     const unsigned sb = (unsigned)(nsm * (slow_bps > 0 ? slow_bps : 1));
-    // the queue counters and the work counters (near-face, stuck, assembly work, slow-path work, near-face groups
-    // done, near-face entries appended to the stuck ones)
+    // the queue counters and the work counters (near-face, stuck, assembly work, slow-path work, near-face entries
+    // appended to the stuck ones)
     cudaError_t err = cudaMemsetAsync(queue_count, 0, kQueueCounters * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
@@ -979,6 +987,11 @@ cudaError_t launch_assemble(const StepParams* dS, int interp, bool mlp, uint32_t
     if (interp == 1) k_slow<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
     else if (interp == 2) k_slow<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
     else k_slow<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if (interp == 1) k_slow_tail<1><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else if (interp == 2) k_slow_tail<2><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
+    else k_slow_tail<0><<<sb, kSlowThreads, 0, st>>>(dS, dgrids);
     if (ev && ev[2]) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

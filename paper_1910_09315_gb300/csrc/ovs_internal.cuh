@@ -116,7 +116,7 @@ struct FieldsDev {
 };
 
 // the slow-path queue's counters (zeroed before each assembly call)
-constexpr int kQueueCounters = 6;
+constexpr int kQueueCounters = 5;
 
 struct SlowEntry {
     int32_t t;      // point index
@@ -198,8 +198,8 @@ struct AsmParams {
     uint8_t* out_status;
     SlowEntry* queue;
     uint32_t* queue_count;  // kQueueCounters: [0] near-face queue, [1] stuck queue (from k_assemble), [2] work
-                            // counter of k_assemble, [3] work counter of k_slow, [4] near-face groups done,
-                            // [5] near-face entries appended to the stuck ones
+                            // counter of k_assemble, [3] work counter of k_slow, [4] near-face entries
+                            // appended to the stuck ones (searched by k_slow_tail)
     unsigned long long* counters;
     int32_t* err;
     unsigned long long* guess_used;  // learned-guess statistics counter, or NULL
