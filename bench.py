@@ -615,6 +615,8 @@ def run_ovs(args, rank, world, local):
     total_ms, e2e_total, pts_all = combine_ranks(world, total_ms, e2e_ms, float(pts), dev)
     stats = None
     if rank == 0:
+        # a warm step, as in the timed region: the hints are those of the step before
+        one_step(W - 1, dev_sets[W - 1])
         ctx.set_options(collect_stats=1)
         ctx.stats(reset=True)
         one_step(W, dev_sets[W])
