@@ -1,14 +1,14 @@
 """Benchmark of the overset assembly + interpolation step on GB300.
 
 One step = one time step of the moving-overset workload: set the frames of the moving grids
-(ovs_set_motion), find the donors of every fringe point (ovs_assemble) and interpolate u, v, w, p with the
-frame velocity transform (ovs_interpolate).  Default workload: the moving-ellipsoid case (stretched
-curvilinear background 128^3, 96x64x64 O-grid rotating at 2 pi rad/time and translating at 0.3/time,
-dt = 1e-3, 100 time steps, FP64 coordinates, FP32 fields), synthetic and seeded.
+(ovs_set_motion), then find the donors of every fringe point and interpolate u, v, w, p with the frame
+velocity transform in one call (ovs_assemble_interpolate).  Default workload: the school of 16 fish O-grids
+(64^3 to 160x96x96) in a stretched curvilinear 512x384x256 background (~50 M nodes), FP64 coordinates,
+FP32 fields, ~2.8 M fringe points a step, synthetic and seeded; --workload selects a smaller one.
 
 Prints ONE JSON line (rank 0).  Metric: fringe points assembled + interpolated per second.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ovs|reference] [--workload cfg1|cfg0|cfg2]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ovs|reference] [--workload cfg0..cfg4]
 
 --impl reference times the plain FP64 CPU oracle (the method written out from the paper) on the host cores,
 on a bounded sample of the same workload per step.
