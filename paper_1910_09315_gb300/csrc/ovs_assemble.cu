@@ -550,7 +550,10 @@ __device__ bool neighbourhood_warp(const GridDev& g, const ff pf[3], const P64& 
     return true;
 }
 
-constexpr int kSlowThreads = 256;
+// 512 threads (16 warps) at the 128 registers the slow-path code takes anyway: a stuck entry whose control cell
+// lists thousands of cells filters them twice as fast as with 256 (the exhaustive search of the most crowded
+// control cells is the slow kernel's longest chain), and 16 near-face entries run side by side per block
+constexpr int kSlowThreads = 512;
 constexpr int kSlowWarps = kSlowThreads / 32;
 
 // Cheap rejections of one cell of an exhaustive search, all in FP32 from the point's FP32 pair (offsets to corner 0
