@@ -186,7 +186,8 @@ int ovs_workspace_size(const ovs_ctx* ctx, int64_t max_points, size_t* bytes);
 int ovs_workspace_attach(ovs_ctx* ctx, void* dptr, size_t bytes, int64_t max_points);
 
 /* Bytes of the per-grid workspace for a grid of these dimensions: cell records (128 B per cell),
- * control-cell bins and the per-node donor hints. */
+ * control-cell bins, the finer bins of crowded control cells (about 2 MiB plus up to 8 B per cell, at most
+ * 32 MiB), the node coordinates as FP32 pairs and the per-node donor hints. */
 int ovs_grid_workspace_size(const ovs_grid_desc* desc, size_t* bytes);
 /* Register a structured curvilinear grid (Sec. 2.2: one block of the composite grid).  Builds, in the
  * caller's workspace, per-cell records and the control cells of Sec. 2.2.5 (uniform axis-aligned bins over
@@ -208,6 +209,14 @@ int ovs_create_grid(ovs_ctx* ctx, const ovs_grid_desc* desc, void* dworkspace, s
  * Synchronises the stream.  Errors: OVS_ERR_ARG (unknown grid, flag not 0 or 1). */
 int ovs_grid_check(const ovs_ctx* ctx, int32_t grid_id, int64_t cells[3], int32_t* overlap);
 int ovs_set_grid_overlap(ovs_ctx* ctx, int32_t grid_id, int32_t overlap);
+/* The control cells of a grid (Sec. 2.2.5: the uniform axis-aligned bins that start the walk and bound the
+ * exhaustive search; each cell is listed in every bin its padded box overlaps), as built by ovs_create_grid:
+ * out[0] bins, out[1] registrations in their lists, out[2] crowded control cells (lists of more than 256 cells,
+ * as around a thin or clustered region; the threshold doubles until at most 4096 of them, and their finer lists,
+ * fit the grid workspace) that were split into 4 x 4 x 4 finer bins, out[3] registrations in those finer bins.  The exhaustive search of a point in a split control cell reads only its finer bin's list, which
+ * holds every cell whose padded box reaches the point (the same rule one level down), so results do not depend
+ * on the split.  Host only.  Errors: OVS_ERR_ARG (unknown grid, out NULL). */
+int ovs_grid_bins(const ovs_ctx* ctx, int32_t grid_id, int64_t out[4]);
 
 /* Set a grid's rigid frame (Sec. 2.1, Fig. "non-inertial"): R (row-major 3x3, body -> inertial, must be
  * orthogonal with det +1 to 1e-12), origin c, translational velocity V and angular velocity omega (inertial

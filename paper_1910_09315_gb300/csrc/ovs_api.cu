@@ -32,6 +32,7 @@ struct GridHost {
     size_t ws_bytes;
     int64_t nbins;
     int64_t nreg;
+    int64_t nsubreg;  // registrations in the finer bins of crowded control cells
     int64_t orient[3];  // cells right-handed, left-handed, folded or degenerate (corner Jacobians at creation)
 };
 
@@ -115,8 +116,9 @@ void identity_motion(MotionDev& m) {
 int64_t cells_axis(const ovs_grid_desc& d, int a) { return d.periodic[a] ? d.n[a] : d.n[a] - 1; }
 
 struct GridLayout {
-    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, xff, mlp, partials, scan, out9, total;
-    int64_t ncells, nnodes, nbins_max, reg_cap;
+    size_t rec, bin_start, bin_count, bin_rep, bin_cells, hint, xff, mlp, partials, scan, out9, crowd, sub_start,
+        sub_count, sub_cells, total;
+    int64_t ncells, nnodes, nbins_max, reg_cap, sub_cap;
 };
 
 GridLayout grid_layout(const ovs_grid_desc& d) {
@@ -145,9 +147,19 @@ GridLayout grid_layout(const ovs_grid_desc& d) {
     L.partials = off;
     off = align_up(off + (size_t)kReduceBlocks * 9 * sizeof(double));
     L.scan = off;
-    off = align_up(off + scan_scratch_elems(L.nbins_max) * 4);
+    off = align_up(off + scan_scratch_elems(std::max<int64_t>(L.nbins_max, (int64_t)kMaxCrowded * kSub3)) * 4);
     L.out9 = off;
     off = align_up(off + 9 * sizeof(double) + 3 * sizeof(unsigned long long));
+    // the finer bins of crowded control cells: their ids (and a device counter), list starts, counts, lists
+    L.sub_cap = std::min<int64_t>(2 * L.ncells + 4096, (int64_t)1 << 23);
+    L.crowd = off;
+    off = align_up(off + (size_t)kMaxCrowded * 4 + 16);
+    L.sub_start = off;
+    off = align_up(off + ((size_t)kMaxCrowded * kSub3 + 1) * 4);
+    L.sub_count = off;
+    off = align_up(off + (size_t)kMaxCrowded * kSub3 * 4);
+    L.sub_cells = off;
+    off = align_up(off + (size_t)L.sub_cap * 4);
     L.total = off;
     return L;
 }
@@ -527,6 +539,52 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
         break;
     }
     if (nreg == 0 && L.ncells > 0) return fail(c, OVS_ERR_WORKSPACE, "control-cell lists exceed the workspace");
+    // crowded control cells (thin or clustered cells crowding a bin, as at a fish's tail) get kSub^3 finer bins,
+    // which the exhaustive search reads instead of the whole list; the threshold is raised until their number
+    // and registrations fit the space set aside (none split is always a valid outcome)
+    g.crowd = (const int32_t*)(base + L.crowd);
+    g.sub_start = (const int32_t*)(base + L.sub_start);
+    g.sub_cells = (const int32_t*)(base + L.sub_cells);
+    g.ncrowd = 0;
+    int64_t nsubreg = 0;
+    if (nreg > 0) {
+        int32_t* crowd = (int32_t*)(base + L.crowd);
+        uint32_t* dn = (uint32_t*)(base + L.crowd + (size_t)kMaxCrowded * 4);
+        uint32_t* counts = (uint32_t*)(base + L.sub_count);
+        int32_t* sstart = (int32_t*)(base + L.sub_start);
+        const int64_t nbins = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+        for (int32_t thr = kCrowdedCount; thr < (1 << 29); thr *= 2) {
+            OVS_CUDA(c, cudaMemsetAsync(dn, 0, sizeof(uint32_t), c->stream));
+            OVS_CUDA(c, launch_crowd_mark(g, nbins, thr, crowd, dn, kMaxCrowded, c->stream));
+            uint32_t hn = 0;
+            OVS_CUDA(c, cudaMemcpyAsync(&hn, dn, sizeof hn, cudaMemcpyDeviceToHost, c->stream));
+            OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (hn == 0) break;
+            if (hn > (uint32_t)kMaxCrowded) continue;
+            std::vector<int32_t> hc(hn);
+            OVS_CUDA(c, cudaMemcpyAsync(hc.data(), crowd, hn * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+            std::sort(hc.begin(), hc.end());  // the search looks a control cell up by bisection
+            OVS_CUDA(c, cudaMemcpyAsync(crowd, hc.data(), hn * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+            OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+            g.ncrowd = (int32_t)hn;
+            const int64_t nsub = (int64_t)hn * kSub3;
+            OVS_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nsub * 4, c->stream));
+            OVS_CUDA(c, launch_sub_count(g, counts, c->stream));
+            OVS_CUDA(c, launch_scan(counts, sstart, nsub, (uint32_t*)(base + L.scan), c->stream));
+            int32_t tot = 0;
+            OVS_CUDA(c, cudaMemcpyAsync(&tot, sstart + nsub, 4, cudaMemcpyDeviceToHost, c->stream));
+            OVS_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (tot < 0 || (int64_t)tot > L.sub_cap) {
+                g.ncrowd = 0;
+                continue;
+            }
+            OVS_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nsub * 4, c->stream));
+            OVS_CUDA(c, launch_sub_fill(g, sstart, counts, (int32_t*)(base + L.sub_cells), c->stream));
+            nsubreg = tot;
+            break;
+        }
+    }
     OVS_CUDA(c, cudaMemsetAsync(base + L.hint, 0xFF, (size_t)L.nnodes * 4, c->stream));
     OVS_CUDA(c, cudaMemsetAsync(base + L.mlp, 0, sizeof(MlpHeader), c->stream));  // no guess network yet
     int id = c->ngrids;
@@ -535,6 +593,7 @@ int ovs_create_grid(ovs_ctx* c, const ovs_grid_desc* d, void* dws, size_t bytes,
     c->gh[id].ws = dws;
     c->gh[id].ws_bytes = bytes;
     c->gh[id].nreg = nreg;
+    c->gh[id].nsubreg = nsubreg;
     for (int q = 0; q < 3; ++q) c->gh[id].orient[q] = (int64_t)ho[q];
     identity_motion(c->motion[id]);
     OVS_CUDA(c, cudaMemcpyAsync(c->d_grids + id, &c->grids[id], sizeof(GridDev), cudaMemcpyHostToDevice, c->stream));
@@ -550,6 +609,15 @@ int ovs_grid_check(const ovs_ctx* c, int32_t gid, int64_t cells[3], int32_t* ove
     if (cells)
         for (int q = 0; q < 3; ++q) cells[q] = c->gh[gid].orient[q];
     if (overlap) *overlap = c->grids[gid].overlap;
+    return OVS_OK;
+}
+
+int ovs_grid_bins(const ovs_ctx* c, int32_t gid, int64_t out[4]) {
+    if (!c || !out || gid < 0 || gid >= c->ngrids) return OVS_ERR_ARG;
+    out[0] = c->gh[gid].nbins;
+    out[1] = c->gh[gid].nreg;
+    out[2] = c->grids[gid].ncrowd;
+    out[3] = c->gh[gid].nsubreg;
     return OVS_OK;
 }
 

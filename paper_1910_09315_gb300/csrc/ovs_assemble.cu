@@ -630,14 +630,13 @@ __device__ __noinline__ bool exhaustive_filter(const GridDev& g, const ff pf[3],
 }
 
 // Warp-level exhaustive search of a control cell (lanes stride its list); lowest id wins.  All lanes call.
-__device__ bool exhaustive_warp(const GridDev& g, double3 p, const ff pf[3], int64_t b, int64_t& cell, double& u,
-                                double& v, double& w) {
+__device__ bool exhaustive_warp(const GridDev& g, double3 p, const ff pf[3], const int32_t* list, int32_t r0,
+                                int32_t r1, int64_t& cell, double& u, double& v, double& w) {
     const int lane = (int)lane_id();
     uint32_t best = 0xFFFFFFFFu;
     double bu = 0, bv = 0, bw = 0;
-    int32_t r0 = __ldg(g.bin_start + b), r1 = __ldg(g.bin_start + b + 1);
     for (int32_t r = r0 + lane; r < r1; r += 32) {
-        uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
+        uint32_t c = (uint32_t)__ldg(list + r);
         if (c >= best) continue;
         float xi[3];
         if (!exhaustive_filter(g, pf, c, xi)) continue;
@@ -794,6 +793,8 @@ struct StuckShared {
     double3 p64;  // the point in the donor's frame: FP64 (the decision's), and as FP32 pairs
     ff pf[3];
     long long bin;
+    int32_t r0, r1;  // the candidate list: [r0, r1) of the control cell's list, or of its finer bin's (sub = 1)
+    int32_t sub;
 };
 
 // A stuck walk (a point outside the grid, or where the walk gave up), stuck entry number q, by the whole block:
@@ -819,6 +820,11 @@ __device__ __forceinline__ void stuck_entry(const StepParams& S, const GridDev* 
         if (threadIdx.x == 0) {
             const double3 p0 = point64(P, G, sp, gd);
             sh.bin = point_bin(g, p0);
+            if (sh.bin >= 0) {
+                const int32_t* list;
+                candidate_list(g, p0, sh.bin, list, sh.r0, sh.r1);
+                sh.sub = list != g.bin_cells;
+            }
             ff pq[3];
             if (!point_ff(P, G, sp, di, pq)) {
                 pq[0] = split_double(p0.x);
@@ -840,9 +846,10 @@ __device__ __forceinline__ void stuck_entry(const StepParams& S, const GridDev* 
             sh.found = 0;
         }
         __syncthreads();
-        const int32_t r0 = __ldg(g.bin_start + b), r1 = __ldg(g.bin_start + b + 1);
+        const int32_t r0 = sh.r0, r1 = sh.r1;
+        const int32_t* list = sh.sub ? g.sub_cells : g.bin_cells;
         for (int32_t r = r0 + (int32_t)threadIdx.x; r < r1; r += kSlowThreads) {
-            uint32_t c = (uint32_t)__ldg(g.bin_cells + r);
+            uint32_t c = (uint32_t)__ldg(list + r);
             float xi[3];
             if (exhaustive_filter(g, pf, c, xi)) {
                 int k = atomicAdd(&sh.ncand, 1);
@@ -880,7 +887,7 @@ __device__ __forceinline__ void stuck_entry(const StepParams& S, const GridDev* 
             // more survivors than the list holds: the warp-cooperative exhaustive search
             int64_t cell = -1;
             double u = 0, v = 0, w = 0;
-            const bool ok = exhaustive_warp(g, p, pf, b, cell, u, v, w);
+            const bool ok = exhaustive_warp(g, p, pf, list, r0, r1, cell, u, v, w);
             if (ok && lane == 0) {
                 sh.found = 1;
                 sh.fcell = cell;

@@ -174,6 +174,53 @@ __global__ void __launch_bounds__(kBuildThreads) k_bin_fill(GridDev g, const int
     }
 }
 
+// Crowded control cells: those listing more than thr cells.
+__global__ void __launch_bounds__(kBuildThreads) k_crowd_mark(const int32_t* start, int64_t nbins, int32_t thr,
+                                                              int32_t* crowd, uint32_t* n, int cap) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nbins; b += (int64_t)gridDim.x * blockDim.x)
+        if (start[b + 1] - start[b] > thr) {
+            const uint32_t k = atomicAdd(n, 1u);
+            if (k < (uint32_t)cap) crowd[k] = (int32_t)b;
+        }
+}
+
+// The finer bins of crowded control cell b that a cell's padded box overlaps, per axis [s0, s1].
+__device__ __forceinline__ void cell_sub_range(const GridDev& g, const CellRec& r, int64_t b, int s0[3], int s1[3]) {
+    double lo[3], hi[3];
+    rec_box(r, lo, hi);
+    const int bi[3] = {(int)(b % g.nb[0]), (int)((b / g.nb[0]) % g.nb[1]), (int)(b / ((int64_t)g.nb[0] * g.nb[1]))};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s0[c] = sub_coord(g, c, lo[c], bi[c]);
+        s1[c] = sub_coord(g, c, hi[c], bi[c]);
+    }
+}
+
+// One block per crowded control cell; its threads take the cells of its list.  FILL = false: count the
+// registrations per finer bin; true: write them at start (cursor counts them again from zero).
+template <bool FILL>
+__global__ void __launch_bounds__(kBuildThreads) k_sub_bins(GridDev g, uint32_t* counts, const int32_t* start,
+                                                            int32_t* cells) {
+    for (int k = blockIdx.x; k < g.ncrowd; k += gridDim.x) {
+        const int64_t b = g.crowd[k];
+        const int32_t r0 = g.bin_start[b], r1 = g.bin_start[b + 1];
+        for (int32_t r = r0 + (int32_t)threadIdx.x; r < r1; r += kBuildThreads) {
+            const int32_t cell = g.bin_cells[r];
+            CellRec rec;
+            load_rec(g.rec, cell, rec);
+            int s0[3], s1[3];
+            cell_sub_range(g, rec, b, s0, s1);
+            for (int sz = s0[2]; sz <= s1[2]; ++sz)
+                for (int sy = s0[1]; sy <= s1[1]; ++sy)
+                    for (int sx = s0[0]; sx <= s1[0]; ++sx) {
+                        const int64_t sb = (int64_t)k * kSub3 + sub_index(sx, sy, sz);
+                        const uint32_t pos = atomicAdd(counts + sb, 1u);
+                        if (FILL) cells[start[sb] + pos] = cell;
+                    }
+        }
+    }
+}
+
 // ---- exclusive scan of uint32 counts into int32 offsets (n + 1 entries) ----
 constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
@@ -295,6 +342,26 @@ cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint3
     k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, start, n, block_sums);
     k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, ntiles, start + n);
     k_scan_add<<<(unsigned)ntiles, kScanThreads, 0, st>>>(start, n, block_sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crowd_mark(const GridDev& g, int64_t nbins, int32_t thr, int32_t* crowd, uint32_t* n, int cap,
+                              cudaStream_t st) {
+    const int64_t nb = (nbins + kBuildThreads - 1) / kBuildThreads;
+    const int blocks = (int)(nb < 152 * 64 ? (nb > 0 ? nb : 1) : 152 * 64);
+    k_crowd_mark<<<blocks, kBuildThreads, 0, st>>>(g.bin_start, nbins, thr, crowd, n, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_count(const GridDev& g, uint32_t* counts, cudaStream_t st) {
+    if (g.ncrowd <= 0) return cudaSuccess;
+    k_sub_bins<false><<<(unsigned)g.ncrowd, kBuildThreads, 0, st>>>(g, counts, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, cudaStream_t st) {
+    if (g.ncrowd <= 0) return cudaSuccess;
+    k_sub_bins<true><<<(unsigned)g.ncrowd, kBuildThreads, 0, st>>>(g, cursor, start, cells);
     return cudaGetLastError();
 }
 

@@ -67,7 +67,20 @@ struct GridDev {
     int32_t blanked;  // 1 once ovs_set_iblank gave the grid a mask (cell records then carry blocked flags)
     int32_t overlap;  // 1: cells may overlap one another (folded cells found, or said by the caller): no point is
                       // final from the walk alone; each goes to the exhaustive lowest-id search of its control cell
+    // crowded control cells (lists longer than a threshold), ascending bin id, each split into kSub^3 finer bins
+    // whose lists the exhaustive search reads instead (every cell registered in each finer bin its padded box
+    // overlaps, as in the first level)
+    const int32_t* crowd;
+    const int32_t* sub_start;  // ncrowd * kSub3 + 1
+    const int32_t* sub_cells;
+    int32_t ncrowd;
+    int32_t pad2;
 };
+
+constexpr int kSub = 4;                 // finer bins per axis inside a crowded control cell
+constexpr int kSub3 = kSub * kSub * kSub;
+constexpr int32_t kCrowdedCount = 256;  // a control cell listing more cells than this is split (first try)
+constexpr int kMaxCrowded = 4096;       // split control cells per grid at most
 
 struct MotionDev {
     double R[9];  // body -> inertial, row-major
@@ -387,6 +400,39 @@ __device__ __forceinline__ int64_t corner_node(const GridDev& g, int i, int j, i
     return (int64_t)ii + (int64_t)g.n[0] * ((int64_t)jj + (int64_t)g.n[1] * kk);
 }
 
+// Index of finer bin (sx, sy, sz) in a crowded control cell, kSub per axis.
+__device__ __forceinline__ int sub_index(int sx, int sy, int sz) { return sx + kSub * (sy + kSub * sz); }
+
+// The finer bin along one axis of a coordinate x inside control cell bi (the control cells' own arithmetic,
+// (x - lo) * inv_w, minus the cell's index, times kSub, floored and clamped): monotone in x, so a point inside a
+// cell's padded box falls in one of the finer bins that box was registered in.
+__device__ __forceinline__ int sub_coord(const GridDev& g, int c, double x, int bi) {
+    const double t = ((x - g.lo[c]) * g.inv_w[c] - (double)bi) * (double)kSub;
+    return (int)fmin(fmax(floor(t), 0.0), (double)(kSub - 1));
+}
+
+// The candidate list of the exhaustive search for a point in control cell b (which must be >= 0): the control
+// cell's own list, or, in a crowded control cell, the list of the finer bin holding the point.
+__device__ __forceinline__ void candidate_list(const GridDev& g, double3 p, int64_t b, const int32_t*& list,
+                                               int32_t& r0, int32_t& r1) {
+    list = g.bin_cells;
+    r0 = __ldg(g.bin_start + b);
+    r1 = __ldg(g.bin_start + b + 1);
+    if (g.ncrowd <= 0 || r1 - r0 <= kCrowdedCount) return;
+    int lo = 0, hi = g.ncrowd - 1;
+    while (lo < hi) {  // the split control cells are sorted by id
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(g.crowd + mid) < b) lo = mid + 1; else hi = mid;
+    }
+    if (__ldg(g.crowd + lo) != (int32_t)b) return;
+    const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    const int64_t sb = (int64_t)lo * kSub3 + sub_index(sub_coord(g, 0, p.x, bx), sub_coord(g, 1, p.y, by),
+                                                       sub_coord(g, 2, p.z, bz));
+    list = g.sub_cells;
+    r0 = __ldg(g.sub_start + sb);
+    r1 = __ldg(g.sub_start + sb + 1);
+}
+
 // bin of a donor-frame point; -1 when outside the padded bounding box (no cell can contain it)
 __device__ __forceinline__ int64_t point_bin(const GridDev& g, double3 p) {
     if (!(p.x >= g.lo[0] && p.x <= g.hi[0] && p.y >= g.lo[1] && p.y <= g.hi[1] && p.z >= g.lo[2] &&
@@ -702,6 +748,13 @@ constexpr int kScanTileElems = 2048;
 cudaError_t launch_scan(const uint32_t* counts, int32_t* start, int64_t n, uint32_t* block_sums, cudaStream_t st);
 // marks each cell of g blocked (a corner with iblank 0) or not (iblank NULL: none blocked)
 cudaError_t launch_mark_blocked(const GridDev& g, const uint8_t* iblank, cudaStream_t st);
+// appends to crowd the control cells listing more than thr cells (n: their count, which may exceed cap)
+cudaError_t launch_crowd_mark(const GridDev& g, int64_t nbins, int32_t thr, int32_t* crowd, uint32_t* n, int cap,
+                              cudaStream_t st);
+// per finer bin of the g.ncrowd crowded control cells (g.crowd), the number of cells registered (counts) / their
+// lists (cells at start, cursor zeroed)
+cudaError_t launch_sub_count(const GridDev& g, uint32_t* counts, cudaStream_t st);
+cudaError_t launch_sub_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, cudaStream_t st);
 cudaError_t launch_bin_fill(const GridDev& g, const int32_t* start, uint32_t* cursor, int32_t* cells, int32_t* rep,
                             cudaStream_t st);
 size_t scan_scratch_elems(int64_t n);

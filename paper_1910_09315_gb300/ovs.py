@@ -62,6 +62,7 @@ EXPORTS = [
     "ovs_interface_flux",
     "ovs_grid_check",
     "ovs_set_grid_overlap",
+    "ovs_grid_bins",
 ]
 
 OVS_NOALLOC_MAX_POINTS = 1 << 20
@@ -180,6 +181,7 @@ def load(path: Optional[str] = None):
                          I32, ctypes.POINTER(ovs_fields_out), I32, ctypes.POINTER(ovs_tuning)],
         "ovs_grid_check": [V, I32, V, ctypes.POINTER(I32)],
         "ovs_set_grid_overlap": [V, I32, I32],
+        "ovs_grid_bins": [V, I32, V],
         "ovs_interface_flux": [V, I32, I64, V, V, I32, V, ctypes.POINTER(ovs_fields), V, V, I32],
         "ovs_autotune_guess": [V, ctypes.POINTER(ovs_fringe_set), I32, ctypes.POINTER(ovs_donors),
                                ctypes.POINTER(ovs_fields), I32, ctypes.POINTER(ovs_fields_out), I32, V, V, I32, V,
@@ -373,6 +375,13 @@ def ovs_grid_check(ctx, grid_id: int):
     ov = ctypes.c_int32()
     _check(ctx, load().ovs_grid_check(ctx, int(grid_id), cells, ctypes.byref(ov)))
     return tuple(int(x) for x in cells), bool(ov.value)
+
+
+def ovs_grid_bins(ctx, grid_id: int):
+    """(control cells, their registrations, crowded control cells split into finer bins, finer-bin registrations)."""
+    out = (ctypes.c_int64 * 4)()
+    _check(ctx, load().ovs_grid_bins(ctx, int(grid_id), out))
+    return tuple(int(x) for x in out)
 
 
 def ovs_set_grid_overlap(ctx, grid_id: int, overlap: bool):
