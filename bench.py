@@ -658,7 +658,7 @@ def run_ovs(args, rank, world, local):
                 "d2h_bytes_per_step": d2h // K,
                 "how": "a time loop through the C ABI: per step one H2D copy of its node ids (pinned), "
                        "ovs_set_motion per grid + ovs_assemble_interpolate, D2H of u, v, w, p and status (pinned); "
-                       "copies on two copy streams, two device buffer sets alternating, so that step s+1's "
+                       "copies on two copy streams, three device buffer sets in turn, so that step s+1's "
                        "copy-in and step s-1's copy-out overlap step s's kernels; host wall clock over the K "
                        "steps, L2 flushed once before",
                 "serial_ms_per_step": e2e_ref},
@@ -683,14 +683,14 @@ def end_to_end(ctx, lib, inputs, host_sets, dev_sets, prep, layout, max_pts, xi_
     """End to end: steps W .. W+K-1 from pinned host node ids to pinned host outputs.  The headline drives the
     C ABI as a C caller's time loop would (structs marshalled once; one H2D copy of the step's node ids on a copy
     stream; the library's calls on its stream after that copy; the D2H copies of u, v, w, p and status on a
-    second copy stream after the call; two device buffer sets alternating, so that copies of neighbouring steps
+    second copy stream after the call; three device buffer sets in turn, so that copies of neighbouring steps
     overlap a step's kernels), timed by the host wall clock over the K steps.  For reference, per-step
     synchronous figures (ms per step): the same C-ABI calls with each step's copies and kernels in sequence, and
     the Python binding (one copy per set, the binding's marshalling on every call).  Returns (total ms,
     H2D bytes, D2H bytes, references)."""
     ctypes_ = __import__("ctypes")
     host_ids = [torch.cat([ids for _, ids, _ in host_sets[s]]).pin_memory() for s in range(W + K)]
-    nb = 2
+    nb = 3  # device buffer sets in turn (with two, a step's call waited on the copy-out of the step two before)
     dstage = [torch.empty(max_pts, dtype=torch.int32, device=dev) for _ in range(nb)]
     ddon = [ctx.alloc_donors(max_pts, xi_dtype) for _ in range(nb)]
     # a step's four output fields side by side in one buffer (u of its n points, then v, w, p), so that one copy
