@@ -1,5 +1,6 @@
 // Grid set-up kernels: per-cell records and the control cells of Sec. 2.2.5 (uniform axis-aligned
-// bins over the grid's bounding box, each cell registered in every bin its padded box overlaps).
+// bins over the grid's bounding box, each cell registered in every bin its padded box overlaps), and the finer
+// bins of crowded control cells (the same registration one level down).
 #include <float.h>
 
 #include "ovs_internal.cuh"
